@@ -1,0 +1,138 @@
+/*
+ * snect.h -- C ABI of the GB300 SNeCT library.
+ *
+ * SNeCT (Choi & Sael, arXiv 1711.08095) fits a Tucker model X ~ G x1 U1 x2 U2 x3 U3
+ * (Eq. 2) to the observed cells of a sparse patient x gene x platform tensor, with an L2
+ * term (Eq. 3, in the per-entry form of Sec. 2.3.2) and a gene-network term
+ * lambda_g * f_g (graph regulariser of Sec. 2.3.1), by the stochastic gradient sweep of
+ * Alg. 1.  This library runs that sweep, the network pass, the objective, fold-in of new
+ * patients (Eq. 9) and top-k patient search (Sec. 3.2.1) on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SNECT_OK (0) or a negative SNECT_E* code; no C++ exception crosses the
+ *     ABI.  snect_last_error() returns a message for the last failing call on a context.
+ *   - Pointers marked "any" may point to host memory (pageable or pinned) or to device
+ *     memory of the context's GPU; the library copies from them during the call and keeps no
+ *     reference afterwards.  Pointers marked "host" must be host memory.
+ *   - Indices are 0-based (the paper counts from 1).  An entry is (i, j, k) =
+ *     (patient, gene, platform), stored as 3 consecutive int32.
+ *   - The core G is J1*J2*J3 floats, g(p,q,r) at (p*J2 + q)*J3 + r; factor U_n is I_n*J_n
+ *     floats, row-major.
+ *   - All device work runs on the stream given at snect_init (the caller's stream, e.g.
+ *     PyTorch's current stream), or on a stream the context creates if that is NULL.  Calls
+ *     that return results on the host synchronise that stream.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef SNECT_H
+#define SNECT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNECT_OK 0
+#define SNECT_EINVAL (-1)   /* bad argument: size, index out of range, NaN, self loop ... */
+#define SNECT_ENOMEM (-2)   /* a device allocation failed */
+#define SNECT_ECUDA (-3)    /* a CUDA call failed; see snect_last_error */
+#define SNECT_ETIMEDOUT (-4)
+#define SNECT_EBUSY (-5)
+
+#define SNECT_FP32 0
+#define SNECT_BF16 1
+
+typedef struct snect_ctx snect_ctx;
+
+/* Hyper-parameters of Alg. 1 (inputs "core size (J1..JN), learning rate eta, regularisation
+ * factors lambda and lambda_g"; the network constrains mode 2, the genes). */
+typedef struct {
+    int32_t I[3];      /* tensor dims I1 (patients), I2 (genes), I3 (platforms) */
+    int32_t J[3];      /* core ranks J1, J2, J3; each in [1, 32], J1*J2*J3 <= 5120 */
+    float lambda;      /* L2 weight lambda */
+    float lambda_g;    /* network weight lambda_g */
+    float lr;          /* learning rate eta */
+    int32_t batch;     /* > 0: deterministic mode, fixed-order mini-batches of this many
+                          entries (<= 4096); 0: fast mode (lock-free sweep) */
+    int32_t wave;      /* fast mode: entries between two updates of the core and the
+                          platform factor (0 = library default) */
+    int32_t precision; /* SNECT_FP32 (SNECT_BF16 reserved) */
+    uint64_t seed;     /* reserved; the caller supplies the visit order and the init */
+} snect_config;
+
+/* Objective terms after the last update (Eq. 3 + Sec. 2.3.2 + graph regulariser), FP64. */
+typedef struct {
+    double data;       /* 1/2 sum over training entries of (x - x~)^2 */
+    double reg;        /* lambda/2 (||G||^2 + sum_n sum_{i observed} ||u_i^(n)||^2) */
+    double graph;      /* f_g = 1/2 sum_edges y ||u^(2)_k1 - u^(2)_k2||^2 */
+    double total;      /* data + reg + lambda_g * graph  (f_opt) */
+    double rmse_train; /* sqrt(mean (x - x~)^2) over the training entries */
+    double rmse_test;  /* same over the test entries passed to snect_loss (0 if none) */
+} snect_loss_t;
+
+/* Creates a context and copies the problem to the GPU (Alg. 1 inputs: tensor X, network Y,
+ * hyper-parameters; line 1's initial G and U are supplied by the caller).
+ *   idx   any, nnz*3 int32 training entries, in the order the sweep visits them
+ *         (deterministic mode cuts this order into consecutive batches)
+ *   val   any, nnz float
+ *   edges any, m*2 int32 undirected gene pairs, each edge once, no self loops
+ *   w     any, m float edge weights y > 0
+ *   G0, U1, U2, U3  any, initial core and factors (layouts above)
+ *   stream  a cudaStream_t, or NULL
+ * Validates ranges (indices, sizes, finite values, self loops); computes the counts
+ * |Omega^{n,i}| and the per-batch row grouping on the GPU.  On failure *out is NULL. */
+int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, const float *val,
+               int64_t nnz, const int32_t *edges, const float *w, int64_t m, const float *G0,
+               const float *U1, const float *U2, const float *U3, void *stream);
+
+/* Runs n_epochs epochs of Alg. 1 lines 2-14: the entry sweep (every batch in order, or the
+ * fast sweep) followed by one network pass over the gene factor.  Asynchronous. */
+int snect_epoch(snect_ctx *ctx, int32_t n_epochs);
+
+/* Deterministic mode only: runs mini-batches [first, first+count) of the visit order
+ * (Alg. 1 lines 4-8, each batch evaluated at its start parameters, contributions summed).
+ * Asynchronous. */
+int snect_batches(snect_ctx *ctx, int64_t first, int64_t count);
+
+/* One network pass over the gene factor (Alg. 1 line 10, every edge applied to both of its
+ * endpoints; each gene row walks its neighbours in ascending order against the snapshot of
+ * the factor taken when the pass starts).  Asynchronous. */
+int snect_edge_pass(snect_ctx *ctx);
+
+/* Objective terms and RMSE (Eq. 3, Sec. 2.3.2, graph regulariser; f_opt = f + lambda_g f_g).
+ * test_idx/test_val: any, n_test held-out entries (may be 0).  Synchronises. */
+int snect_loss(snect_ctx *ctx, const int32_t *test_idx, const float *test_val, int64_t n_test,
+               snect_loss_t *out);
+
+/* Copies the current core and factors out to / in from any memory (layouts above). */
+int snect_get_factors(snect_ctx *ctx, float *G, float *U1, float *U2, float *U3);
+int snect_set_factors(snect_ctx *ctx, const float *G, const float *U1, const float *U2,
+                      const float *U3);
+
+/* Fold-in of one new patient (Eq. 9), holding G, U2, U3 fixed: with w_jk = G x2 u2_j x3 u3_k,
+ * u = (sum w w^T + lambda I)^{-1} sum x w over the query's n observed (gene, platform) cells.
+ * The J1 x J1 Gram and right-hand side are summed in FP32 on the GPU in a fixed order and
+ * solved by an FP64 Cholesky factorisation.  jk: any, n*2 int32; val: any, n float;
+ * u_out: any, J1 floats.  Returns SNECT_EINVAL if n < 1 or the system is not positive
+ * definite.  Synchronises. */
+int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n, float *u_out);
+
+/* Top-k search (Sec. 3.2.1): the k rows of U1 with the largest cosine similarity to u
+ * (J1 floats, any), descending, ties to the lower row index, a zero-norm row scores 0.
+ * idx_out (int32) / score_out (float): any, k each.  1 <= k <= min(I1, 64).  Synchronises. */
+int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, float *score_out);
+
+/* Number of kernel launches the context has issued so far (for launch accounting). */
+int64_t snect_launch_count(const snect_ctx *ctx);
+
+/* Message for the last failing call on ctx (or for the last failing snect_init if ctx is
+ * NULL).  The string stays valid until the next call on the context. */
+const char *snect_last_error(const snect_ctx *ctx);
+
+/* Frees the context's device memory and graphs.  NULL is a no-op. */
+void snect_destroy(snect_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNECT_H */

@@ -1,0 +1,250 @@
+"""GB300 SNeCT: network-constrained Tucker decomposition by SGD on one GPU.
+
+Thin Python binding of the C ABI in ``include/snect.h`` (library ``libsnect.so``, built
+from ``csrc/`` by ``build.py``).  Every computation runs in the library's CUDA kernels;
+this module only marshals arguments.  Importing the package does not need a GPU;
+creating a context does, and there is no CPU fallback: if the library is missing or no
+GPU is visible the calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA memory); the
+library copies them during the call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Config", "LossTerms", "Snect", "SnectError", "load", "lib_path", "EXPORTS", "FP32", "BF16"]
+
+FP32 = 0
+BF16 = 1
+
+# every symbol include/snect.h declares
+EXPORTS = (
+    "snect_init",
+    "snect_epoch",
+    "snect_batches",
+    "snect_edge_pass",
+    "snect_loss",
+    "snect_get_factors",
+    "snect_set_factors",
+    "snect_foldin",
+    "snect_topk",
+    "snect_launch_count",
+    "snect_last_error",
+    "snect_destroy",
+)
+
+
+class SnectError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("snect error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_int32 * 3),
+        ("J", ctypes.c_int32 * 3),
+        ("lambda_", ctypes.c_float),
+        ("lambda_g", ctypes.c_float),
+        ("lr", ctypes.c_float),
+        ("batch", ctypes.c_int32),
+        ("wave", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class LossTerms(ctypes.Structure):
+    _fields_ = [
+        ("data", ctypes.c_double),
+        ("reg", ctypes.c_double),
+        ("graph", ctypes.c_double),
+        ("total", ctypes.c_double),
+        ("rmse_train", ctypes.c_double),
+        ("rmse_test", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libsnect.so (optionally building it first) and declares the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libsnect.so is not built; run paper_1711_08095_gb300.build.build() "
+                          "(or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "snect_init": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(Config), P, P, i64, P, P, i64, P, P, P, P, P]),
+        "snect_epoch": (ctypes.c_int, [P, i32]),
+        "snect_batches": (ctypes.c_int, [P, i64, i64]),
+        "snect_edge_pass": (ctypes.c_int, [P]),
+        "snect_loss": (ctypes.c_int, [P, P, P, i64, ctypes.POINTER(LossTerms)]),
+        "snect_get_factors": (ctypes.c_int, [P, P, P, P, P]),
+        "snect_set_factors": (ctypes.c_int, [P, P, P, P, P]),
+        "snect_foldin": (ctypes.c_int, [P, P, P, i64, P]),
+        "snect_topk": (ctypes.c_int, [P, P, i32, P, P]),
+        "snect_launch_count": (ctypes.c_int64, [P]),
+        "snect_last_error": (ctypes.c_char_p, [P]),
+        "snect_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, keep: list, dtype) -> Optional[int]:
+    """Address of a contiguous array of the given numpy dtype (numpy or torch)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            a = a.to(tdt).contiguous()
+        keep.append(a)
+        return a.data_ptr() if a.numel() else None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    keep.append(arr)
+    return arr.ctypes.data if arr.size else None
+
+
+def _current_stream():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Snect:
+    """One decomposition problem resident on the GPU (a snect_ctx)."""
+
+    def __init__(self, I: Sequence[int], J: Sequence[int], idx, val, edges, w, G0, U0, *, lam: float,
+                 lam_g: float, lr: float, batch: int = 0, wave: int = 0, stream=None, precision: int = FP32):
+        self._lib = load()
+        cfg = Config()
+        cfg.I[:] = [int(x) for x in I]
+        cfg.J[:] = [int(x) for x in J]
+        cfg.lambda_, cfg.lambda_g, cfg.lr = float(lam), float(lam_g), float(lr)
+        cfg.batch, cfg.wave, cfg.precision, cfg.seed = int(batch), int(wave), int(precision), 0
+        self.I, self.J = tuple(cfg.I), tuple(cfg.J)
+        keep = []
+        nnz = int(val.shape[0])
+        m = int(w.shape[0])
+        h = ctypes.c_void_p()
+        st = _current_stream() if stream is None else stream
+        rc = self._lib.snect_init(ctypes.byref(h), ctypes.byref(cfg), _ptr(idx, keep, np.int32),
+                                  _ptr(val, keep, np.float32), nnz, _ptr(edges, keep, np.int32),
+                                  _ptr(w, keep, np.float32), m, _ptr(G0, keep, np.float32),
+                                  _ptr(U0[0], keep, np.float32), _ptr(U0[1], keep, np.float32),
+                                  _ptr(U0[2], keep, np.float32), st)
+        if rc != 0:
+            raise SnectError(rc, self._lib.snect_last_error(None).decode())
+        self._h = h
+        self.nnz, self.m = nnz, m
+
+    # -- helpers --------------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise SnectError(rc, self._lib.snect_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.snect_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path -------------------------------------------------------------------------
+    def epoch(self, n: int = 1):
+        self._check(self._lib.snect_epoch(self._h, int(n)))
+
+    def batches(self, first: int, count: int = 1):
+        self._check(self._lib.snect_batches(self._h, int(first), int(count)))
+
+    def edge_pass(self):
+        self._check(self._lib.snect_edge_pass(self._h))
+
+    def loss(self, test_idx=None, test_val=None) -> dict:
+        keep = []
+        out = LossTerms()
+        n = 0 if test_val is None else int(test_val.shape[0])
+        self._check(self._lib.snect_loss(self._h, _ptr(test_idx, keep, np.int32) if n else None,
+                                         _ptr(test_val, keep, np.float32) if n else None, n,
+                                         ctypes.byref(out)))
+        return out.as_dict()
+
+    def get_factors(self):
+        G = np.empty(self.J, dtype=np.float32)
+        U = [np.empty((self.I[n], self.J[n]), dtype=np.float32) for n in range(3)]
+        self._check(self._lib.snect_get_factors(self._h, G.ctypes.data, U[0].ctypes.data, U[1].ctypes.data,
+                                                U[2].ctypes.data))
+        return G, U
+
+    def set_factors(self, G=None, U=(None, None, None)):
+        keep = []
+        self._check(self._lib.snect_set_factors(self._h, _ptr(G, keep, np.float32), _ptr(U[0], keep, np.float32),
+                                                _ptr(U[1], keep, np.float32), _ptr(U[2], keep, np.float32)))
+
+    def foldin(self, jk, val) -> np.ndarray:
+        keep = []
+        u = np.empty(self.J[0], dtype=np.float32)
+        self._check(self._lib.snect_foldin(self._h, _ptr(jk, keep, np.int32), _ptr(val, keep, np.float32),
+                                           int(val.shape[0]), u.ctypes.data))
+        return u
+
+    def topk(self, u, k: int = 10):
+        keep = []
+        idx = np.empty(k, dtype=np.int32)
+        sc = np.empty(k, dtype=np.float32)
+        self._check(self._lib.snect_topk(self._h, _ptr(u, keep, np.float32), int(k), idx.ctypes.data,
+                                         sc.ctypes.data))
+        return idx, sc
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.snect_launch_count(self._h))
+
+    @property
+    def handle(self):
+        return self._h

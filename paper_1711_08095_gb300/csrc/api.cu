@@ -1,0 +1,465 @@
+// C ABI entry points (include/snect.h): argument checks, device buffers, the epoch graph.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "serve.cuh"
+
+namespace snect {
+
+namespace {
+thread_local std::string g_init_error;
+
+template <typename T>
+int dmalloc(Ctx *c, T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) return SNECT_OK;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, SNECT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return SNECT_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// copies count elements from any memory into a fresh device buffer (stream-ordered)
+template <typename T>
+int stage(Ctx *c, T **dst, const T *src, int64_t count) {
+    *dst = nullptr;
+    if (count <= 0) return SNECT_OK;
+    if (!src) return fail(c, SNECT_EINVAL, "null input pointer");
+    SNECT_CUDA(c, cudaMallocAsync((void **)dst, sizeof(T) * (size_t)count, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(*dst, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, c->stream));
+    return SNECT_OK;
+}
+
+int copy_in(Ctx *c, float *dst, const float *src, int64_t count) {
+    if (!src) return fail(c, SNECT_EINVAL, "null factor pointer");
+    SNECT_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(float) * count, cudaMemcpyDefault, c->stream));
+    return SNECT_OK;
+}
+
+void free_all(Ctx *c) {
+    if (c->epoch_exec) cudaGraphExecDestroy(c->epoch_exec);
+    c->epoch_exec = nullptr;
+    free_fast(c);
+    dfree(c->rec);
+    for (int m = 0; m < 3; ++m) {
+        dfree(c->cnt[m]);
+        dfree(c->U[m]);
+        dfree(c->grp_pos[m]);
+        dfree(c->grp_head[m]);
+    }
+    dfree(c->G);
+    dfree(c->edges);
+    dfree(c->ew);
+    dfree(c->csr_ptr);
+    dfree(c->csr_col);
+    dfree(c->csr_w);
+    dfree(c->snap);
+    dfree(c->gbuf);
+    dfree(c->part);
+    dfree(c->wtable);
+    dfree(c->fold_part);
+    dfree(c->q_jk);
+    dfree(c->q_val);
+    dfree(c->q_u);
+    dfree(c->q_status);
+    dfree(c->score);
+    dfree(c->taken);
+    dfree(c->top_i);
+    dfree(c->top_s);
+    dfree(c->lacc);
+    dfree(c->flag);
+}
+
+int check_config(const snect_config *cfg, std::string *why) {
+    for (int n = 0; n < 3; ++n) {
+        if (cfg->I[n] < 1) return *why = "I_n must be >= 1", SNECT_EINVAL;
+        if (cfg->J[n] < 1 || cfg->J[n] > kMaxRank) return *why = "J_n must be in [1, 32]", SNECT_EINVAL;
+    }
+    if ((int64_t)cfg->J[0] * cfg->J[1] * cfg->J[2] > kMaxCore)
+        return *why = "J1*J2*J3 must be <= 5120", SNECT_EINVAL;
+    if (!isfinite(cfg->lambda) || cfg->lambda < 0.f) return *why = "lambda must be finite and >= 0", SNECT_EINVAL;
+    if (!isfinite(cfg->lambda_g) || cfg->lambda_g < 0.f)
+        return *why = "lambda_g must be finite and >= 0", SNECT_EINVAL;
+    if (!isfinite(cfg->lr) || cfg->lr <= 0.f) return *why = "lr must be finite and > 0", SNECT_EINVAL;
+    if (cfg->batch < 0 || cfg->batch > kMaxBatch) return *why = "batch must be in [0, 4096]", SNECT_EINVAL;
+    if (cfg->wave < 0) return *why = "wave must be >= 0", SNECT_EINVAL;
+    if (cfg->precision != SNECT_FP32) return *why = "only SNECT_FP32 is available", SNECT_EINVAL;
+    return SNECT_OK;
+}
+
+int enqueue_det_epoch(Ctx *c) {
+    const int64_t B = c->cfg.batch;
+    for (int64_t b = 0; b < c->n_batches; ++b) {
+        const int64_t first = b * B, len = std::min<int64_t>(B, c->nnz - first);
+        SNECT_CUDA(c, launch_det_grad(c, first, len));
+        SNECT_CUDA(c, launch_det_apply(c, first, len));
+    }
+    return SNECT_OK;
+}
+
+int enqueue_epoch(Ctx *c) {
+    int rc = c->cfg.batch > 0 ? enqueue_det_epoch(c) : enqueue_fast_epoch(c);
+    if (rc) return rc;
+    SNECT_CUDA(c, launch_edge_pass(c));
+    return SNECT_OK;
+}
+
+// one epoch captured once into a CUDA graph (on a private stream: capture is not allowed on
+// the legacy default stream), replayed on the context's stream
+int build_epoch_graph(Ctx *c) {
+    cudaStream_t orig = c->stream, cap = nullptr;
+    SNECT_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    c->stream = cap;
+    const int64_t before = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = SNECT_OK;
+    if (e == cudaSuccess) {
+        rc = enqueue_epoch(c);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (rc == SNECT_OK && e2 != cudaSuccess) e = e2;
+    }
+    c->stream = orig;
+    c->epoch_kernels = c->launches - before;
+    c->launches = before;
+    if (rc == SNECT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->epoch_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        c->epoch_exec = nullptr;
+        return fail(c, SNECT_ECUDA, std::string("epoch graph: ") + cudaGetErrorString(e));
+    }
+    return SNECT_OK;
+}
+
+int ensure_query_capacity(Ctx *c, int64_t n) {
+    if (n <= c->q_cap) return SNECT_OK;
+    dfree(c->q_jk);
+    dfree(c->q_val);
+    dfree(c->fold_part);
+    c->q_cap = 0;
+    int64_t cap = std::max<int64_t>(n, 1 << 16);
+    int rc = dmalloc(c, &c->q_jk, cap);
+    if (!rc) rc = dmalloc(c, &c->q_val, cap);
+    const int64_t pf = foldin_parts(cap) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1);
+    if (!rc) rc = dmalloc(c, &c->fold_part, pf);
+    if (rc) return rc;
+    c->q_cap = cap;
+    c->fold_part_cap = pf;
+    return SNECT_OK;
+}
+
+int ensure_wtable(Ctx *c) {
+    if (c->wtable_version == c->param_version && c->wtable) return SNECT_OK;
+    if (!c->wtable) {
+        int rc = dmalloc(c, &c->wtable, (int64_t)c->d.I2 * c->d.I3 * c->d.J1);
+        if (rc) return rc;
+    }
+    SNECT_CUDA(c, launch_wtable(c, c->wtable));
+    c->wtable_version = c->param_version;
+    return SNECT_OK;
+}
+
+}  // namespace
+
+int fail(Ctx *c, int code, const std::string &msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_init_error = msg;
+    return code;
+}
+
+}  // namespace snect
+
+using namespace snect;
+
+extern "C" {
+
+int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, const float *val,
+               int64_t nnz, const int32_t *edges, const float *w, int64_t m, const float *G0,
+               const float *U1, const float *U2, const float *U3, void *stream) {
+    if (!out || !cfg) return fail(nullptr, SNECT_EINVAL, "null argument");
+    *out = nullptr;
+    std::string why;
+    if (check_config(cfg, &why)) return fail(nullptr, SNECT_EINVAL, why);
+    if (nnz < 0 || m < 0) return fail(nullptr, SNECT_EINVAL, "negative size");
+    if (nnz > INT32_MAX - 1 || 2 * m > INT32_MAX - 1) return fail(nullptr, SNECT_EINVAL, "too many entries or edges");
+    if (cfg->batch == 0 && cfg->I[2] > kMaxPlatforms)
+        return fail(nullptr, SNECT_EINVAL, "fast mode needs I3 <= 64");
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return fail(nullptr, SNECT_ENOMEM, "host allocation");
+    c->cfg = *cfg;
+    c->d = Dims{cfg->I[0], cfg->I[1], cfg->I[2], cfg->J[0], cfg->J[1], cfg->J[2]};
+    c->nnz = nnz;
+    c->m = m;
+    c->PI = cfg->J[0] * cfg->J[1] * cfg->J[2];
+    c->SJ = cfg->J[0] + cfg->J[1] + cfg->J[2];
+    cudaGetDevice(&c->device);
+    int rc = SNECT_OK;
+    auto bail = [&](int code) {
+        std::string msg = c->err;
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        free_all(c);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return fail(nullptr, code, msg);
+    };
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            c->err = "cudaStreamCreate failed";
+            c->stream = nullptr;
+            return bail(SNECT_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    const Dims &d = c->d;
+    if ((rc = dmalloc(c, &c->rec, nnz)) || (rc = dmalloc(c, &c->cnt[0], d.I1)) ||
+        (rc = dmalloc(c, &c->cnt[1], d.I2)) || (rc = dmalloc(c, &c->cnt[2], d.I3)) ||
+        (rc = dmalloc(c, &c->G, c->PI)) || (rc = dmalloc(c, &c->U[0], (int64_t)d.I1 * d.J1)) ||
+        (rc = dmalloc(c, &c->U[1], (int64_t)d.I2 * d.J2)) ||
+        (rc = dmalloc(c, &c->U[2], (int64_t)d.I3 * d.J3)) || (rc = dmalloc(c, &c->edges, m)) ||
+        (rc = dmalloc(c, &c->ew, m)) || (rc = dmalloc(c, &c->csr_ptr, (int64_t)d.I2 + 1)) ||
+        (rc = dmalloc(c, &c->csr_col, 2 * m)) || (rc = dmalloc(c, &c->csr_w, 2 * m)) ||
+        (rc = dmalloc(c, &c->snap, (int64_t)d.I2 * d.J2)) || (rc = dmalloc(c, &c->lacc, 8)) ||
+        (rc = dmalloc(c, &c->flag, 4)) || (rc = dmalloc(c, &c->q_u, kMaxRank)) ||
+        (rc = dmalloc(c, &c->q_status, 1)) || (rc = dmalloc(c, &c->score, d.I1)) ||
+        (rc = dmalloc(c, &c->taken, d.I1)) || (rc = dmalloc(c, &c->top_i, 64)) ||
+        (rc = dmalloc(c, &c->top_s, 64)))
+        return bail(rc);
+    // inputs (any memory) -> device
+    int32_t *d_idx = nullptr, *d_edges = nullptr;
+    float *d_val = nullptr, *d_w = nullptr;
+    if ((rc = stage(c, &d_idx, idx, nnz * 3)) || (rc = stage(c, &d_val, val, nnz)) ||
+        (rc = stage(c, &d_edges, edges, m * 2)) || (rc = stage(c, &d_w, w, m)))
+        return bail(rc);
+    if (!rc) rc = copy_in(c, c->G, G0, c->PI);
+    if (!rc) rc = copy_in(c, c->U[0], U1, (int64_t)d.I1 * d.J1);
+    if (!rc) rc = copy_in(c, c->U[1], U2, (int64_t)d.I2 * d.J2);
+    if (!rc) rc = copy_in(c, c->U[2], U3, (int64_t)d.I3 * d.J3);
+    if (!rc) rc = prep_problem(c, d_idx, d_val);
+    if (!rc) rc = prep_graph(c, d_edges, d_w);
+    if (d_idx) cudaFreeAsync(d_idx, c->stream);
+    if (d_val) cudaFreeAsync(d_val, c->stream);
+    if (d_edges) cudaFreeAsync(d_edges, c->stream);
+    if (d_w) cudaFreeAsync(d_w, c->stream);
+    if (rc) return bail(rc);
+    if (cfg->batch > 0) {
+        c->n_batches = (nnz + cfg->batch - 1) / cfg->batch;
+        int64_t gf = 0, pf = 0;
+        det_scratch_floats(c, &gf, &pf);
+        if ((rc = dmalloc(c, &c->grp_pos[0], nnz)) || (rc = dmalloc(c, &c->grp_pos[1], nnz)) ||
+            (rc = dmalloc(c, &c->grp_pos[2], nnz)) || (rc = dmalloc(c, &c->grp_head[0], nnz)) ||
+            (rc = dmalloc(c, &c->grp_head[1], nnz)) || (rc = dmalloc(c, &c->grp_head[2], nnz)) ||
+            (rc = dmalloc(c, &c->gbuf, gf)) || (rc = dmalloc(c, &c->part, pf)))
+            return bail(rc);
+        if ((rc = prep_det_groups(c))) return bail(rc);
+        cudaError_t e = det_init_attrs(c);
+        if (e != cudaSuccess) {
+            c->err = std::string("kernel attributes: ") + cudaGetErrorString(e);
+            return bail(SNECT_ECUDA);
+        }
+    } else {
+        if ((rc = prep_fast_tiles(c))) return bail(rc);
+    }
+    cudaError_t e = loss_init_attrs(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("set-up: ") + cudaGetErrorString(e);
+        return bail(SNECT_ECUDA);
+    }
+    *out = reinterpret_cast<snect_ctx *>(c);
+    return SNECT_OK;
+}
+
+int snect_epoch(snect_ctx *h, int32_t n_epochs) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (n_epochs < 0) return fail(c, SNECT_EINVAL, "n_epochs must be >= 0");
+    if (n_epochs == 0) return SNECT_OK;
+    if (!c->epoch_exec) {
+        int rc = build_epoch_graph(c);
+        if (rc) return rc;
+    }
+    for (int32_t t = 0; t < n_epochs; ++t) {
+        SNECT_CUDA(c, cudaGraphLaunch(c->epoch_exec, c->stream));
+        c->launches += c->epoch_kernels;
+    }
+    c->param_version++;
+    return SNECT_OK;
+}
+
+int snect_batches(snect_ctx *h, int64_t first, int64_t count) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (c->cfg.batch <= 0) return fail(c, SNECT_EINVAL, "snect_batches needs deterministic mode");
+    if (first < 0 || count < 0 || first + count > c->n_batches)
+        return fail(c, SNECT_EINVAL, "batch range outside [0, n_batches)");
+    const int64_t B = c->cfg.batch;
+    for (int64_t b = first; b < first + count; ++b) {
+        const int64_t f = b * B, len = std::min<int64_t>(B, c->nnz - f);
+        SNECT_CUDA(c, launch_det_grad(c, f, len));
+        SNECT_CUDA(c, launch_det_apply(c, f, len));
+    }
+    c->param_version++;
+    return SNECT_OK;
+}
+
+int snect_edge_pass(snect_ctx *h) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    SNECT_CUDA(c, launch_edge_pass(c));
+    c->param_version++;
+    return SNECT_OK;
+}
+
+int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int64_t n_test,
+               snect_loss_t *out) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !out) return SNECT_EINVAL;
+    if (n_test < 0) return fail(c, SNECT_EINVAL, "n_test must be >= 0");
+    SNECT_CUDA(c, cudaMemsetAsync(c->lacc, 0, sizeof(double) * 8, c->stream));
+    SNECT_CUDA(c, launch_loss(c, c->rec, c->nnz, 0));
+    Rec *trec = nullptr;
+    int32_t *d_idx = nullptr;
+    float *d_val = nullptr;
+    int rc = SNECT_OK;
+    if (n_test > 0) {
+        if ((rc = stage(c, &d_idx, test_idx, n_test * 3)) || (rc = stage(c, &d_val, test_val, n_test)))
+            return rc;
+        SNECT_CUDA(c, cudaMallocAsync((void **)&trec, sizeof(Rec) * n_test, c->stream));
+        rc = pack_records(c, d_idx, d_val, n_test, trec, true, 3);
+        if (rc == SNECT_OK) {
+            cudaError_t e = launch_loss(c, trec, n_test, 1);
+            if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
+        }
+    }
+    if (rc == SNECT_OK) {
+        cudaError_t e = launch_loss_reg_graph(c);
+        if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
+    }
+    double acc[8] = {0};
+    if (rc == SNECT_OK) {
+        cudaError_t e = cudaMemcpyAsync(acc, c->lacc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
+    }
+    if (d_idx) cudaFreeAsync(d_idx, c->stream);
+    if (d_val) cudaFreeAsync(d_val, c->stream);
+    if (trec) cudaFreeAsync(trec, c->stream);
+    if (rc) return rc;
+    const double lam = c->cfg.lambda, lg = c->cfg.lambda_g;
+    out->data = 0.5 * acc[0];
+    out->reg = 0.5 * lam * acc[2];
+    out->graph = 0.5 * acc[3];
+    out->total = out->data + out->reg + lg * out->graph;
+    out->rmse_train = c->nnz ? sqrt(acc[0] / (double)c->nnz) : 0.0;
+    out->rmse_test = n_test ? sqrt(acc[1] / (double)n_test) : 0.0;
+    return SNECT_OK;
+}
+
+int snect_get_factors(snect_ctx *h, float *G, float *U1, float *U2, float *U3) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    const Dims &d = c->d;
+    if (G) SNECT_CUDA(c, cudaMemcpyAsync(G, c->G, sizeof(float) * c->PI, cudaMemcpyDefault, c->stream));
+    if (U1)
+        SNECT_CUDA(c, cudaMemcpyAsync(U1, c->U[0], sizeof(float) * d.I1 * d.J1, cudaMemcpyDefault, c->stream));
+    if (U2)
+        SNECT_CUDA(c, cudaMemcpyAsync(U2, c->U[1], sizeof(float) * (int64_t)d.I2 * d.J2, cudaMemcpyDefault,
+                                      c->stream));
+    if (U3)
+        SNECT_CUDA(c, cudaMemcpyAsync(U3, c->U[2], sizeof(float) * d.I3 * d.J3, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SNECT_OK;
+}
+
+int snect_set_factors(snect_ctx *h, const float *G, const float *U1, const float *U2, const float *U3) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    const Dims &d = c->d;
+    if (G) SNECT_CUDA(c, cudaMemcpyAsync(c->G, G, sizeof(float) * c->PI, cudaMemcpyDefault, c->stream));
+    if (U1)
+        SNECT_CUDA(c, cudaMemcpyAsync(c->U[0], U1, sizeof(float) * d.I1 * d.J1, cudaMemcpyDefault, c->stream));
+    if (U2)
+        SNECT_CUDA(c, cudaMemcpyAsync(c->U[1], U2, sizeof(float) * (int64_t)d.I2 * d.J2, cudaMemcpyDefault,
+                                      c->stream));
+    if (U3)
+        SNECT_CUDA(c, cudaMemcpyAsync(c->U[2], U3, sizeof(float) * d.I3 * d.J3, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->param_version++;
+    return SNECT_OK;
+}
+
+int snect_foldin(snect_ctx *h, const int32_t *jk, const float *val, int64_t n, float *u_out) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !u_out) return SNECT_EINVAL;
+    if (n < 1) return fail(c, SNECT_EINVAL, "a query needs at least one observed cell");
+    if (!jk || !val) return fail(c, SNECT_EINVAL, "null query pointer");
+    int rc = ensure_query_capacity(c, n);
+    if (!rc) rc = ensure_wtable(c);
+    if (rc) return rc;
+    SNECT_CUDA(c, cudaMemcpyAsync(c->q_val, val, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(c->q_jk, jk, sizeof(int2) * n, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    SNECT_CUDA(c, launch_check_cells(c, c->stream, c->q_jk, c->q_val, n, c->flag));
+    SNECT_CUDA(c, launch_foldin(c, c->stream, c->q_jk, c->q_val, n, c->wtable, c->fold_part, c->q_u,
+                                c->q_status));
+    int32_t status = 0, bad = 0;
+    SNECT_CUDA(c, cudaMemcpyAsync(&status, c->q_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(u_out, c->q_u, sizeof(float) * c->d.J1, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, SNECT_EINVAL, "query cell out of range or value not finite");
+    if (status) return fail(c, SNECT_EINVAL, "fold-in normal matrix is not positive definite");
+    return SNECT_OK;
+}
+
+int snect_topk(snect_ctx *h, const float *u, int32_t k, int32_t *idx_out, float *score_out) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !u || !idx_out || !score_out) return SNECT_EINVAL;
+    if (k < 1 || k > 64 || k > c->d.I1) return fail(c, SNECT_EINVAL, "k must be in [1, min(I1, 64)]");
+    SNECT_CUDA(c, cudaMemcpyAsync(c->q_u, u, sizeof(float) * c->d.J1, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, launch_topk(c, c->stream, c->q_u, k, c->score, c->taken, c->top_i, c->top_s));
+    SNECT_CUDA(c, cudaMemcpyAsync(idx_out, c->top_i, sizeof(int32_t) * k, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(score_out, c->top_s, sizeof(float) * k, cudaMemcpyDefault, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SNECT_OK;
+}
+
+int64_t snect_launch_count(const snect_ctx *h) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(h);
+    return c ? c->launches : 0;
+}
+
+const char *snect_last_error(const snect_ctx *h) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(h);
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+void snect_destroy(snect_ctx *h) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of libsnect.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/snect.h"
+
+namespace snect {
+
+constexpr int kMaxRank = 32;      // largest J_n
+constexpr int kMaxCore = 5120;    // largest J1*J2*J3
+constexpr int kMaxBatch = 4096;   // largest deterministic mini-batch
+constexpr int kMaxPlatforms = 64; // largest I3 in fast mode (platform rows are dense there)
+
+// One observed entry, 16 bytes: (i, j, k) and the value's bits.  One vector load per entry.
+struct __align__(16) Rec {
+    int32_t i, j, k;
+    float x;
+};
+
+struct Dims {
+    int32_t I1, I2, I3;
+    int32_t J1, J2, J3;
+};
+
+struct Ctx {
+    snect_config cfg{};
+    Dims d{};
+    int64_t nnz = 0, m = 0;
+    int32_t PI = 0, SJ = 0;  // J1*J2*J3 and J1+J2+J3
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int64_t launches = 0;
+    std::string err;
+
+    // problem
+    Rec *rec = nullptr;       // nnz entries in visit order
+    int32_t *cnt[3] = {};     // |Omega^{n,i}| per mode (training entries)
+    float *G = nullptr;       // core
+    float *U[3] = {};         // factors
+    // gene network
+    int2 *edges = nullptr;    // m undirected edges
+    float *ew = nullptr;      // m weights
+    int32_t *csr_ptr = nullptr;  // I2 + 1
+    int32_t *csr_col = nullptr;  // 2m neighbours, ascending within a row
+    float *csr_w = nullptr;      // 2m weights
+    float *snap = nullptr;       // I2*J2 snapshot for the network pass
+    int32_t max_degree = 0;
+    // deterministic mode
+    int64_t n_batches = 0;
+    int32_t *grp_pos[3] = {};    // per mode: entry positions grouped by (batch, row), stable
+    uint8_t *grp_head[3] = {};   // 1 where a row segment starts
+    float *gbuf = nullptr;       // scratch: batch * SJ per-entry row gradients
+    float *part = nullptr;       // scratch: per-CTA core partial sums
+    int32_t grad_blocks = 0;     // CTAs of the gradient kernel per full batch
+    // fast mode
+    int64_t n_waves = 0;
+    int64_t wave = 0;
+    int32_t *tile_start = nullptr;  // per tile: first entry (entries grouped by platform per wave)
+    int32_t *tile_len = nullptr;
+    int32_t *tile_k = nullptr;
+    int64_t *wave_tile = nullptr;   // host: first tile of each wave (n_waves + 1)
+    int64_t n_tiles = 0;
+    float *dense_acc = nullptr;     // per wave: core gradient sums + platform gradient sums + stats
+    float *gram = nullptr;          // count-weighted second moments of U1, U2 (J1^2 + J2^2)
+    // fold-in / top-k
+    float *wtable = nullptr;        // I2*I3*J1: w_jk = G x2 u2_j x3 u3_k
+    int64_t param_version = 0;      // bumped whenever G or a factor may have changed
+    int64_t wtable_version = -1;
+    float *fold_part = nullptr;     // scratch: per-CTA Gram partials of one query
+    int64_t fold_part_cap = 0;      // floats
+    int2 *q_jk = nullptr;           // staging for one query's cells
+    float *q_val = nullptr;
+    int64_t q_cap = 0;
+    float *q_u = nullptr;           // kMaxRank
+    int32_t *q_status = nullptr;
+    float *score = nullptr;         // I1
+    uint8_t *taken = nullptr;       // I1
+    int32_t *top_i = nullptr;       // 64
+    float *top_s = nullptr;         // 64
+    // loss
+    double *lacc = nullptr;         // 8 doubles
+    // CUDA graph of one epoch
+    cudaGraphExec_t epoch_exec = nullptr;
+    int64_t epoch_kernels = 0;      // kernels in one replay of the graph
+    // error word written by kernels (validation)
+    int32_t *flag = nullptr;
+};
+
+// error helpers ---------------------------------------------------------------------------
+int fail(Ctx *c, int code, const std::string &msg);
+#define SNECT_CUDA(c, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e__ = (call);                                                            \
+        if (e__ != cudaSuccess)                                                              \
+            return ::snect::fail((c), SNECT_ECUDA,                                           \
+                                 std::string(#call) + ": " + cudaGetErrorString(e__));       \
+    } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// launchers (each returns a CUDA error code; they increment c->launches) ------------------
+cudaError_t launch_det_grad(Ctx *c, int64_t first, int64_t len);
+cudaError_t launch_det_apply(Ctx *c, int64_t first, int64_t len);
+cudaError_t launch_edge_pass(Ctx *c);
+cudaError_t launch_loss(Ctx *c, const Rec *recs, int64_t n, int which);
+cudaError_t launch_loss_reg_graph(Ctx *c);
+
+// prep (prep.cu)
+int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val);
+int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w);
+int prep_det_groups(Ctx *c);
+int prep_fast_tiles(Ctx *c);
+int enqueue_fast_epoch(Ctx *c);
+void free_fast(Ctx *c);
+int det_scratch_floats(const Ctx *c, int64_t *gbuf_floats, int64_t *part_floats);
+cudaError_t det_init_attrs(Ctx *c);
+cudaError_t loss_init_attrs(Ctx *c);
+int pack_records(Ctx *c, const int32_t *d_idx, const float *d_val, int64_t n, Rec *out,
+                 bool check_ranges, int32_t n_modes);
+
+}  // namespace snect

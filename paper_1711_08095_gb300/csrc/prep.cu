@@ -1,0 +1,261 @@
+// Set-up work done once per problem on the GPU: validation and packing of the entries,
+// the training counts |Omega^{n,i}|, the per-batch row grouping of the deterministic mode,
+// and the sorted adjacency (CSR) of the gene network.
+#include <cub/cub.cuh>
+
+#include "common.cuh"
+
+namespace snect {
+
+namespace {
+
+enum : int32_t {
+    kBadIndex = 1,
+    kBadValue = 2,
+    kSelfLoop = 4,
+    kDupEdge = 8,
+    kBadWeight = 16,
+};
+
+__global__ void k_pack(const int32_t *__restrict__ idx, const float *__restrict__ val, int64_t n,
+                       int32_t n_modes, int32_t I1, int32_t I2, int32_t I3, Rec *__restrict__ out,
+                       int32_t *flag) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    Rec r;
+    r.i = idx[e * n_modes + 0];
+    r.j = idx[e * n_modes + 1];
+    r.k = n_modes == 3 ? idx[e * 3 + 2] : 0;
+    r.x = val[e];
+    bool bad = r.i < 0 || r.i >= I1 || r.j < 0 || r.j >= I2 || r.k < 0 || r.k >= I3;
+    if (bad) {
+        atomicOr(flag, kBadIndex);
+        r.i = r.j = r.k = 0;  // keep later kernels in bounds; the call reports the error
+    }
+    if (!isfinite(r.x)) atomicOr(flag, kBadValue);
+    out[e] = r;
+}
+
+__global__ void k_counts(const Rec *__restrict__ rec, int64_t n, int32_t *c1, int32_t *c2,
+                         int32_t *c3) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    Rec r = rec[e];
+    atomicAdd(c1 + r.i, 1);
+    atomicAdd(c2 + r.j, 1);
+    atomicAdd(c3 + r.k, 1);
+}
+
+// key = (batch << 32) | row of the given mode; value = entry position
+__global__ void k_group_keys(const Rec *__restrict__ rec, int64_t n, int32_t batch, int mode,
+                             uint64_t *keys, int32_t *vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    Rec r = rec[e];
+    uint32_t row = mode == 0 ? r.i : (mode == 1 ? r.j : r.k);
+    keys[e] = ((uint64_t)(e / batch) << 32) | row;
+    vals[e] = (int32_t)e;
+}
+
+__global__ void k_heads(const uint64_t *__restrict__ keys, int64_t n, uint8_t *head) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    head[s] = (s == 0 || keys[s] != keys[s - 1]) ? 1 : 0;
+}
+
+__global__ void k_half_edges(const int32_t *__restrict__ edges, const float *__restrict__ w,
+                             int64_t m, int32_t I2, uint64_t *keys, int32_t *vals, int2 *out_edges,
+                             float *out_w, int32_t *flag) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    int32_t u = edges[2 * t], v = edges[2 * t + 1];
+    float y = w[t];
+    if (u < 0 || u >= I2 || v < 0 || v >= I2) {
+        atomicOr(flag, kBadIndex);
+        u = 0;
+        v = 1;
+    }
+    if (u == v) atomicOr(flag, kSelfLoop);
+    if (!(y > 0.0f) || !isfinite(y)) atomicOr(flag, kBadWeight);
+    out_edges[t] = make_int2(u, v);
+    out_w[t] = y;
+    keys[2 * t] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)v;
+    vals[2 * t] = (int32_t)t;
+    keys[2 * t + 1] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)u;
+    vals[2 * t + 1] = (int32_t)t;
+}
+
+// ptr[k] = first sorted half-edge whose source is >= k; col/w from the sorted keys
+__global__ void k_csr(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                      int64_t n2, int32_t I2, const float *__restrict__ w, int32_t *ptr,
+                      int32_t *col, float *cw, int32_t *flag) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > n2) return;
+    if (s == n2) {  // tail: rows after the last source
+        int32_t last = n2 ? (int32_t)(keys[n2 - 1] >> 32) : -1;
+        for (int32_t k = last + 1; k <= I2; ++k) ptr[k] = (int32_t)n2;
+        return;
+    }
+    uint64_t key = keys[s];
+    int32_t src = (int32_t)(key >> 32);
+    col[s] = (int32_t)(key & 0xffffffffu);
+    cw[s] = w[vals[s]];
+    int32_t prev = s ? (int32_t)(keys[s - 1] >> 32) : -1;
+    if (s && keys[s - 1] == key) atomicOr(flag, kDupEdge);
+    for (int32_t k = prev + 1; k <= src; ++k) ptr[k] = (int32_t)s;
+}
+
+__global__ void k_max_degree(const int32_t *__restrict__ ptr, int32_t I2, int32_t *out) {
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= I2) return;
+    atomicMax(out, ptr[k + 1] - ptr[k]);
+}
+
+std::string flag_message(int32_t f) {
+    std::string s;
+    if (f & kBadIndex) s += " index out of range;";
+    if (f & kBadValue) s += " non-finite value;";
+    if (f & kSelfLoop) s += " self loop in the gene network;";
+    if (f & kDupEdge) s += " duplicate edge in the gene network;";
+    if (f & kBadWeight) s += " edge weight not finite and positive;";
+    return s;
+}
+
+int read_flag(Ctx *c, int32_t *out) {
+    SNECT_CUDA(c, cudaMemcpyAsync(out, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SNECT_OK;
+}
+
+// stable radix sort of (key, value) pairs; temporary buffers allocated here
+int sort_pairs(Ctx *c, uint64_t *keys, int32_t *vals, uint64_t *keys_out, int32_t *vals_out,
+               int64_t n, int end_bit) {
+    size_t tmp_bytes = 0;
+    SNECT_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys_out, vals, vals_out,
+                                                   n, 0, end_bit, c->stream));
+    void *tmp = nullptr;
+    SNECT_CUDA(c, cudaMallocAsync(&tmp, tmp_bytes, c->stream));
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys_out, vals, vals_out, n,
+                                                    0, end_bit, c->stream);
+    c->launches += 4;  // radix passes (an estimate; set-up only)
+    cudaFreeAsync(tmp, c->stream);
+    if (e != cudaSuccess) return fail(c, SNECT_ECUDA, std::string("radix sort: ") + cudaGetErrorString(e));
+    return SNECT_OK;
+}
+
+int bits_for(uint64_t v) {
+    int b = 1;
+    while (b < 64 && (v >> b)) ++b;
+    return b;
+}
+
+}  // namespace
+
+int pack_records(Ctx *c, const int32_t *d_idx, const float *d_val, int64_t n, Rec *out,
+                 bool check_ranges, int32_t n_modes) {
+    if (n == 0) return SNECT_OK;
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    int32_t I3 = n_modes == 3 ? c->d.I3 : 1;
+    k_pack<<<ceil_div(n, 256), 256, 0, c->stream>>>(d_idx, d_val, n, n_modes, c->d.I1, c->d.I2, I3,
+                                                     out, c->flag);
+    c->launches++;
+    SNECT_CUDA(c, cudaGetLastError());
+    if (check_ranges) {
+        int32_t f = 0;
+        int rc = read_flag(c, &f);
+        if (rc) return rc;
+        if (f) return fail(c, SNECT_EINVAL, "entries:" + flag_message(f));
+    }
+    return SNECT_OK;
+}
+
+int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val) {
+    int rc = pack_records(c, d_idx, d_val, c->nnz, c->rec, true, 3);
+    if (rc) return rc;
+    for (int md = 0; md < 3; ++md) {
+        int32_t In = md == 0 ? c->d.I1 : (md == 1 ? c->d.I2 : c->d.I3);
+        SNECT_CUDA(c, cudaMemsetAsync(c->cnt[md], 0, sizeof(int32_t) * In, c->stream));
+    }
+    if (c->nnz) {
+        k_counts<<<ceil_div(c->nnz, 256), 256, 0, c->stream>>>(c->rec, c->nnz, c->cnt[0], c->cnt[1],
+                                                               c->cnt[2]);
+        c->launches++;
+        SNECT_CUDA(c, cudaGetLastError());
+    }
+    return SNECT_OK;
+}
+
+int prep_det_groups(Ctx *c) {
+    int64_t n = c->nnz;
+    if (n == 0) return SNECT_OK;
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int32_t *vals = nullptr;
+    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * n, c->stream));
+    int rc = SNECT_OK;
+    int end_bit = 32 + bits_for((uint64_t)c->n_batches);
+    for (int md = 0; md < 3 && rc == SNECT_OK; ++md) {
+        k_group_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, c->cfg.batch, md, keys, vals);
+        c->launches++;
+        rc = sort_pairs(c, keys, vals, keys2, c->grp_pos[md], n, end_bit);
+        if (rc) break;
+        k_heads<<<ceil_div(n, 256), 256, 0, c->stream>>>(keys2, n, c->grp_head[md]);
+        c->launches++;
+    }
+    cudaFreeAsync(keys, c->stream);
+    cudaFreeAsync(keys2, c->stream);
+    cudaFreeAsync(vals, c->stream);
+    if (rc) return rc;
+    SNECT_CUDA(c, cudaGetLastError());
+    return SNECT_OK;
+}
+
+int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
+    int64_t m = c->m;
+    int32_t I2 = c->d.I2;
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    if (m == 0) {
+        SNECT_CUDA(c, cudaMemsetAsync(c->csr_ptr, 0, sizeof(int32_t) * (I2 + 1), c->stream));
+        c->max_degree = 0;
+        return SNECT_OK;
+    }
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int32_t *vals = nullptr, *vals2 = nullptr;
+    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * 2 * m, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * 2 * m, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * 2 * m, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&vals2, sizeof(int32_t) * 2 * m, c->stream));
+    k_half_edges<<<ceil_div(m, 256), 256, 0, c->stream>>>(d_edges, d_w, m, I2, keys, vals, c->edges,
+                                                          c->ew, c->flag);
+    c->launches++;
+    int rc = sort_pairs(c, keys, vals, keys2, vals2, 2 * m, 32 + bits_for((uint64_t)I2));
+    if (rc == SNECT_OK) {
+        k_csr<<<ceil_div(2 * m + 1, 256), 256, 0, c->stream>>>(keys2, vals2, 2 * m, I2, c->ew,
+                                                               c->csr_ptr, c->csr_col, c->csr_w,
+                                                               c->flag);
+        c->launches++;
+    }
+    int32_t *d_maxdeg = nullptr;
+    if (rc == SNECT_OK) {
+        // the flag word's neighbour holds the maximum degree
+        d_maxdeg = c->flag + 1;
+        cudaMemsetAsync(d_maxdeg, 0, sizeof(int32_t), c->stream);
+        k_max_degree<<<ceil_div(I2, 256), 256, 0, c->stream>>>(c->csr_ptr, I2, d_maxdeg);
+        c->launches++;
+    }
+    cudaFreeAsync(keys, c->stream);
+    cudaFreeAsync(keys2, c->stream);
+    cudaFreeAsync(vals, c->stream);
+    cudaFreeAsync(vals2, c->stream);
+    if (rc) return rc;
+    SNECT_CUDA(c, cudaGetLastError());
+    int32_t hf[2] = {0, 0};
+    SNECT_CUDA(c, cudaMemcpyAsync(hf, c->flag, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hf[0]) return fail(c, SNECT_EINVAL, "gene network:" + flag_message(hf[0]));
+    c->max_degree = hf[1];
+    return SNECT_OK;
+}
+
+}  // namespace snect

@@ -1,0 +1,261 @@
+// Fold-in of a new patient (Eq. 9) and top-k patient search (Sec. 3.2.1).
+//
+// Fold-in holds G, U2, U3 fixed and solves for the patient row u:
+//   min_u 1/2 sum_{(j,k) observed} (x_jk - u . w_jk)^2 + lambda/2 ||u||^2,
+//   w_jk = G x2 u2_j x3 u3_k  (length J1)
+// i.e. (sum w w^T + lambda I) u = sum x w.  The lambda/2 ||u||^2 term is what the per-entry
+// L2 terms of Sec. 2.3.2 add up to for one row.
+//   k_wtable         w_jk for every (gene, platform) pair once the factors are fixed
+//                    (I2*I3 rows of J1 floats; L2-resident at the paper's sizes);
+//   k_foldin_partial each CTA sums w w^T and x w over a fixed run of the query's cells, in
+//                    cell order (one thread per Gram element), into its own partial;
+//   k_foldin_solve   one CTA adds the partials in CTA order, adds lambda I, and solves by an
+//                    FP64 Cholesky factorisation.
+// The partition into CTAs depends only on the query's size, so the result of a query is the
+// same whether it runs alone or beside others.
+//
+// Top-k: cos(u, u1_i) for every patient row, then k rounds of a block-wide arg-max
+// (largest score, lower index on ties); a zero-norm row or query scores 0.
+#include "common.cuh"
+#include "serve.cuh"
+
+namespace snect {
+
+namespace {
+
+__global__ void k_wtable(const float *__restrict__ G, const float *__restrict__ U2,
+                         const float *__restrict__ U3, int32_t I2, int32_t I3, int32_t J1,
+                         int32_t J2, int32_t J3, float *__restrict__ table) {
+    extern __shared__ float sG[];
+    const int PI = J1 * J2 * J3;
+    for (int t = threadIdx.x; t < PI; t += blockDim.x) sG[t] = G[t];
+    __syncthreads();
+    const int64_t jk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= (int64_t)I2 * I3) return;
+    const int64_t j = jk / I3, k = jk % I3;
+    const float *b = U2 + j * J2;
+    const float *c = U3 + k * J3;
+    float cr[kMaxRank];
+    for (int r = 0; r < J3; ++r) cr[r] = c[r];
+    for (int p = 0; p < J1; ++p) {
+        float s = 0.f;
+        for (int q = 0; q < J2; ++q) {
+            float t = 0.f;
+            const float *g = sG + (p * J2 + q) * J3;
+            for (int r = 0; r < J3; ++r) t = fmaf(g[r], cr[r], t);
+            s = fmaf(t, b[q], s);
+        }
+        table[jk * J1 + p] = s;
+    }
+}
+
+// cells [blockIdx.x * chunk, ...) of one query; part: (J1*J1 + J1) floats per CTA
+__global__ void __launch_bounds__(kFoldThreads)
+    k_foldin_partial(const int2 *__restrict__ jk, const float *__restrict__ val, int64_t n,
+                     int64_t chunk, const float *__restrict__ table, int32_t I3, int32_t J1,
+                     float *__restrict__ part) {
+    __shared__ float sw[kFoldTile * kMaxRank];
+    __shared__ float sx[kFoldTile];
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = min(n, c0 + chunk);
+    const int nG = J1 * J1;
+    float acc[kFoldPerThread];
+#pragma unroll
+    for (int t = 0; t < kFoldPerThread; ++t) acc[t] = 0.f;
+    float accx = 0.f;
+    for (int64_t base = c0; base < c1; base += kFoldTile) {
+        const int len = (c1 - base) < kFoldTile ? (int)(c1 - base) : kFoldTile;
+        __syncthreads();
+        for (int t = threadIdx.x; t < len * J1; t += blockDim.x) {
+            const int e = t / J1, p = t % J1;
+            const int2 cell = jk[base + e];
+            sw[e * J1 + p] = table[((int64_t)cell.x * I3 + cell.y) * J1 + p];
+        }
+        for (int t = threadIdx.x; t < len; t += blockDim.x) sx[t] = val[base + t];
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kFoldPerThread; ++t) {
+            const int s = threadIdx.x + t * kFoldThreads;
+            if (s < nG) {
+                const int p = s / J1, q = s % J1;
+                float a = acc[t];
+                for (int e = 0; e < len; ++e) a = fmaf(sw[e * J1 + p], sw[e * J1 + q], a);
+                acc[t] = a;
+            }
+        }
+        if (threadIdx.x < J1) {
+            const int p = threadIdx.x;
+            for (int e = 0; e < len; ++e) accx = fmaf(sx[e], sw[e * J1 + p], accx);
+        }
+    }
+    float *out = part + (int64_t)blockIdx.x * (nG + J1);
+#pragma unroll
+    for (int t = 0; t < kFoldPerThread; ++t) {
+        const int s = threadIdx.x + t * kFoldThreads;
+        if (s < nG) out[s] = acc[t];
+    }
+    if (threadIdx.x < J1) out[nG + threadIdx.x] = accx;
+}
+
+__global__ void __launch_bounds__(kFoldThreads)
+    k_foldin_solve(const float *__restrict__ part, int32_t n_part, int32_t J1, float ridge,
+                   float *__restrict__ u_out, int32_t *__restrict__ status) {
+    __shared__ double M[kMaxRank * kMaxRank];
+    __shared__ double rhs[kMaxRank];
+    const int nG = J1 * J1;
+    for (int s = threadIdx.x; s < nG + J1; s += blockDim.x) {
+        float a = 0.f;
+        for (int t = 0; t < n_part; ++t) a += part[(int64_t)t * (nG + J1) + s];
+        if (s < nG) {
+            M[s] = (double)a + ((s / J1 == s % J1) ? (double)ridge : 0.0);
+        } else {
+            rhs[s - nG] = (double)a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // Cholesky M = L L^T (lower triangle, in place), then two triangular solves
+    for (int j = 0; j < J1; ++j) {
+        double d = M[j * J1 + j];
+        for (int k = 0; k < j; ++k) d -= M[j * J1 + k] * M[j * J1 + k];
+        if (!(d > 0.0)) {
+            *status = 1;
+            for (int p = 0; p < J1; ++p) u_out[p] = 0.f;
+            return;
+        }
+        d = sqrt(d);
+        M[j * J1 + j] = d;
+        for (int i = j + 1; i < J1; ++i) {
+            double s = M[i * J1 + j];
+            for (int k = 0; k < j; ++k) s -= M[i * J1 + k] * M[j * J1 + k];
+            M[i * J1 + j] = s / d;
+        }
+    }
+    for (int i = 0; i < J1; ++i) {
+        double s = rhs[i];
+        for (int k = 0; k < i; ++k) s -= M[i * J1 + k] * rhs[k];
+        rhs[i] = s / M[i * J1 + i];
+    }
+    for (int i = J1 - 1; i >= 0; --i) {
+        double s = rhs[i];
+        for (int k = i + 1; k < J1; ++k) s -= M[k * J1 + i] * rhs[k];
+        rhs[i] = s / M[i * J1 + i];
+    }
+    for (int p = 0; p < J1; ++p) u_out[p] = (float)rhs[p];
+    *status = 0;
+}
+
+__global__ void k_cosine(const float *__restrict__ U1, int32_t I1, int32_t J1,
+                         const float *__restrict__ u, float *__restrict__ score) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I1) return;
+    float nu = 0.f, d = 0.f, nr = 0.f;
+    for (int p = 0; p < J1; ++p) {
+        const float x = U1[(int64_t)i * J1 + p], y = u[p];
+        d = fmaf(x, y, d);
+        nr = fmaf(x, x, nr);
+        nu = fmaf(y, y, nu);
+    }
+    score[i] = (nr > 0.f && nu > 0.f) ? d / (sqrtf(nr) * sqrtf(nu)) : 0.f;
+}
+
+// one CTA: k rounds of (largest score, lowest index) over the unpicked rows
+__global__ void __launch_bounds__(1024)
+    k_topk(const float *__restrict__ score, int32_t I1, int32_t k, int32_t *__restrict__ idx_out,
+           float *__restrict__ score_out, uint8_t *__restrict__ taken) {
+    __shared__ float ws[32];
+    __shared__ int32_t wi[32];
+    for (int32_t i = threadIdx.x; i < I1; i += blockDim.x) taken[i] = 0;
+    __syncthreads();
+    for (int32_t round = 0; round < k; ++round) {
+        float bs = -INFINITY;
+        int32_t bi = INT32_MAX;
+        for (int32_t i = threadIdx.x; i < I1; i += blockDim.x) {
+            if (taken[i]) continue;
+            const float s = score[i];
+            if (s > bs || (s == bs && i < bi)) {
+                bs = s;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+            const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (os > bs || (os == bs && oi < bi)) {
+                bs = os;
+                bi = oi;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            ws[threadIdx.x >> 5] = bs;
+            wi[threadIdx.x >> 5] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float b = -INFINITY;
+            int32_t ix = INT32_MAX;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (ws[w] > b || (ws[w] == b && wi[w] < ix)) {
+                    b = ws[w];
+                    ix = wi[w];
+                }
+            idx_out[round] = ix;
+            score_out[round] = b;
+            taken[ix] = 1;
+        }
+        __syncthreads();
+    }
+}
+
+// validates a query's cells in place: out-of-range cells become (0, 0) and set the flag
+__global__ void k_check_cells(int2 *__restrict__ jk, const float *__restrict__ val, int64_t n,
+                              int32_t I2, int32_t I3, int32_t *flag) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int2 c = jk[e];
+    if (c.x < 0 || c.x >= I2 || c.y < 0 || c.y >= I3) {
+        jk[e] = make_int2(0, 0);
+        atomicOr(flag, 1);
+    }
+    if (!isfinite(val[e])) atomicOr(flag, 2);
+}
+
+}  // namespace
+
+cudaError_t launch_check_cells(Ctx *c, cudaStream_t st, int2 *jk, const float *val, int64_t n,
+                               int32_t *flag) {
+    k_check_cells<<<ceil_div(n, 256), 256, 0, st>>>(jk, val, n, c->d.I2, c->d.I3, flag);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+int64_t foldin_parts(int64_t n) { return std::max<int64_t>(1, ceil_div(n, kFoldChunk)); }
+
+cudaError_t launch_wtable(Ctx *c, float *table) {
+    const int64_t rows = (int64_t)c->d.I2 * c->d.I3;
+    k_wtable<<<ceil_div(rows, 128), 128, sizeof(float) * c->PI, c->stream>>>(
+        c->G, c->U[1], c->U[2], c->d.I2, c->d.I3, c->d.J1, c->d.J2, c->d.J3, table);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_foldin(Ctx *c, cudaStream_t st, const int2 *jk, const float *val, int64_t n,
+                          const float *table, float *part, float *u_out, int32_t *status) {
+    const int64_t np = foldin_parts(n);
+    k_foldin_partial<<<(unsigned)np, kFoldThreads, 0, st>>>(jk, val, n, kFoldChunk, table, c->d.I3,
+                                                            c->d.J1, part);
+    k_foldin_solve<<<1, kFoldThreads, 0, st>>>(part, (int32_t)np, c->d.J1, c->cfg.lambda, u_out, status);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk(Ctx *c, cudaStream_t st, const float *u, int32_t k, float *score,
+                        uint8_t *taken, int32_t *idx_out, float *score_out) {
+    k_cosine<<<ceil_div(c->d.I1, 256), 256, 0, st>>>(c->U[0], c->d.I1, c->d.J1, u, score);
+    k_topk<<<1, 1024, 0, st>>>(score, c->d.I1, k, idx_out, score_out, taken);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace snect
