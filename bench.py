@@ -1,0 +1,307 @@
+"""Benchmark of the SNeCT sweep on GB300.
+
+Workload (one step = one epoch of Alg. 1: the fast entry sweep over every training entry
+plus the network pass): the paper-scale problem -- 4,500 patients x 15,000 genes x 5
+platforms, 30M observed cells (27M train / 3M test), planted Tucker values with core
+10 x 10 x 5 plus N(0, 0.1^2) noise, a 300,000-edge power-law gene network, FP32, core ranks
+10 x 10 x 5.  Synthetic data: the PanCan12 tensor and the PathwayCommons network are not
+available.
+
+Metric: nnz-updates/s per epoch (training entries x epochs / seconds), higher is better.
+`value` times K epochs with every input resident in HBM (CUDA events on the library's
+stream); `e2e` times whole training jobs through the public C ABI from pinned host buffers
+(host->device copy of the problem, set-up, 10 epochs, objective read back).
+
+`--impl reference` times the FP64 CPU oracle (sequential Alg. 1 with one worker) on a
+bounded sample of the same workload on the host cores.
+
+Multi-GPU (`torchrun --nproc-per-node N`): the decomposition of one tensor is not sharded
+here, so each rank runs an independent replica (weak scaling, no collective on the data
+path); `value` sums the ranks' updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nnz-updates/s per epoch"
+UNIT = "nnz-updates/s"
+WORKLOAD = dict(
+    workload="paper-scale SNeCT sweep: 4500x15000x5 tensor, 30M observed (27M train), "
+             "core 10x10x5, 300k-edge power-law gene network, FP32 fast mode",
+    I=[4500, 15000, 5], J=[10, 10, 5], nnz_train=27_000_000, edges=300_000, lam=0.01, lam_g=0.1, lr=0.01,
+)
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="a small problem of the same shape (for profiling)")
+    return ap.parse_args()
+
+
+def make_problem(small=False):
+    import snect_synth as S
+
+    if small:
+        return S.config2(n_patients=1500, nnz=6_000_000, n_edges=100_000)
+    return S.config2()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+
+        def find(keys):
+            for k in keys:
+                for kk, v in d.items():
+                    if kk.lower() == k and isinstance(v, (int, float)):
+                        return float(v)
+            return None
+
+        hbm = find(["hbm_gbs", "hbm_gb_s", "copy_gbs"])
+        if hbm:
+            return hbm, "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.gpu = gpu_index
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n):
+    import torch
+
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, world, dist
+
+
+def cpu_baseline(p, budget_s=15.0):
+    """The FP64 oracle's sequential epoch (Alg. 1, one worker) on the first entries of the
+    workload, sized to about budget_s seconds of one host core; nnz-updates/s."""
+    import oracle
+
+    P = oracle.Params(p.G0, p.U0)
+    n = 20_000
+    t0 = time.perf_counter()
+    oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx[:n], p.val[:n], p.edges[:0], p.w[:0])
+    dt = time.perf_counter() - t0
+    n2 = int(min(p.nnz, max(n, budget_s / max(dt, 1e-9) * n)))
+    P = oracle.Params(p.G0, p.U0)
+    t0 = time.perf_counter()
+    oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx[:n2], p.val[:n2], p.edges[:0], p.w[:0])
+    dt = time.perf_counter() - t0
+    return {"value": n2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, sequential per-entry epoch over the first %d training entries of the "
+                      "workload (%.1f s on one host core; the network pass excluded)" % (n2, dt),
+            "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = make_problem(args.small)
+    import oracle
+
+    oracle.build()
+    n = 400_000  # entries per step: a bounded sample of the workload's epoch
+    P = oracle.Params(p.G0, p.U0)
+    for _ in range(max(1, min(args.warmup, 1))):
+        oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx[:n], p.val[:n], p.edges[:0], p.w[:0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx[:n], p.val[:n], p.edges[:0], p.w[:0])
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": dict(WORKLOAD, sample_entries_per_step=n),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "sequential FP64 oracle epoch over the first %d training entries per step" % n},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_1711_08095_gb300 as snect
+
+    rank, world, dist = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    snect.load(build_if_missing=True)
+    p = make_problem(args.small)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    # ---- resident inputs: device tensors -> context; K timed epochs ----------------------
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ctx = snect.Snect(p.I, p.J, t(p.idx), t(p.val), t(p.edges), t(p.w), t(p.G0), [t(u) for u in p.U0], lam=p.lam,
+                      lam_g=p.lam_g, lr=p.lr, batch=0)
+    for _ in range(args.warmup):
+        ctx.epoch(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = ctx.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.epoch(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.launches - l0
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    sweep_ms, sweep_n = ctx.sweep_times()  # sweep kernels of the last timed epoch
+    loss = ctx.loss(t(p.test_idx), t(p.test_val))
+    ctx.close()
+    del ctx
+    torch.cuda.synchronize()
+    value = p.nnz * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the C ABI from pinned host buffers ---------------------------
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    h = dict(idx=pin(p.idx), val=pin(p.val), edges=pin(p.edges), w=pin(p.w), G0=pin(p.G0),
+             U0=[pin(u) for u in p.U0], tidx=pin(p.test_idx), tval=pin(p.test_val))
+    h2d = sum(x.numel() * x.element_size() for x in [h["idx"], h["val"], h["edges"], h["w"], h["G0"], *h["U0"],
+                                                      h["tidx"], h["tval"]])
+    d2h = 6 * 8 + sum(int(np.prod(u.shape)) * 4 for u in p.U0) + int(np.prod(p.G0.shape)) * 4
+    job_epochs = 10
+    e2e_times = []
+    for _ in range(args.e2e_jobs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = snect.Snect(p.I, p.J, h["idx"], h["val"], h["edges"], h["w"], h["G0"], h["U0"], lam=p.lam,
+                        lam_g=p.lam_g, lr=p.lr, batch=0)
+        c.epoch(job_epochs)
+        job_loss = c.loss(h["tidx"], h["tval"])
+        c.get_factors()
+        e2e_times.append(time.perf_counter() - t0)
+        c.close()
+    e2e_s = statistics.median(e2e_times)
+
+    pk, pk_kind = peaks()
+    # roofline of the sweep kernel: algorithmic bytes per entry = 16 (entry record) +
+    # 4*(J1+J2+J3) gathered rows + 4*(J1+J2+J3) row write-back, per launch = one wave
+    J = p.J
+    bytes_per_nnz = 16 + 8 * sum(J)
+    achieved = (bytes_per_nnz * p.nnz / sweep_n) / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism="replicas x%d" % world if world > 1 else "single GPU",
+                       l2="inputs larger than L2: 432 MB of entry records streamed per epoch",
+                       small=bool(args.small)),
+        "e2e": {"value": p.nnz * job_epochs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "step": "one training job: snect_init from pinned host buffers, %d epochs, objective and "
+                        "factors read back (median of %d jobs, %.1f ms)" % (job_epochs, len(e2e_times), e2e_s * 1e3)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+                     "frac": (achieved / pk) if achieved else None, "traffic": None,
+                     "kernel": "k_fast_sweep (one launch per wave)",
+                     "bytes_per_unit": bytes_per_nnz, "units_per_launch": p.nnz / max(sweep_n, 1),
+                     "peak_kind": pk_kind,
+                     "timing": "CUDA events around each sweep launch inside the last timed epoch (%d launches, "
+                               "%.3f ms)" % (sweep_n, sweep_ms)},
+        "clocks": clk.summary(),
+        "quality": {"rmse_test_after_warmup_and_steps": loss["rmse_test"], "rmse_train": loss["rmse_train"],
+                    "epochs_run": args.warmup + args.steps, "e2e_job_rmse_test": job_loss["rmse_test"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -19,8 +19,8 @@
  *   - The core G is J1*J2*J3 floats, g(p,q,r) at (p*J2 + q)*J3 + r; factor U_n is I_n*J_n
  *     floats, row-major.
  *   - All device work runs on the stream given at snect_init (the caller's stream, e.g.
- *     PyTorch's current stream), or on a stream the context creates if that is NULL.  Calls
- *     that return results on the host synchronise that stream.
+ *     PyTorch's current stream; NULL means the default stream).  Calls that return results on
+ *     the host synchronise that stream.
  *   - A context is not thread-safe: one host thread at a time.
  */
 #ifndef SNECT_H
@@ -78,7 +78,7 @@ typedef struct {
  *   edges any, m*2 int32 undirected gene pairs, each edge once, no self loops
  *   w     any, m float edge weights y > 0
  *   G0, U1, U2, U3  any, initial core and factors (layouts above)
- *   stream  a cudaStream_t, or NULL
+ *   stream  a cudaStream_t, or NULL for the default stream
  * Validates ranges (indices, sizes, finite values, self loops); computes the counts
  * |Omega^{n,i}| and the per-batch row grouping on the GPU.  On failure *out is NULL. */
 int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, const float *val,
@@ -121,6 +121,12 @@ int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n,
  * (J1 floats, any), descending, ties to the lower row index, a zero-norm row scores 0.
  * idx_out (int32) / score_out (float): any, k each.  1 <= k <= min(I1, 64).  Synchronises. */
 int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, float *score_out);
+
+/* Device time of the entry-sweep kernels of the most recent epoch (fast mode: one launch per
+ * wave), measured with CUDA events recorded on the context's stream immediately before and
+ * after each launch.  *ms_total = summed milliseconds, *n_launches = launches timed.
+ * Deterministic mode reports the gradient kernels of its batches.  Synchronises. */
+int snect_sweep_times(snect_ctx *ctx, double *ms_total, int64_t *n_launches);
 
 /* Number of kernel launches the context has issued so far (for launch accounting). */
 int64_t snect_launch_count(const snect_ctx *ctx);

@@ -169,6 +169,20 @@ def epoch(I, params: Params, lam, lam_g, lr, batch, idx, val, edges, w):
                      ep, wp, ctypes.c_int64(edges.shape[0]))
 
 
+def sgd_epoch(I, params: Params, lam, lam_g, lr, idx, val, edges, w):
+    """One sequential per-entry SGD epoch (Alg. 1 with one worker), then one network pass."""
+    lib = _load()
+    I, Ip = _i32(I)
+    J, Jp = _i32(params.J)
+    idx, ip = _i32(idx)
+    val, vp = _f64(val)
+    edges, ep = _i32(edges.reshape(-1, 2) if len(edges) else np.zeros((0, 2), np.int32))
+    w, wp = _f64(w)
+    lib.oracle_sgd_epoch(Ip, Jp, ctypes.c_double(lam), ctypes.c_double(lam_g), ctypes.c_double(lr),
+                         params.G.ctypes.data_as(_f64p), *(u.ctypes.data_as(_f64p) for u in params.U), ip, vp,
+                         ctypes.c_int64(idx.shape[0]), ep, wp, ctypes.c_int64(edges.shape[0]))
+
+
 def foldin(G, U2, U3, jk, x, ridge):
     """Closed-form fold-in of one new patient row (Eq. 9 with ridge term)."""
     lib = _load()

@@ -281,6 +281,37 @@ void oracle_epoch(const int32_t *I, const int32_t *J, double lambda, double lamb
     for (int md = 0; md < 3; ++md) free(cnt[md]);
 }
 
+/* Sequential per-entry SGD epoch: Alg. 1 with one worker (P = 1).  Each entry's gradient is
+ * evaluated at the current parameters and applied at once (the same step as a mini-batch of
+ * one entry, without copying the factor matrices), then one network-term pass (R4). */
+void oracle_sgd_epoch(const int32_t *I, const int32_t *J, double lambda, double lambda_g, double lr,
+                      double *G, double *U1, double *U2, double *U3, const int32_t *idx,
+                      const double *val, int64_t n, const int32_t *edges, const double *w,
+                      int64_t m) {
+    int64_t *cnt[3];
+    for (int md = 0; md < 3; ++md) cnt[md] = (int64_t *)malloc(sizeof(int64_t) * ((size_t)I[md] + 1));
+    oracle_counts(I, idx, n, cnt[0], cnt[1], cnt[2]);
+    int64_t PI = (int64_t)J[0] * J[1] * J[2];
+    double *gG = (double *)malloc(sizeof(double) * PI);
+    double ga[64], gb[64], gc[64];
+    for (int64_t e = 0; e < n; ++e) {
+        const int32_t *t = idx + 3 * e;
+        double *a = U1 + (int64_t)t[0] * J[0];
+        double *b = U2 + (int64_t)t[1] * J[1];
+        double *c = U3 + (int64_t)t[2] * J[2];
+        entry_grads(J, G, a, b, c, val[e], lambda / (double)cnt[0][t[0]],
+                    lambda / (double)cnt[1][t[1]], lambda / (double)cnt[2][t[2]],
+                    lambda / (double)n, ga, gb, gc, gG);
+        for (int q = 0; q < J[0]; ++q) a[q] -= lr * ga[q];
+        for (int q = 0; q < J[1]; ++q) b[q] -= lr * gb[q];
+        for (int q = 0; q < J[2]; ++q) c[q] -= lr * gc[q];
+        for (int64_t s = 0; s < PI; ++s) G[s] -= lr * gG[s];
+    }
+    oracle_edge_pass(I[1], J[1], lambda_g, lr, U2, edges, w, m);
+    free(gG);
+    for (int md = 0; md < 3; ++md) free(cnt[md]);
+}
+
 /* In-place Cholesky factorisation of the SPD matrix A (n x n, row-major) into its lower
  * factor L (A = L L^T), then solves A x = b.  Returns 0, or -1 if A is not positive definite. */
 static int cholesky_solve(int n, double *A, double *b) {

@@ -35,6 +35,7 @@ EXPORTS = (
     "snect_set_factors",
     "snect_foldin",
     "snect_topk",
+    "snect_sweep_times",
     "snect_launch_count",
     "snect_last_error",
     "snect_destroy",
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = False):
         "snect_set_factors": (ctypes.c_int, [P, P, P, P, P]),
         "snect_foldin": (ctypes.c_int, [P, P, P, i64, P]),
         "snect_topk": (ctypes.c_int, [P, P, i32, P, P]),
+        "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
         "snect_last_error": (ctypes.c_char_p, [P]),
         "snect_destroy": (None, [P]),
@@ -240,6 +242,13 @@ class Snect:
         self._check(self._lib.snect_topk(self._h, _ptr(u, keep, np.float32), int(k), idx.ctypes.data,
                                          sc.ctypes.data))
         return idx, sc
+
+    def sweep_times(self):
+        """(summed ms, launches) of the sweep kernels of the most recent epoch."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     @property
     def launches(self) -> int:

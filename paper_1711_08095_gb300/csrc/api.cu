@@ -52,6 +52,10 @@ int copy_in(Ctx *c, float *dst, const float *src, int64_t count) {
 void free_all(Ctx *c) {
     if (c->epoch_exec) cudaGraphExecDestroy(c->epoch_exec);
     c->epoch_exec = nullptr;
+    for (auto e : c->ev_begin) cudaEventDestroy(e);
+    for (auto e : c->ev_end) cudaEventDestroy(e);
+    c->ev_begin.clear();
+    c->ev_end.clear();
     free_fast(c);
     dfree(c->rec);
     for (int m = 0; m < 3; ++m) {
@@ -66,6 +70,7 @@ void free_all(Ctx *c) {
     dfree(c->csr_ptr);
     dfree(c->csr_col);
     dfree(c->csr_w);
+    dfree(c->heavy_rows);
     dfree(c->snap);
     dfree(c->gbuf);
     dfree(c->part);
@@ -104,7 +109,9 @@ int enqueue_det_epoch(Ctx *c) {
     const int64_t B = c->cfg.batch;
     for (int64_t b = 0; b < c->n_batches; ++b) {
         const int64_t first = b * B, len = std::min<int64_t>(B, c->nnz - first);
+        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[b], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_det_grad(c, first, len));
+        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[b], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_det_apply(c, first, len));
     }
     return SNECT_OK;
@@ -176,6 +183,17 @@ int ensure_wtable(Ctx *c) {
 
 }  // namespace
 
+int timing_events(Ctx *c, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        SNECT_CUDA(c, cudaEventCreate(&a));
+        c->ev_begin.push_back(a);
+        SNECT_CUDA(c, cudaEventCreate(&b));
+        c->ev_end.push_back(b);
+    }
+    return SNECT_OK;
+}
+
 int fail(Ctx *c, int code, const std::string &msg) {
     if (c)
         c->err = msg;
@@ -213,22 +231,13 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
     int rc = SNECT_OK;
     auto bail = [&](int code) {
         std::string msg = c->err;
-        if (c->stream) cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(c->stream);
         free_all(c);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return fail(nullptr, code, msg);
     };
-    if (stream) {
-        c->stream = (cudaStream_t)stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            c->err = "cudaStreamCreate failed";
-            c->stream = nullptr;
-            return bail(SNECT_ECUDA);
-        }
-        c->own_stream = true;
-    }
+    c->stream = (cudaStream_t)stream;  // NULL: the default stream
     const Dims &d = c->d;
     if ((rc = dmalloc(c, &c->rec, nnz)) || (rc = dmalloc(c, &c->cnt[0], d.I1)) ||
         (rc = dmalloc(c, &c->cnt[1], d.I2)) || (rc = dmalloc(c, &c->cnt[2], d.I3)) ||
@@ -269,14 +278,14 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
             (rc = dmalloc(c, &c->grp_head[1], nnz)) || (rc = dmalloc(c, &c->grp_head[2], nnz)) ||
             (rc = dmalloc(c, &c->gbuf, gf)) || (rc = dmalloc(c, &c->part, pf)))
             return bail(rc);
-        if ((rc = prep_det_groups(c))) return bail(rc);
+        if ((rc = prep_det_groups(c)) || (rc = timing_events(c, c->n_batches))) return bail(rc);
         cudaError_t e = det_init_attrs(c);
         if (e != cudaSuccess) {
             c->err = std::string("kernel attributes: ") + cudaGetErrorString(e);
             return bail(SNECT_ECUDA);
         }
     } else {
-        if ((rc = prep_fast_tiles(c))) return bail(rc);
+        if ((rc = prep_fast_tiles(c)) || (rc = init_fast(c))) return bail(rc);
     }
     cudaError_t e = loss_init_attrs(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -443,6 +452,22 @@ int snect_topk(snect_ctx *h, const float *u, int32_t k, int32_t *idx_out, float 
     return SNECT_OK;
 }
 
+int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !ms_total || !n_launches) return SNECT_EINVAL;
+    *ms_total = 0.0;
+    *n_launches = 0;
+    if (!c->epoch_exec) return SNECT_OK;  // no epoch has run yet
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < c->ev_begin.size(); ++i) {
+        float ms = 0.f;
+        SNECT_CUDA(c, cudaEventElapsedTime(&ms, c->ev_begin[i], c->ev_end[i]));
+        *ms_total += ms;
+        ++*n_launches;
+    }
+    return SNECT_OK;
+}
+
 int64_t snect_launch_count(const snect_ctx *h) {
     const Ctx *c = reinterpret_cast<const Ctx *>(h);
     return c ? c->launches : 0;
@@ -456,7 +481,7 @@ const char *snect_last_error(const snect_ctx *h) {
 void snect_destroy(snect_ctx *h) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     free_all(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/snect.h"
 
@@ -14,6 +15,7 @@ constexpr int kMaxRank = 32;      // largest J_n
 constexpr int kMaxCore = 5120;    // largest J1*J2*J3
 constexpr int kMaxBatch = 4096;   // largest deterministic mini-batch
 constexpr int kMaxPlatforms = 64; // largest I3 in fast mode (platform rows are dense there)
+constexpr int kHeavyDegree = 128;  // network rows above this degree take the chunked pass
 
 // One observed entry, 16 bytes: (i, j, k) and the value's bits.  One vector load per entry.
 struct __align__(16) Rec {
@@ -50,6 +52,8 @@ struct Ctx {
     float *csr_w = nullptr;      // 2m weights
     float *snap = nullptr;       // I2*J2 snapshot for the network pass
     int32_t max_degree = 0;
+    int32_t *heavy_rows = nullptr;  // genes of degree > kHeavyDegree (one CTA each in the pass)
+    int64_t n_heavy = 0;
     // deterministic mode
     int64_t n_batches = 0;
     int32_t *grp_pos[3] = {};    // per mode: entry positions grouped by (batch, row), stable
@@ -59,14 +63,20 @@ struct Ctx {
     int32_t grad_blocks = 0;     // CTAs of the gradient kernel per full batch
     // fast mode
     int64_t n_waves = 0;
-    int64_t wave = 0;
+    int64_t wave = 0;               // entries per wave
+    int64_t n_tiles = 0;
     int32_t *tile_start = nullptr;  // per tile: first entry (entries grouped by platform per wave)
     int32_t *tile_len = nullptr;
     int32_t *tile_k = nullptr;
-    int64_t *wave_tile = nullptr;   // host: first tile of each wave (n_waves + 1)
-    int64_t n_tiles = 0;
-    float *dense_acc = nullptr;     // per wave: core gradient sums + platform gradient sums + stats
-    float *gram = nullptr;          // count-weighted second moments of U1, U2 (J1^2 + J2^2)
+    int32_t *tile_ctr = nullptr;    // per wave: tiles claimed so far
+    std::vector<int64_t> wave_tile; // first tile of each wave (n_waves + 1)
+    std::vector<int64_t> wave_len;  // entries of each wave
+    float *wave_nk = nullptr;       // per wave and platform: entries (n_waves * I3)
+    float *macc = nullptr;          // per platform: sum over the wave of r a b^T (I3 * J1 * J2)
+    float *gram = nullptr;          // moments of U1, U2 (two buffers of gram_stride) + eigenvectors
+    int64_t gram_stride = 0;
+    int32_t fast_grid = 0;          // persistent CTAs of the wave kernel (occupancy)
+    float *gacc[2] = {};            // per patient / gene row: gradient sums and curvature (J_n + 1)
     // fold-in / top-k
     float *wtable = nullptr;        // I2*I3*J1: w_jk = G x2 u2_j x3 u3_k
     int64_t param_version = 0;      // bumped whenever G or a factor may have changed
@@ -87,6 +97,8 @@ struct Ctx {
     // CUDA graph of one epoch
     cudaGraphExec_t epoch_exec = nullptr;
     int64_t epoch_kernels = 0;      // kernels in one replay of the graph
+    // events around the sweep launches of one epoch (recorded inside the epoch graph)
+    std::vector<cudaEvent_t> ev_begin, ev_end;
     // error word written by kernels (validation)
     int32_t *flag = nullptr;
 };
@@ -114,12 +126,17 @@ cudaError_t launch_loss_reg_graph(Ctx *c);
 int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val);
 int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w);
 int prep_det_groups(Ctx *c);
-int prep_fast_tiles(Ctx *c);
+int prep_fast_tiles(Ctx *c);       // prep.cu: groups each wave's entries by platform, tiles
+int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of the fast sweep
 int enqueue_fast_epoch(Ctx *c);
 void free_fast(Ctx *c);
+constexpr int kFastTile = 256;     // entries per tile (one per thread of the wave kernel)
+constexpr int64_t kMinWave = 4096;      // default wave: nnz/64 clamped to [kMinWave, kMaxWave]
+constexpr int64_t kMaxWave = 1 << 20;
 int det_scratch_floats(const Ctx *c, int64_t *gbuf_floats, int64_t *part_floats);
 cudaError_t det_init_attrs(Ctx *c);
 cudaError_t loss_init_attrs(Ctx *c);
+int timing_events(Ctx *c, int64_t n);  // makes n begin/end event pairs
 int pack_records(Ctx *c, const int32_t *d_idx, const float *d_val, int64_t n, Rec *out,
                  bool check_ranges, int32_t n_modes);
 

@@ -57,6 +57,30 @@ __device__ __forceinline__ float contract_entry(const float *__restrict__ G, int
     return xt;
 }
 
+// x~ alone (Eq. 2 entrywise): sum_p a_p sum_q b_q sum_r g_pqr c_r.
+template <int CJ1, int CJ2, int CJ3>
+__device__ __forceinline__ float predict_entry(const float *__restrict__ G, int J1r, int J2r, int J3r,
+                                               const float *a, const float *b, const float *c) {
+    const int J1 = CJ1 ? CJ1 : J1r;
+    const int J2 = CJ2 ? CJ2 : J2r;
+    const int J3 = CJ3 ? CJ3 : J3r;
+    float xt = 0.f;
+#pragma unroll
+    for (int p = 0; p < J1; ++p) {
+        float vp = 0.f;
+#pragma unroll
+        for (int q = 0; q < J2; ++q) {
+            const float *g = G + (p * J2 + q) * J3;
+            float t = 0.f;
+#pragma unroll
+            for (int r = 0; r < J3; ++r) t = fmaf(g[r], c[r], t);
+            vp = fmaf(t, b[q], vp);
+        }
+        xt = fmaf(a[p], vp, xt);
+    }
+    return xt;
+}
+
 // Supported compile-time shapes; anything else runs the runtime-rank instantiation.
 #define SNECT_DISPATCH_RANKS(J1, J2, J3, FN, ...)                                      \
     (((J1) == 5 && (J2) == 5 && (J3) == 2)      ? FN<5, 5, 2>(__VA_ARGS__)            \

@@ -35,11 +35,12 @@ __global__ void __launch_bounds__(256)
     for (int t = threadIdx.x; t < PI; t += blockDim.x) sG[t] = Gg[t];
     __syncthreads();
     double local = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    // one entry per thread: a grid-stride loop would let the compiler keep all of G in
+    // registers across iterations
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) {
         const Rec r = rec[e];
         float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value], c[RankCap<CJ3>::value];
-        float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value], w3[RankCap<CJ3>::value];
 #pragma unroll
         for (int p = 0; p < J1; ++p)
             a[p] = U1[(int64_t)r.i * J1 + p];
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int s = 0; s < J3; ++s)
             c[s] = U3[(int64_t)r.k * J3 + s];
-        const float xt = contract_entry<CJ1, CJ2, CJ3>(sG, J1, J2, J3, a, b, c, v, w2, w3);
+        const float xt = predict_entry<CJ1, CJ2, CJ3>(sG, J1, J2, J3, a, b, c);
         const double res = (double)r.x - (double)xt;
         local += res * res;
     }
@@ -111,7 +112,7 @@ int loss_grid(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(ceil_
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_loss(Ctx *c, const Rec *recs, int64_t n, int which) {
     const size_t smem = sizeof(float) * c->PI;
-    k_loss_entries<CJ1, CJ2, CJ3><<<loss_grid(n), 256, smem, c->stream>>>(
+    k_loss_entries<CJ1, CJ2, CJ3><<<ceil_div(n, 256), 256, smem, c->stream>>>(
         recs, n, c->d, c->G, c->U[0], c->U[1], c->U[2], c->lacc + which);
     c->launches++;
     return cudaGetLastError();

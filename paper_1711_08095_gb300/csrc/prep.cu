@@ -3,6 +3,8 @@
 // and the sorted adjacency (CSR) of the gene network.
 #include <cub/cub.cuh>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace snect {
@@ -109,6 +111,29 @@ __global__ void k_max_degree(const int32_t *__restrict__ ptr, int32_t I2, int32_
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= I2) return;
     atomicMax(out, ptr[k + 1] - ptr[k]);
+}
+
+// key = (wave << 32) | platform; value = entry position (fast mode grouping)
+__global__ void k_wave_keys(const Rec *__restrict__ rec, int64_t n, int64_t wave, uint64_t *keys,
+                            int32_t *vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    keys[e] = ((uint64_t)(e / wave) << 32) | (uint32_t)rec[e].k;
+    vals[e] = (int32_t)e;
+}
+
+__global__ void k_permute(const Rec *__restrict__ src, const int32_t *__restrict__ perm, int64_t n,
+                          Rec *__restrict__ dst) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    dst[e] = src[perm[e]];
+}
+
+__global__ void k_wave_hist(const Rec *__restrict__ rec, int64_t n, int64_t wave, int32_t I3,
+                            int32_t *hist) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    atomicAdd(hist + (e / wave) * I3 + rec[e].k, 1);
 }
 
 std::string flag_message(int32_t f) {
@@ -255,6 +280,99 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
     if (hf[0]) return fail(c, SNECT_EINVAL, "gene network:" + flag_message(hf[0]));
     c->max_degree = hf[1];
+    if (c->max_degree > kHeavyDegree) {  // hub rows for the chunked network pass
+        std::vector<int32_t> ptr((size_t)I2 + 1), heavy;
+        SNECT_CUDA(c, cudaMemcpy(ptr.data(), c->csr_ptr, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+        for (int32_t k = 0; k < I2; ++k)
+            if (ptr[k + 1] - ptr[k] > kHeavyDegree) heavy.push_back(k);
+        c->n_heavy = (int64_t)heavy.size();
+        SNECT_CUDA(c, cudaMalloc((void **)&c->heavy_rows, sizeof(int32_t) * heavy.size()));
+        SNECT_CUDA(c, cudaMemcpy(c->heavy_rows, heavy.data(), sizeof(int32_t) * heavy.size(),
+                                 cudaMemcpyHostToDevice));
+    }
+    return SNECT_OK;
+}
+
+// Fast mode: the visit order is cut into waves of c->wave entries; inside a wave the entries
+// are stably grouped by platform (so one tile of kFastTile entries holds one platform) and
+// each platform segment is cut into tiles.
+int prep_fast_tiles(Ctx *c) {
+    const int64_t n = c->nnz;
+    const int32_t I3 = c->d.I3;
+    int64_t W = c->cfg.wave > 0 ? c->cfg.wave : std::min<int64_t>(kMaxWave, std::max<int64_t>(kMinWave, (n + 63) / 64));
+    if (n) {  // an even number of waves (>= 2), so the moment buffers alternate across epochs
+        int64_t nw = (n + W - 1) / W;
+        nw = std::max<int64_t>(2, (nw + 1) & ~(int64_t)1);
+        W = (n + nw - 1) / nw;
+        c->n_waves = nw;
+    } else {
+        c->n_waves = 0;
+    }
+    c->wave = W;
+    c->wave_tile.assign(1, 0);
+    c->wave_len.clear();
+    if (n == 0) return SNECT_OK;
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int32_t *vals = nullptr, *vals2 = nullptr, *hist = nullptr;
+    Rec *tmp = nullptr;
+    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&vals2, sizeof(int32_t) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&tmp, sizeof(Rec) * n, c->stream));
+    SNECT_CUDA(c, cudaMallocAsync(&hist, sizeof(int32_t) * c->n_waves * I3, c->stream));
+    k_wave_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, keys, vals);
+    c->launches++;
+    int rc = sort_pairs(c, keys, vals, keys2, vals2, n, 32 + bits_for((uint64_t)c->n_waves));
+    if (rc == SNECT_OK) {
+        k_permute<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, vals2, n, tmp);
+        cudaMemcpyAsync(c->rec, tmp, sizeof(Rec) * n, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemsetAsync(hist, 0, sizeof(int32_t) * c->n_waves * I3, c->stream);
+        k_wave_hist<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, I3, hist);
+        c->launches += 2;
+    }
+    std::vector<int32_t> h((size_t)c->n_waves * I3);
+    if (rc == SNECT_OK) {
+        cudaError_t e = cudaMemcpyAsync(h.data(), hist, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, std::string("wave histogram: ") + cudaGetErrorString(e));
+    }
+    cudaFreeAsync(keys, c->stream);
+    cudaFreeAsync(keys2, c->stream);
+    cudaFreeAsync(vals, c->stream);
+    cudaFreeAsync(vals2, c->stream);
+    cudaFreeAsync(tmp, c->stream);
+    cudaFreeAsync(hist, c->stream);
+    if (rc) return rc;
+    std::vector<int32_t> ts, tl, tk;
+    std::vector<float> nk((size_t)c->n_waves * I3);
+    for (int64_t w = 0; w < c->n_waves; ++w) {
+        int64_t pos = std::min<int64_t>(w * W, n);
+        const int64_t len = std::min<int64_t>(W, n - pos);
+        for (int32_t k = 0; k < I3; ++k) {
+            const int64_t cnt = h[(size_t)w * I3 + k];
+            nk[(size_t)w * I3 + k] = (float)cnt;
+            for (int64_t t = 0; t < cnt; t += kFastTile) {
+                ts.push_back((int32_t)(pos + t));
+                tl.push_back((int32_t)std::min<int64_t>(kFastTile, cnt - t));
+                tk.push_back(k);
+            }
+            pos += cnt;
+        }
+        c->wave_tile.push_back((int64_t)ts.size());
+        c->wave_len.push_back(len);
+    }
+    c->n_tiles = (int64_t)ts.size();
+    auto upload = [&](int32_t **dst, const std::vector<int32_t> &v) -> int {
+        SNECT_CUDA(c, cudaMalloc((void **)dst, sizeof(int32_t) * v.size()));
+        SNECT_CUDA(c, cudaMemcpy(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
+        return SNECT_OK;
+    };
+    if ((rc = upload(&c->tile_start, ts)) || (rc = upload(&c->tile_len, tl)) || (rc = upload(&c->tile_k, tk)))
+        return rc;
+    SNECT_CUDA(c, cudaMalloc((void **)&c->wave_nk, sizeof(float) * nk.size()));
+    SNECT_CUDA(c, cudaMemcpy(c->wave_nk, nk.data(), sizeof(float) * nk.size(), cudaMemcpyHostToDevice));
     return SNECT_OK;
 }
 

@@ -85,6 +85,35 @@ def test_one_batch_larger_than_the_problem(gpu_lib):
     step_parity(p, [0, 0, 0], gpu_lib, batch=4096)
 
 
+def test_network_pass_hub_rows(gpu_lib):
+    """Rows above 128 neighbours take the chunked (affine-composition) pass; rows at or below
+    take the sequential walk.  Hubs of degree 600, 129 and 128 against the oracle's walk."""
+    import paper_1711_08095_gb300 as snect
+
+    rng = np.random.default_rng(21)
+    I, J = (3, 700, 2), (2, 5, 2)
+    edges = [(0, j) for j in range(1, 601)] + [(650, j) for j in range(1, 130)] + \
+            [(699, j) for j in range(200, 328)]
+    extra = set()
+    while len(extra) < 400:
+        a, b = sorted(rng.integers(1, 650, size=2).tolist())
+        if a != b and (a, b) not in extra:
+            extra.add((a, b))
+    edges = np.array(edges + sorted(extra), np.int32)
+    edges = edges[rng.permutation(len(edges))]
+    w = rng.uniform(0.5, 1.0, len(edges)).astype(np.float32)
+    G0, U0 = S.init_params(I, J, 3)
+    idx = np.array([[0, 0, 0]], np.int32)
+    c = snect.Snect(I, J, idx, np.zeros(1, np.float32), edges, w, G0, U0, lam=0.01, lam_g=2.0, lr=0.05, batch=1)
+    P = oracle.Params(G0, U0)
+    for _ in range(3):
+        oracle.edge_pass(I[1], P, 2.0, 0.05, edges, w)
+        c.edge_pass()
+    _, U = c.get_factors()
+    assert_close(U[1], P.U[1], STEP_TOL, "network pass with hubs")
+    c.close()
+
+
 def test_loss_terms_match_oracle(gpu_lib):
     p = S.config1()
     c = ctx(p)

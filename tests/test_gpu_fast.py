@@ -1,0 +1,95 @@
+"""GPU fast (lock-free) sweep, through the C ABI.
+
+The fast mode is not a fixed-order computation, so it is judged on what it reaches: test
+RMSE within 1% of the FP64 oracle's sequential per-entry SGD (Alg. 1 with one worker)
+after the same number of epochs from the same start.  At the paper-scale size it is checked
+on sampled predictions (Eq. 2 at sampled entries, against the oracle on the GPU's factors)
+and on properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import snect_synth as S
+
+pytestmark = pytest.mark.gpu
+
+RMSE_TOL = 0.01
+
+
+def ctx(p, **kw):
+    import paper_1711_08095_gb300 as snect
+
+    return snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                       batch=0, **kw)
+
+
+@pytest.fixture(scope="module")
+def small():
+    # the paper-scale structure at 1/150 of the entries: 150 patients x 15,000 genes x 5
+    return S.config2(n_patients=150, nnz=200_000, n_edges=10_000)
+
+
+def test_fast_mode_reaches_sequential_oracle_rmse(small, gpu_lib):
+    """Both run 40 epochs from the same start; the fast mode's test RMSE is within 1% of the
+    oracle's sequential per-entry SGD (the oracle's own RMSE still falls by ~1% per 5 epochs
+    there, so this compares the two trajectories near convergence)."""
+    p, E = small, 40
+    c = ctx(p)
+    c.epoch(E)
+    got = c.loss(p.test_idx, p.test_val)["rmse_test"]
+    c.close()
+    P = oracle.Params(p.G0, p.U0)
+    for _ in range(E):
+        oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx, p.val, p.edges, p.w)
+    want = oracle.rmse(P, p.test_idx, p.test_val)
+    assert np.isfinite(got)
+    assert abs(got - want) <= RMSE_TOL * want, (got, want)
+
+
+def test_fast_mode_is_stable_for_any_wave(small, gpu_lib):
+    """The wave-end proximal steps keep every wave size finite and descending."""
+    p = small
+    for wave in (1024, 65536, 10 ** 6):
+        c = ctx(p, wave=wave)
+        l0 = c.loss(p.test_idx, p.test_val)
+        c.epoch(5)
+        l1 = c.loss(p.test_idx, p.test_val)
+        c.close()
+        assert np.isfinite(l1["total"]) and l1["total"] < l0["total"], (wave, l0, l1)
+
+
+def test_fast_mode_unobserved_rows_stay_and_small_waves_work(gpu_lib):
+    p = S.config2(n_patients=60, n_genes=2000, nnz=40_000, n_edges=3_000)
+    c = ctx(p, wave=1000)  # many waves, ragged platform segments and tiles
+    c.epoch(3)
+    G, U = c.get_factors()
+    for n in range(2):
+        unseen = np.setdiff1d(np.arange(p.I[n]), p.idx[:, n])
+        if n == 1:  # genes also move through the network pass; check the isolated ones
+            deg = np.zeros(p.I[1], int)
+            np.add.at(deg, p.edges.reshape(-1), 1)
+            unseen = unseen[deg[unseen] == 0]
+        assert np.array_equal(U[n][unseen], p.U0[n][unseen])
+    l = c.loss(p.test_idx, p.test_val)
+    assert np.isfinite(l["total"]) and np.isfinite(G).all()
+    c.close()
+
+
+def test_paper_scale_sampled_predictions_and_properties(gpu_lib):
+    """Config 2 at full size in the launch configuration the benchmark times."""
+    p = S.config2()
+    c = ctx(p)
+    l0 = c.loss(p.test_idx, p.test_val)
+    c.epoch(2)
+    l2 = c.loss(p.test_idx, p.test_val)
+    assert np.isfinite(l2["total"]) and l2["rmse_test"] < l0["rmse_test"]
+    G, U = c.get_factors()
+    # sampled predictions: the objective's RMSE on 5,000 sampled test entries equals the
+    # oracle's on the same entries with the GPU's factors
+    rng = np.random.default_rng(0)
+    s = rng.choice(p.test_idx.shape[0], 5000, replace=False)
+    got = c.loss(p.test_idx[s], p.test_val[s])["rmse_test"]
+    want = oracle.rmse(oracle.Params(G, U), p.test_idx[s], p.test_val[s])
+    assert abs(got - want) <= 1e-5 * want, (got, want)
+    c.close()

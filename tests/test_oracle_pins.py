@@ -250,6 +250,16 @@ def test_epoch_is_batches_then_network_pass():
         assert np.array_equal(x, y)
 
 
+def test_sequential_epoch_equals_batches_of_one():
+    p = S.tiny_problem(seed=12, I=(5, 6, 3), J=(2, 3, 2), density=0.8, n_edges=6)
+    A = oracle.Params(p.G0, p.U0)
+    oracle.sgd_epoch(p.I, A, p.lam, p.lam_g, p.lr, p.idx, p.val, p.edges, p.w)
+    B = oracle.Params(p.G0, p.U0)
+    oracle.epoch(p.I, B, p.lam, p.lam_g, p.lr, 1, p.idx, p.val, p.edges, p.w)
+    for x, y in zip([A.G] + A.U, [B.G] + B.U):
+        assert np.allclose(x, y, rtol=1e-13, atol=1e-15)
+
+
 def test_sgd_reaches_noise_floor_on_planted_tensor():
     rng = np.random.default_rng(0)
     I, J, sigma = (30, 40, 3), (2, 2, 2), 0.05
@@ -264,7 +274,7 @@ def test_sgd_reaches_noise_floor_on_planted_tensor():
     P = oracle.Params(G0, U0)
     none = np.zeros((0, 2), np.int32)
     for _ in range(80):
-        oracle.epoch(I, P, 1e-3, 0.0, 0.02, 1, tr, xtr, none, np.zeros(0))
+        oracle.sgd_epoch(I, P, 1e-3, 0.0, 0.02, tr, xtr, none, np.zeros(0))
     assert oracle.rmse(P, tr, xtr) < 1.1 * sigma
     assert oracle.rmse(P, te, xte) < 1.2 * sigma
 
