@@ -122,6 +122,26 @@ int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n,
  * idx_out (int32) / score_out (float): any, k each.  1 <= k <= min(I1, 64).  Synchronises. */
 int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, float *score_out);
 
+/* Fold-in that allocates nothing, for callers that cannot call cudaMalloc (a process that
+ * lives inside another framework's memory budget or allocator, a serving loop that must not
+ * stall on the allocator, code that keeps every device buffer pre-reserved).  The paper has
+ * no counterpart: this is snect_foldin's computation without a context.
+ *   G, U2, U3  device, the frozen core and gene / platform factors (layouts above)
+ *   jk, val    device, the query's n cells ((gene, platform) int32 pairs) and values
+ *   u_out      device, J1 floats
+ *   stream     a cudaStream_t, or NULL for the default stream; the call synchronises it.
+ * Its only working memory is a fixed device array inside the library (about 1 MiB, reserved
+ * on every GPU that loads the library until the process exits), which bounds the query at
+ * n <= 1,048,576 cells; larger queries return SNECT_EINVAL.  The first call on each device
+ * looks up that array's address with the device current; make that first call before any
+ * stream capture.  Calls share the array, so two calls whose work overlaps on the GPU (from
+ * different streams or threads) race; serialise them.  Errors: SNECT_EINVAL for bad sizes,
+ * an out-of-range cell, a non-finite value or a system that is not positive definite;
+ * messages through snect_last_error(NULL). */
+int snect_foldin_static(const float *G, const float *U2, const float *U3, int32_t I2, int32_t I3,
+                        int32_t J1, int32_t J2, int32_t J3, const int32_t *jk, const float *val,
+                        int64_t n, float lambda, float *u_out, void *stream);
+
 /* Device time of the entry-sweep kernels of the most recent epoch (fast mode: one launch per
  * wave), measured with CUDA events recorded on the context's stream immediately before and
  * after each launch.  *ms_total = summed milliseconds, *n_launches = launches timed.

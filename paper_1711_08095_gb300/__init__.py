@@ -35,6 +35,7 @@ EXPORTS = (
     "snect_set_factors",
     "snect_foldin",
     "snect_topk",
+    "snect_foldin_static",
     "snect_sweep_times",
     "snect_launch_count",
     "snect_last_error",
@@ -107,6 +108,7 @@ def load(build_if_missing: bool = False):
         "snect_set_factors": (ctypes.c_int, [P, P, P, P, P]),
         "snect_foldin": (ctypes.c_int, [P, P, P, i64, P]),
         "snect_topk": (ctypes.c_int, [P, P, i32, P, P]),
+        "snect_foldin_static": (ctypes.c_int, [P, P, P, i32, i32, i32, i32, i32, P, P, i64, ctypes.c_float, P, P]),
         "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
         "snect_last_error": (ctypes.c_char_p, [P]),
