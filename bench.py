@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="a small problem of the same shape (for profiling)")
+    ap.add_argument("--serve-queries", type=int, default=20000, help="fold-in + top-k queries (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, queries/s")
     return ap.parse_args()
 
 
@@ -167,6 +169,77 @@ def cpu_baseline(p, budget_s=15.0):
             "sample": "FP64 oracle, sequential per-entry epoch over the first %d training entries of the "
                       "workload (%.1f s on one host core; the network pass excluded)" % (n2, dt),
             "host_cores": os.cpu_count()}
+
+
+def serving(args, snect):
+    """Serving form: the paper-scale planted model at core 16 x 16 x 5 frozen on the device; a
+    Poisson stream of new-patient queries (5,000-75,000 observed cells, log-uniform) folded in
+    and searched (cosine top-10 over 4,500 patients) by the continuous-batching server.
+    Latency = submit to completion (host clock)."""
+    import snect_synth as S
+
+    m = S.serving_model()
+    I = tuple(u.shape[0] for u in m.U)
+    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
+    ctx = snect.Snect(I, m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32),
+                      np.zeros(0, np.float32), m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
+    pool_n = 256
+    pool = [S.serving_query(m, q=q) for q in range(pool_n)]  # distinct queries, resubmitted in turn
+    arrivals = S.poisson_arrivals(args.serve_queries, args.serve_rate)
+    srv = ctx.serve(n_slots=16, mem_budget_bytes=512 << 20, max_cells=75_000)
+    for jk, x, _ in pool[:8]:  # warm-up
+        srv.poll(srv.submit(jk, x, 10), 10)
+    tickets = [None] * len(arrivals)
+    t0 = time.perf_counter()
+
+    def producer():
+        for qi, ta in enumerate(arrivals):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            jk, x, _ = pool[qi % pool_n]
+            tickets[qi] = srv.submit(jk, x, 10)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    lat = []
+    for qi in range(len(arrivals)):
+        while tickets[qi] is None:
+            time.sleep(0.0002)
+        _, _, _, l = srv.poll(tickets[qi], 10)
+        lat.append(l)
+    t_end = time.perf_counter()
+    th.join()
+    st = srv.stats()
+    srv.stop()
+    ctx.close()
+    lat = np.array(lat)
+    cells = np.array([len(pool[qi % pool_n][1]) for qi in range(len(arrivals))])
+    return {"queries": int(len(arrivals)), "offered_qps": args.serve_rate,
+            "achieved_qps": len(arrivals) / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "mean_cells": float(cells.mean()), "slots": 16, "max_concurrent": st["max_concurrent"],
+            "workload": "4500x15000x5 planted model, core 16x16x5, frozen; Poisson arrivals; queries of "
+                        "5,000-75,000 cells (log-uniform), %d distinct queries resubmitted in turn; "
+                        "closed-form ridge fold-in + cosine top-10; latency from submit to result" % pool_n,
+            "paper_context_ms_per_query": 550.0}
+
+
+def quality(loss, job_loss, job_epochs, epochs_run, small):
+    """Test RMSE of the e2e jobs (10 epochs from the initial factors) beside the oracle's after
+    the same 10 sequential epochs (tests/golden/config2_oracle.json, written from oracle/)."""
+    q = {"rmse_test_after_%d_epochs" % job_epochs: job_loss["rmse_test"],
+         "rmse_test_after_%d_epochs" % epochs_run: loss["rmse_test"]}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "config2_oracle.json")) as fh:
+            g = json.load(fh)
+        if not small:
+            ref = g["rmse_test"][job_epochs - 1]
+            q["oracle_sequential_rmse_test_after_%d_epochs" % job_epochs] = ref
+            q["relative_to_oracle"] = job_loss["rmse_test"] / ref - 1.0
+    except (OSError, KeyError, IndexError):
+        pass
+    return q
 
 
 def run_reference(args):
@@ -291,11 +364,12 @@ def main():
                      "timing": "CUDA events around each sweep launch inside the last timed epoch (%d launches, "
                                "%.3f ms)" % (sweep_n, sweep_ms)},
         "clocks": clk.summary(),
-        "quality": {"rmse_test_after_warmup_and_steps": loss["rmse_test"], "rmse_train": loss["rmse_train"],
-                    "epochs_run": args.warmup + args.steps, "e2e_job_rmse_test": job_loss["rmse_test"]},
+        "quality": quality(loss, job_loss, job_epochs, args.warmup + args.steps, args.small),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0 and args.serve_queries > 0:
+        line["serving"] = serving(args, snect)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

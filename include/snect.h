@@ -122,6 +122,34 @@ int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n,
  * idx_out (int32) / score_out (float): any, k each.  1 <= k <= min(I1, 64).  Synchronises. */
 int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, float *score_out);
 
+/* Continuous-batching service of fold-in + top-k queries (Eq. 9 and Sec. 3.2.1 on a stream
+ * of new patients).  snect_serve_start builds the (gene, platform) table of the frozen factors
+ * and n_slots slots (one CUDA stream, pinned staging and device buffers for max_cells cells
+ * each).  A scheduler thread admits queued requests oldest first whenever a slot is free and
+ * the device bytes of the requests in flight plus the next one stay within mem_budget_bytes
+ * (a request of n cells counts 12 n + 4 ceil(n / 4096) (J1^2 + J1) bytes: its cells and its
+ * Gram partials);
+ * admitted requests run concurrently on their slots' streams.  A request's result does not
+ * depend on what else is running.  While a server runs, the context must not be trained or
+ * have its factors set.  Errors: SNECT_EINVAL (sizes, budget below one largest request),
+ * SNECT_ENOMEM. */
+typedef struct snect_server snect_server;
+int snect_serve_start(snect_ctx *ctx, int32_t n_slots, int64_t mem_budget_bytes, int32_t max_cells,
+                      snect_server **out);
+/* Queues one query: jk (host, n*2 int32 (gene, platform)), val (host, n floats) are copied;
+ * 1 <= n <= max_cells, 1 <= k <= min(I1, 64).  Thread-safe.  *ticket identifies the result. */
+int snect_serve_submit(snect_server *srv, const int32_t *jk, const float *val, int64_t n, int32_t k,
+                       int64_t *ticket);
+/* Result of a ticket: u_out (J1 floats), idx_out / score_out (k each), latency_ms (submit to
+ * completion, host clock); any output pointer may be NULL.  wait = 0 returns SNECT_EBUSY if
+ * the request has not finished.  Each ticket's result is returned once.  Thread-safe. */
+int snect_serve_poll(snect_server *srv, int64_t ticket, int32_t wait, float *u_out, int32_t *idx_out,
+                     float *score_out, double *latency_ms);
+/* Counters: requests admitted and completed so far, and the most requests in flight at once. */
+int snect_serve_stats(snect_server *srv, int64_t *admitted, int64_t *completed, int64_t *max_concurrent);
+/* Finishes every queued request, stops the scheduler and frees the slots. */
+int snect_serve_stop(snect_server *srv);
+
 /* Fold-in that allocates nothing, for callers that cannot call cudaMalloc (a process that
  * lives inside another framework's memory budget or allocator, a serving loop that must not
  * stall on the allocator, code that keeps every device buffer pre-reserved).  The paper has

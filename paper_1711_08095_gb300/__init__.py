@@ -36,6 +36,11 @@ EXPORTS = (
     "snect_foldin",
     "snect_topk",
     "snect_foldin_static",
+    "snect_serve_start",
+    "snect_serve_submit",
+    "snect_serve_poll",
+    "snect_serve_stats",
+    "snect_serve_stop",
     "snect_sweep_times",
     "snect_launch_count",
     "snect_last_error",
@@ -108,6 +113,12 @@ def load(build_if_missing: bool = False):
         "snect_set_factors": (ctypes.c_int, [P, P, P, P, P]),
         "snect_foldin": (ctypes.c_int, [P, P, P, i64, P]),
         "snect_topk": (ctypes.c_int, [P, P, i32, P, P]),
+        "snect_serve_start": (ctypes.c_int, [P, i32, i64, i32, ctypes.POINTER(P)]),
+        "snect_serve_submit": (ctypes.c_int, [P, P, P, i64, i32, ctypes.POINTER(ctypes.c_int64)]),
+        "snect_serve_poll": (ctypes.c_int, [P, i64, i32, P, P, P, ctypes.POINTER(ctypes.c_double)]),
+        "snect_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+        "snect_serve_stop": (ctypes.c_int, [P]),
         "snect_foldin_static": (ctypes.c_int, [P, P, P, i32, i32, i32, i32, i32, P, P, i64, ctypes.c_float, P, P]),
         "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
@@ -252,6 +263,10 @@ class Snect:
         self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def serve(self, n_slots: int = 8, mem_budget_bytes: int = 1 << 30, max_cells: int = 75_000):
+        """Starts a continuous-batching fold-in + top-k server on this context's factors."""
+        return Server(self, n_slots, mem_budget_bytes, max_cells)
+
     @property
     def launches(self) -> int:
         return int(self._lib.snect_launch_count(self._h))
@@ -259,3 +274,58 @@ class Snect:
     @property
     def handle(self):
         return self._h
+
+
+class Server:
+    """A running snect_server (see snect_serve_* in include/snect.h)."""
+
+    def __init__(self, ctx: "Snect", n_slots: int, mem_budget_bytes: int, max_cells: int):
+        self._lib = ctx._lib
+        self._ctx = ctx
+        self.J1 = ctx.J[0]
+        h = ctypes.c_void_p()
+        rc = self._lib.snect_serve_start(ctx.handle, int(n_slots), int(mem_budget_bytes), int(max_cells),
+                                         ctypes.byref(h))
+        if rc != 0:
+            raise SnectError(rc, self._lib.snect_last_error(ctx.handle).decode())
+        self._h = h
+
+    def submit(self, jk, val, k: int = 10) -> int:
+        jk = np.ascontiguousarray(jk, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float32)
+        t = ctypes.c_int64()
+        rc = self._lib.snect_serve_submit(self._h, jk.ctypes.data, val.ctypes.data, int(val.shape[0]), int(k),
+                                          ctypes.byref(t))
+        if rc != 0:
+            raise SnectError(rc, "submit rejected (size, k, or server stopping)")
+        return t.value
+
+    def poll(self, ticket: int, k: int = 10, wait: bool = True):
+        """(u, idx, score, latency_ms) of a finished ticket, or None if not finished and not waiting."""
+        u = np.empty(self.J1, np.float32)
+        idx = np.empty(k, np.int32)
+        sc = np.empty(k, np.float32)
+        lat = ctypes.c_double()
+        rc = self._lib.snect_serve_poll(self._h, int(ticket), 1 if wait else 0, u.ctypes.data, idx.ctypes.data,
+                                        sc.ctypes.data, ctypes.byref(lat))
+        if rc == -5 and not wait:
+            return None
+        if rc != 0:
+            raise SnectError(rc, "request %d failed" % ticket)
+        return u, idx, sc, lat.value
+
+    def stats(self):
+        a, c, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._lib.snect_serve_stats(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(m))
+        return dict(admitted=a.value, completed=c.value, max_concurrent=m.value)
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            self._lib.snect_serve_stop(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

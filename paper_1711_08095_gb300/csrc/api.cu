@@ -183,6 +183,8 @@ int ensure_wtable(Ctx *c) {
 
 }  // namespace
 
+int ensure_wtable_for_serving(Ctx *c) { return ensure_wtable(c); }
+
 int timing_events(Ctx *c, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -470,7 +472,7 @@ int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches) {
 
 int64_t snect_launch_count(const snect_ctx *h) {
     const Ctx *c = reinterpret_cast<const Ctx *>(h);
-    return c ? c->launches : 0;
+    return c ? c->launches.load() : 0;
 }
 
 const char *snect_last_error(const snect_ctx *h) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -36,7 +37,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    int64_t launches = 0;
+    std::atomic<int64_t> launches{0};
     std::string err;
 
     // problem
@@ -76,7 +77,8 @@ struct Ctx {
     float *gram = nullptr;          // moments of U1, U2 (two buffers of gram_stride) + eigenvectors
     int64_t gram_stride = 0;
     int32_t fast_grid = 0;          // persistent CTAs of the wave kernel (occupancy)
-    float *gacc[2] = {};            // per patient / gene row: gradient sums and curvature (J_n + 1)
+    float *gacc[2] = {};            // per patient / gene row: gradient sums + entries per platform
+    float *curv = nullptr;          // platform curvatures of the row steps (two buffers)
     // fold-in / top-k
     float *wtable = nullptr;        // I2*I3*J1: w_jk = G x2 u2_j x3 u3_k
     int64_t param_version = 0;      // bumped whenever G or a factor may have changed
@@ -131,8 +133,8 @@ int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of
 int enqueue_fast_epoch(Ctx *c);
 void free_fast(Ctx *c);
 constexpr int kFastTile = 256;     // entries per tile (one per thread of the wave kernel)
-constexpr int64_t kMinWave = 4096;      // default wave: nnz/64 clamped to [kMinWave, kMaxWave]
-constexpr int64_t kMaxWave = 1 << 20;
+constexpr int64_t kMinWave = 4096;      // default wave: nnz/16 clamped to [kMinWave, kMaxWave]
+constexpr int64_t kMaxWave = 1 << 21;
 int det_scratch_floats(const Ctx *c, int64_t *gbuf_floats, int64_t *part_floats);
 cudaError_t det_init_attrs(Ctx *c);
 cudaError_t loss_init_attrs(Ctx *c);

@@ -299,7 +299,7 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
 int prep_fast_tiles(Ctx *c) {
     const int64_t n = c->nnz;
     const int32_t I3 = c->d.I3;
-    int64_t W = c->cfg.wave > 0 ? c->cfg.wave : std::min<int64_t>(kMaxWave, std::max<int64_t>(kMinWave, (n + 63) / 64));
+    int64_t W = c->cfg.wave > 0 ? c->cfg.wave : std::min<int64_t>(kMaxWave, std::max<int64_t>(kMinWave, (n + 15) / 16));
     if (n) {  // an even number of waves (>= 2), so the moment buffers alternate across epochs
         int64_t nw = (n + W - 1) / W;
         nw = std::max<int64_t>(2, (nw + 1) & ~(int64_t)1);

@@ -1,0 +1,359 @@
+// Continuous-batching service for fold-in + top-k queries (Eq. 9, Sec. 3.2.1).
+//
+// Requests (a new patient's observed (gene, platform, value) cells) are submitted from any
+// host thread and copied into a host queue.  One scheduler thread admits queued requests,
+// oldest first, whenever a slot is free and the bytes of the requests already on the GPU plus
+// this one stay within the device-memory budget; requests that arrive while others are
+// running are admitted as soon as slots and memory free up.  Each slot owns a CUDA stream,
+// pinned staging buffers and device buffers sized for the largest query, so admitted requests
+// overlap on the device.  Per request the slot stream runs: copy in -> cell check -> fold-in
+// partials (fixed CTA partition) -> FP64 Cholesky solve -> cosine scores -> top-k -> copy out,
+// then records an event; the scheduler polls the events and publishes finished results.
+// The kernels and their partition depend only on the request, so a request's result is the
+// same alone and in any mix.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "serve.cuh"
+
+namespace snect {
+
+int ensure_wtable_for_serving(Ctx *c);  // api.cu
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t ticket;
+    std::vector<int32_t> jk;
+    std::vector<float> val;
+    int32_t k;
+    Clock::time_point t_submit;
+};
+
+struct Result {
+    int status = 0;  // 0 ok, else SNECT_E*
+    std::vector<float> u;
+    std::vector<int32_t> idx;
+    std::vector<float> score;
+    double latency_ms = 0.0;
+    double queue_ms = 0.0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int32_t *h_jk = nullptr;  // pinned
+    float *h_val = nullptr;
+    float *h_u = nullptr;
+    int32_t *h_idx = nullptr;
+    float *h_score = nullptr;
+    int32_t *h_flag = nullptr;
+    int2 *d_jk = nullptr;
+    float *d_val = nullptr, *d_part = nullptr, *d_u = nullptr, *d_score = nullptr, *d_top_s = nullptr;
+    int32_t *d_status = nullptr, *d_top_i = nullptr, *d_flag = nullptr;
+    uint8_t *d_taken = nullptr;
+    bool busy = false;
+    Request req;
+    int64_t bytes = 0;
+    Clock::time_point t_admit;
+};
+
+}  // namespace
+
+struct Server {
+    Ctx *c = nullptr;
+    int32_t max_cells = 0;
+    int64_t budget = 0;
+    int64_t in_flight_bytes = 0;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_submit, cv_done;
+    std::deque<Request> queue;
+    std::unordered_map<int64_t, Result> done;
+    std::atomic<bool> stop{false};
+    std::thread worker;
+    int64_t next_ticket = 1;
+    int64_t admitted = 0, completed = 0, max_concurrent = 0;
+    std::string err;
+};
+
+namespace {
+
+int64_t request_bytes(const Ctx *c, int64_t n) {
+    return n * (int64_t)(sizeof(int2) + sizeof(float)) +
+           foldin_parts(n) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1) * (int64_t)sizeof(float);
+}
+
+void free_slot(Slot &s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    cudaFreeHost(s.h_jk);
+    cudaFreeHost(s.h_val);
+    cudaFreeHost(s.h_u);
+    cudaFreeHost(s.h_idx);
+    cudaFreeHost(s.h_score);
+    cudaFreeHost(s.h_flag);
+    cudaFree(s.d_jk);
+    cudaFree(s.d_val);
+    cudaFree(s.d_part);
+    cudaFree(s.d_u);
+    cudaFree(s.d_score);
+    cudaFree(s.d_top_s);
+    cudaFree(s.d_status);
+    cudaFree(s.d_top_i);
+    cudaFree(s.d_flag);
+    cudaFree(s.d_taken);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot();
+}
+
+cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
+    const int64_t parts = foldin_parts(max_cells) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1);
+    cudaError_t e;
+#define TRY(x)                         \
+    if ((e = (x)) != cudaSuccess) return e;
+    TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    TRY(cudaMallocHost((void **)&s.h_jk, sizeof(int32_t) * 2 * max_cells));
+    TRY(cudaMallocHost((void **)&s.h_val, sizeof(float) * max_cells));
+    TRY(cudaMallocHost((void **)&s.h_u, sizeof(float) * kMaxRank));
+    TRY(cudaMallocHost((void **)&s.h_idx, sizeof(int32_t) * 64));
+    TRY(cudaMallocHost((void **)&s.h_score, sizeof(float) * 64));
+    TRY(cudaMallocHost((void **)&s.h_flag, sizeof(int32_t) * 2));
+    TRY(cudaMalloc((void **)&s.d_jk, sizeof(int2) * max_cells));
+    TRY(cudaMalloc((void **)&s.d_val, sizeof(float) * max_cells));
+    TRY(cudaMalloc((void **)&s.d_part, sizeof(float) * parts));
+    TRY(cudaMalloc((void **)&s.d_u, sizeof(float) * kMaxRank));
+    TRY(cudaMalloc((void **)&s.d_score, sizeof(float) * c->d.I1));
+    TRY(cudaMalloc((void **)&s.d_top_s, sizeof(float) * 64));
+    TRY(cudaMalloc((void **)&s.d_status, sizeof(int32_t)));
+    TRY(cudaMalloc((void **)&s.d_top_i, sizeof(int32_t) * 64));
+    TRY(cudaMalloc((void **)&s.d_flag, sizeof(int32_t)));
+    TRY(cudaMalloc((void **)&s.d_taken, c->d.I1));
+#undef TRY
+    return cudaSuccess;
+}
+
+// launches one request on its slot (scheduler thread)
+cudaError_t launch_request(Ctx *c, Slot &s) {
+    const Request &r = s.req;
+    const int64_t n = (int64_t)r.val.size();
+    std::memcpy(s.h_jk, r.jk.data(), sizeof(int32_t) * 2 * n);
+    std::memcpy(s.h_val, r.val.data(), sizeof(float) * n);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(s.d_jk, s.h_jk, sizeof(int2) * n, cudaMemcpyHostToDevice, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(s.d_val, s.h_val, sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
+    if ((e = cudaMemsetAsync(s.d_flag, 0, sizeof(int32_t), s.stream))) return e;
+    if ((e = launch_check_cells(c, s.stream, s.d_jk, s.d_val, n, s.d_flag))) return e;
+    if ((e = launch_foldin(c, s.stream, s.d_jk, s.d_val, n, c->wtable, s.d_part, s.d_u, s.d_status))) return e;
+    if ((e = launch_topk(c, s.stream, s.d_u, r.k, s.d_score, s.d_taken, s.d_top_i, s.d_top_s))) return e;
+    if ((e = cudaMemcpyAsync(s.h_u, s.d_u, sizeof(float) * c->d.J1, cudaMemcpyDeviceToHost, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(s.h_idx, s.d_top_i, sizeof(int32_t) * r.k, cudaMemcpyDeviceToHost, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(s.h_score, s.d_top_s, sizeof(float) * r.k, cudaMemcpyDeviceToHost, s.stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(s.h_flag, s.d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(s.h_flag + 1, s.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream)))
+        return e;
+    return cudaEventRecord(s.done, s.stream);
+}
+
+void scheduler(Server *S) {
+    Ctx *c = S->c;
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        // admit: oldest first, while a slot is free and the budget allows
+        bool progressed = false;
+        while (!S->queue.empty()) {
+            const int64_t need = request_bytes(c, (int64_t)S->queue.front().val.size());
+            if (S->in_flight_bytes > 0 && S->in_flight_bytes + need > S->budget) break;
+            int free_slot_i = -1;
+            for (size_t i = 0; i < S->slots.size(); ++i)
+                if (!S->slots[i].busy) {
+                    free_slot_i = (int)i;
+                    break;
+                }
+            if (free_slot_i < 0) break;
+            Slot &s = S->slots[free_slot_i];
+            s.req = std::move(S->queue.front());
+            S->queue.pop_front();
+            s.busy = true;
+            s.bytes = need;
+            s.t_admit = Clock::now();
+            S->in_flight_bytes += need;
+            S->admitted++;
+            int64_t conc = 0;
+            for (auto &x : S->slots) conc += x.busy;
+            S->max_concurrent = std::max(S->max_concurrent, conc);
+            lk.unlock();
+            cudaError_t e = launch_request(c, s);
+            lk.lock();
+            if (e != cudaSuccess) {
+                Result res;
+                res.status = SNECT_ECUDA;
+                S->done[s.req.ticket] = std::move(res);
+                S->err = std::string("serving launch: ") + cudaGetErrorString(e);
+                s.busy = false;
+                S->in_flight_bytes -= s.bytes;
+                S->cv_done.notify_all();
+            }
+            progressed = true;
+        }
+        // retire finished requests
+        for (auto &s : S->slots) {
+            if (!s.busy) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            Result res;
+            const auto now = Clock::now();
+            res.latency_ms = std::chrono::duration<double, std::milli>(now - s.req.t_submit).count();
+            res.queue_ms = std::chrono::duration<double, std::milli>(s.t_admit - s.req.t_submit).count();
+            if (q != cudaSuccess) {
+                res.status = SNECT_ECUDA;
+                S->err = std::string("serving: ") + cudaGetErrorString(q);
+            } else if (s.h_flag[0]) {
+                res.status = SNECT_EINVAL;
+            } else if (s.h_flag[1]) {
+                res.status = SNECT_EINVAL;
+            } else {
+                res.u.assign(s.h_u, s.h_u + c->d.J1);
+                res.idx.assign(s.h_idx, s.h_idx + s.req.k);
+                res.score.assign(s.h_score, s.h_score + s.req.k);
+            }
+            S->done[s.req.ticket] = std::move(res);
+            s.busy = false;
+            S->in_flight_bytes -= s.bytes;
+            S->completed++;
+            progressed = true;
+            S->cv_done.notify_all();
+        }
+        bool any_busy = false;
+        for (auto &s : S->slots) any_busy |= s.busy;
+        if (S->stop.load() && S->queue.empty() && !any_busy) break;
+        if (!progressed) {
+            if (any_busy) {  // poll the GPU again shortly
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                lk.lock();
+            } else {
+                S->cv_submit.wait_for(lk, std::chrono::milliseconds(5));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace snect
+
+using namespace snect;
+
+extern "C" {
+
+int snect_serve_start(snect_ctx *h, int32_t n_slots, int64_t mem_budget_bytes, int32_t max_cells,
+                      snect_server **out) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !out) return SNECT_EINVAL;
+    *out = nullptr;
+    if (n_slots < 1 || n_slots > 256) return fail(c, SNECT_EINVAL, "n_slots must be in [1, 256]");
+    if (max_cells < 1) return fail(c, SNECT_EINVAL, "max_cells must be >= 1");
+    if (mem_budget_bytes < request_bytes(c, max_cells))
+        return fail(c, SNECT_EINVAL, "memory budget smaller than one largest request");
+    int rc = ensure_wtable_for_serving(c);
+    if (rc) return rc;
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    Server *S = new Server();
+    S->c = c;
+    S->max_cells = max_cells;
+    S->budget = mem_budget_bytes;
+    S->slots.resize(n_slots);
+    for (auto &s : S->slots) {
+        cudaError_t e = alloc_slot(c, s, max_cells);
+        if (e != cudaSuccess) {
+            for (auto &x : S->slots) free_slot(x);
+            delete S;
+            cudaGetLastError();
+            return fail(c, SNECT_ENOMEM, std::string("serving slot: ") + cudaGetErrorString(e));
+        }
+    }
+    S->worker = std::thread(scheduler, S);
+    *out = reinterpret_cast<snect_server *>(S);
+    return SNECT_OK;
+}
+
+int snect_serve_submit(snect_server *h, const int32_t *jk, const float *val, int64_t n, int32_t k,
+                       int64_t *ticket) {
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || !jk || !val || !ticket) return SNECT_EINVAL;
+    if (n < 1 || n > S->max_cells) return SNECT_EINVAL;
+    if (k < 1 || k > 64 || k > S->c->d.I1) return SNECT_EINVAL;
+    Request r;
+    r.jk.assign(jk, jk + 2 * n);
+    r.val.assign(val, val + n);
+    r.k = k;
+    r.t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop.load()) return SNECT_EBUSY;
+        r.ticket = S->next_ticket++;
+        *ticket = r.ticket;
+        S->queue.push_back(std::move(r));
+    }
+    S->cv_submit.notify_one();
+    return SNECT_OK;
+}
+
+int snect_serve_poll(snect_server *h, int64_t ticket, int32_t wait, float *u_out, int32_t *idx_out,
+                     float *score_out, double *latency_ms) {
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S) return SNECT_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->done.find(ticket);
+    while (it == S->done.end()) {
+        if (!wait) return SNECT_EBUSY;
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(50));
+        it = S->done.find(ticket);
+    }
+    Result res = std::move(it->second);
+    S->done.erase(it);
+    lk.unlock();
+    if (res.status) return res.status;
+    if (u_out) std::memcpy(u_out, res.u.data(), sizeof(float) * res.u.size());
+    if (idx_out) std::memcpy(idx_out, res.idx.data(), sizeof(int32_t) * res.idx.size());
+    if (score_out) std::memcpy(score_out, res.score.data(), sizeof(float) * res.score.size());
+    if (latency_ms) *latency_ms = res.latency_ms;
+    return SNECT_OK;
+}
+
+int snect_serve_stats(snect_server *h, int64_t *admitted, int64_t *completed, int64_t *max_concurrent) {
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S) return SNECT_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (admitted) *admitted = S->admitted;
+    if (completed) *completed = S->completed;
+    if (max_concurrent) *max_concurrent = S->max_concurrent;
+    return SNECT_OK;
+}
+
+int snect_serve_stop(snect_server *h) {
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S) return SNECT_EINVAL;
+    S->stop.store(true);
+    S->cv_submit.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (auto &s : S->slots) free_slot(s);
+    delete S;
+    return SNECT_OK;
+}
+
+}  // extern "C"

@@ -7,15 +7,18 @@
 // parameters (no entry waits for another, nothing is locked), and at the end of the wave
 // each parameter block takes one proximal (implicit) step
 //     theta <- theta - (H + I/lr)^{-1} g,
-// g = the summed gradient of the wave's entries, H = a bound of their curvature:
-//   * patient / gene row: H ~ h I with h = sum_e (||v_e||^2 + lambda/|Omega^{n,i}|), the trace
-//     of the row's Gauss-Newton matrix (an upper bound of its top eigenvalue);
-//   * platform row k: H = n_k G_(3) (Ma kron Mb) G_(3)^T + n_k lambda/|Omega^{3,k}| I, a J3 x J3
-//     Cholesky solve (Ma, Mb: second moments of the patient and gene rows over the entries);
-//   * core: H ~ lambda_max(sum_k n_k c_k c_k^T) lambda_max(Ma) lambda_max(Mb) I.
-// With few entries per wave (lr * h << 1) the step is the summed per-entry step of Alg. 1;
-// with many it tends to the Newton step of the wave's quadratic, so it stays stable for any
-// wave size.
+// g = the summed gradient of the wave's entries, H their Gauss-Newton curvature, with the
+// rows of one entry's other modes replaced by their second moments over the training entries
+// (Ma = E[a a^T], Mb = E[b b^T]):
+//   * patient row i:  H = sum_k n_ik Gc_k Mb Gc_k^T + n_i lambda/|Omega^{1,i}| I   (J1 x J1)
+//   * gene row j:     H = sum_k n_jk Gc_k^T Ma Gc_k + n_j lambda/|Omega^{2,j}| I   (J2 x J2)
+//     (n_ik: the row's entries of platform k in the wave; one warp per row, Cholesky)
+//   * platform row k: H = n_k G_(3) (Ma kron Mb) G_(3)^T + n_k lambda/|Omega^{3,k}| I
+//   * core:           H = Cn kron Mb kron Ma + n lambda/|Omega| I, Cn = sum_k n_k c_k c_k^T,
+//     solved in the eigenbases of Ma, Mb, Cn (one-warp Jacobi, warm-started per wave).
+// A direction of small curvature moves by lr * g, like the summed per-entry steps of Alg. 1;
+// one of large curvature moves by the Newton step of the wave's quadratic.  Every wave size
+// is stable.
 //
 // Inside a wave the entries are grouped by platform, so within a tile c_k is fixed and the
 // contraction uses Gc = G x3 c_k (J1 x J2):
@@ -34,7 +37,6 @@ namespace snect {
 namespace {
 
 constexpr int kFastThreads = kFastTile;  // one entry per thread per tile
-constexpr int kGramRows = 128;
 
 __host__ __device__ constexpr int even_up(int x) { return (x + 1) & ~1; }
 __host__ __device__ constexpr int align4(int x) { return (x + 3) & ~3; }
@@ -50,7 +52,8 @@ struct FastArgs {
     const int32_t *cnt1, *cnt2;
     float lam;
     float *macc;
-    float *gA, *gB;  // per row: J_n gradient sums + 1 curvature sum
+    float *gA, *gB;  // per row: gradient sums (J_n, padded to 4) + entries per platform
+    int32_t rs1, rs2;  // row strides of gA, gB
 };
 
 template <int CJ1, int CJ2, int CJ3>
@@ -148,37 +151,36 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
             for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
             const float r = xt - e.x;
             const float la = A.lam / (float)A.cnt1[e.i], lb = A.lam / (float)A.cnt2[e.j];
-            // row accumulators: [gradient (J), curvature, zero padding] in float4 groups
-            constexpr int RA = (RankCap<CJ1>::value + 4) & ~3, RB = (RankCap<CJ2>::value + 4) & ~3;
-            const int RS1 = (J1 + 4) & ~3, RS2 = (J2 + 4) & ~3;
+            // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
+            constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
+            const int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
             float gva[RA], gvb[RB];
-            float hv = la, hw = lb;
 #pragma unroll
             for (int p = 0; p < J1; ++p) {
                 gva[p] = fmaf(r, v[p], la * a[p]);
-                hv = fmaf(v[p], v[p], hv);
                 ra[p] = r * a[p];
             }
-            gva[J1] = hv;
 #pragma unroll
-            for (int p = J1 + 1; p < RS1; ++p) gva[p] = 0.f;
+            for (int p = J1; p < JA; ++p) gva[p] = 0.f;
 #pragma unroll
             for (int q = 0; q < J2; ++q) {
                 gvb[q] = fmaf(r, w2[q], lb * b[q]);
-                hw = fmaf(w2[q], w2[q], hw);
                 bb[q] = b[q];
             }
-            gvb[J2] = hw;
 #pragma unroll
-            for (int q = J2 + 1; q < RS2; ++q) gvb[q] = 0.f;
-            float4 *ga = reinterpret_cast<float4 *>(A.gA + (int64_t)e.i * RS1);
-            float4 *gb = reinterpret_cast<float4 *>(A.gB + (int64_t)e.j * RS2);
+            for (int q = J2; q < JB; ++q) gvb[q] = 0.f;
+            float *ga = A.gA + (int64_t)e.i * A.rs1;
+            float *gb = A.gB + (int64_t)e.j * A.rs2;
 #pragma unroll
-            for (int t = 0; t < RS1 / 4; ++t)
-                atomicAdd(ga + t, make_float4(gva[4 * t], gva[4 * t + 1], gva[4 * t + 2], gva[4 * t + 3]));
+            for (int t = 0; t < JA / 4; ++t)
+                atomicAdd(reinterpret_cast<float4 *>(ga) + t,
+                          make_float4(gva[4 * t], gva[4 * t + 1], gva[4 * t + 2], gva[4 * t + 3]));
 #pragma unroll
-            for (int t = 0; t < RS2 / 4; ++t)
-                atomicAdd(gb + t, make_float4(gvb[4 * t], gvb[4 * t + 1], gvb[4 * t + 2], gvb[4 * t + 3]));
+            for (int t = 0; t < JB / 4; ++t)
+                atomicAdd(reinterpret_cast<float4 *>(gb) + t,
+                          make_float4(gvb[4 * t], gvb[4 * t + 1], gvb[4 * t + 2], gvb[4 * t + 3]));
+            atomicAdd(ga + JA + k, 1.f);
+            atomicAdd(gb + JB + k, 1.f);
             if (J1P != J1) ra[J1] = 0.f;
             if (J2P != J2) bb[J2] = 0.f;
         } else {
@@ -200,84 +202,197 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
     }
 }
 
-// Patient / gene rows at the end of a wave: u <- u - g / (1/lr + h), accumulators cleared;
-// then the count-weighted second moments of the updated rows into gram_out:
-// [0 .. J1^2) = sum_i cnt1_i/n a_i a_i^T, [J1^2 .. J1^2 + J2^2) = sum_j cnt2_j/n b_j b_j^T.
-__device__ void wave_rows(int blk, float *__restrict__ U1, float *__restrict__ U2, float *__restrict__ gA,
-                          float *__restrict__ gB, const int32_t *__restrict__ cnt1,
-                          const int32_t *__restrict__ cnt2, const Dims &d, float inv_lr, float inv_n,
-                          int32_t nb1, float *__restrict__ gram_out, float *rows, float *wts) {
+// ---------------------------------------------------------------------------------------
+// End of a wave
+
+// Every entry's residual is fitted by four parameter blocks at once (its patient row, gene row,
+// platform row and the core), all from the wave-start values; their curvatures are counted
+// kBlocks times so that the four proximal steps together do not overshoot the residual
+// (additive Schwarz damping).  Directions of small curvature keep the step lr * g.
+constexpr float kBlocks = 4.f;
+constexpr int kRowWarps = 8;       // warps per CTA of the row step (one row per warp at a time)
+constexpr int kRowsPerCta = 64;    // rows of one mode per CTA
+constexpr int kTileStride = kMaxRank + 1;
+constexpr int kCkStage = 8192;     // platform curvatures staged in shared memory up to this size
+
+// Patient / gene rows: u <- u - (H + (n lambda/|Omega^{n,i}| + 1/lr) I)^{-1} g with
+// H = sum_k n_ik C_k (C_k = the platform curvature of this mode), accumulators cleared; then
+// the count-weighted second moments of the updated rows (sum_i cnt_i/n u_i u_i^T) into
+// gram_out.  With do_step = 0 only the moments are formed.
+__device__ void wave_rows(int blk, int do_step, float *__restrict__ U1, float *__restrict__ U2,
+                          float *__restrict__ gA, float *__restrict__ gB, int32_t rs1, int32_t rs2,
+                          const int32_t *__restrict__ cnt1, const int32_t *__restrict__ cnt2,
+                          const Dims &d, float lam, float inv_lr, float inv_n, int32_t nb1,
+                          const float *__restrict__ curv_in, float *__restrict__ gram_out, float *sm) {
     const bool first = blk < nb1;
     const int J = first ? d.J1 : d.J2;
-    const int RS = (J + 4) & ~3;
+    const int JP = (J + 3) & ~3;
+    const int RS = first ? rs1 : rs2;
     const int I = first ? d.I1 : d.I2;
+    const int I3 = d.I3;
     float *U = first ? U1 : U2;
     float *g = first ? gA : gB;
     const int32_t *cnt = first ? cnt1 : cnt2;
-    const int64_t r0 = (int64_t)(first ? blk : blk - nb1) * kGramRows;
+    const float *Ckg = curv_in + (first ? 0 : (int64_t)I3 * d.J1 * d.J1);  // I3 blocks of J x J
+    const int64_t r0 = (int64_t)(first ? blk : blk - nb1) * kRowsPerCta;
     const int64_t left = (int64_t)I - r0;
-    const int nr = left < kGramRows ? (int)left : kGramRows;
+    const int nr = left < kRowsPerCta ? (int)left : kRowsPerCta;
     if (nr <= 0) return;
-    for (int t = threadIdx.x; t < nr * J; t += blockDim.x) {
-        const int i = t / J, q = t % J;
-        const int64_t row = r0 + i;
-        float *gr = g + row * RS;
-        const float h = gr[J];
-        float u = U[row * J + q];
-        if (h > 0.f) {
-            u -= gr[q] / (inv_lr + h);
-            U[row * J + q] = u;
-        }
-        gr[q] = 0.f;
-        rows[t] = u;
-    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sH = sm + warp * (kMaxRank * kTileStride + 2 * kMaxRank);  // J x J tile, stride 33
+    float *sg = sH + kMaxRank * kTileStride;                           // J
+    float *su = sg + kMaxRank;                                         // J
+    float *sMom = sm + kRowWarps * (kMaxRank * kTileStride + 2 * kMaxRank);  // kRowWarps x J*J
+    float *sCk = sMom + kRowWarps * kMaxRank * kMaxRank;  // platform curvatures, if they fit
+    const bool stage = I3 * J * J <= kCkStage;
+    if (stage && do_step)
+        for (int e = threadIdx.x; e < I3 * J * J; e += blockDim.x) sCk[e] = Ckg[e];
     __syncthreads();
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        g[(r0 + t) * RS + J] = 0.f;
-        wts[t] = (float)cnt[r0 + t] * inv_n;
+    const float *Ck = stage ? sCk : Ckg;
+    float mom[kMaxRank];  // this lane's moment elements lane, lane+32, ... < J*J
+    const int nmine = (J * J + 31 - lane) / 32;
+    for (int t = 0; t < nmine; ++t) mom[t] = 0.f;
+    for (int ri = warp; ri < nr; ri += kRowWarps) {
+        const int64_t row = r0 + ri;
+        float *acc = g + row * RS;
+        float n = 0.f;
+        for (int k = 0; k < I3; ++k) n += acc[JP + k];
+        if (lane < J) su[lane] = U[row * J + lane];
+        __syncwarp();
+        if (do_step && n > 0.f) {
+            const float diag = kBlocks * n * lam / (float)max(cnt[row], 1) + inv_lr;
+            for (int e = lane; e < J * J; e += 32) {
+                const int p = e / J, q = e % J;
+                float h = p == q ? diag : 0.f;
+                for (int k = 0; k < I3; ++k) {
+                    const float nk = acc[JP + k];
+                    if (nk > 0.f) h = fmaf(kBlocks * nk, Ck[(int64_t)k * J * J + e], h);
+                }
+                sH[p * kTileStride + q] = h;
+            }
+            __syncwarp();
+            // Cholesky H = L L^T, right-looking (lane l owns row l of the lower triangle)
+            for (int j = 0; j < J; ++j) {
+                const float dj = sqrtf(fmaxf(sH[j * kTileStride + j], 1e-20f));
+                __syncwarp();
+                if (lane == j) sH[j * kTileStride + j] = dj;
+                if (lane > j && lane < J) sH[lane * kTileStride + j] /= dj;
+                __syncwarp();
+                if (lane > j && lane < J) {
+                    const float lj = sH[lane * kTileStride + j];
+                    for (int m = j + 1; m <= lane; ++m) sH[lane * kTileStride + m] -= lj * sH[m * kTileStride + j];
+                }
+                __syncwarp();
+            }
+            // L y = g, then L^T x = y; lane l holds component l, columns broadcast by shuffles
+            float gl = lane < J ? acc[lane] : 0.f;
+            for (int i = 0; i < J; ++i) {
+                const float xi = __shfl_sync(0xffffffffu, gl, i) / sH[i * kTileStride + i];
+                if (lane == i) gl = xi;
+                else if (lane > i && lane < J) gl -= sH[lane * kTileStride + i] * xi;
+            }
+            for (int i = J - 1; i >= 0; --i) {
+                const float xi = __shfl_sync(0xffffffffu, gl, i) / sH[i * kTileStride + i];
+                if (lane == i) gl = xi;
+                else if (lane < i) gl -= sH[i * kTileStride + lane] * xi;
+            }
+            if (lane < J) {
+                su[lane] -= gl;
+                U[row * J + lane] = su[lane];
+            }
+            __syncwarp();
+        }
+        for (int e = lane; e < RS; e += 32) acc[e] = 0.f;
+        const float wgt = (float)cnt[row] * inv_n;
+        for (int t = 0; t < nmine; ++t) {
+            const int e = lane + 32 * t;
+            mom[t] = fmaf(wgt * su[e / J], su[e % J], mom[t]);
+        }
+        __syncwarp();
     }
+    for (int t = 0; t < nmine; ++t) sMom[warp * J * J + lane + 32 * t] = mom[t];
     __syncthreads();
     float *out = gram_out + (first ? 0 : d.J1 * d.J1);
-    for (int s = threadIdx.x; s < J * J; s += blockDim.x) {
-        const int p = s / J, q = s % J;
-        float acc = 0.f;
-        for (int i = 0; i < nr; ++i) acc = fmaf(wts[i] * rows[i * J + p], rows[i * J + q], acc);
-        atomicAdd(out + s, acc);
+    for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
+        float x = 0.f;
+        for (int w = 0; w < kRowWarps; ++w) x += sMom[w * J * J + e];
+        atomicAdd(out + e, x);
     }
 }
 
-// largest eigenvalue of a symmetric PSD n x n matrix (n <= 32) by power iteration, one warp,
-// warm-started from the vector of the previous wave (vec, n floats, kept in global memory)
-__device__ float warp_top_eig(const float *M, int n, float *vec) {
+// Eigen-decomposition of a symmetric n x n matrix (n <= 32) by cyclic Jacobi rotations, one
+// warp.  M (stride kTileStride) is overwritten: its diagonal ends as the eigenvalues; V
+// (stride kTileStride) holds the eigenvectors as columns.  Vwarm (n x n, global) is the
+// previous decomposition: M is first rotated into that basis, so a slowly changing matrix
+// needs few sweeps; the result is written back to Vwarm.
+__device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm) {
     const int lane = threadIdx.x & 31;
-    float v = lane < n ? vec[lane] : 0.f;
-    float v2 = v * v;
+    // V = Vwarm (identity if it is all zero), M <- V^T M V
+    float vsum = 0.f;
+    for (int e = lane; e < n * n; e += 32) vsum += fabsf(Vwarm[e]);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-    if (!(v2 > 0.f)) {
-        v = lane < n ? rsqrtf((float)n) : 0.f;
-    } else {
-        v *= rsqrtf(v2);
+    for (int o = 16; o; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+    for (int e = lane; e < n * n; e += 32) {
+        const int p = e / n, q = e % n;
+        V[p * kTileStride + q] = vsum > 0.f ? Vwarm[e] : (p == q ? 1.f : 0.f);
     }
-    float lam = 0.f;
-    for (int it = 0; it < 12; ++it) {
-        float y = 0.f;
+    __syncwarp();
+    if (lane < n) {  // T = M V  (row lane)
         for (int q = 0; q < n; ++q) {
-            const float vq = __shfl_sync(0xffffffffu, v, q);
-            if (lane < n) y = fmaf(M[lane * n + q], vq, y);
+            float x = 0.f;
+            for (int k = 0; k < n; ++k) x = fmaf(M[lane * kTileStride + k], V[k * kTileStride + q], x);
+            T[lane * kTileStride + q] = x;
         }
-        float nn = y * y;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-        const float norm = sqrtf(nn);
-        if (!(norm > 0.f)) return 0.f;
-        lam = norm;
-        v = y / norm;
     }
-    if (lane < n) vec[lane] = v;
-    // with a few iterations |Mv| can sit slightly below the top eigenvalue; 5% headroom keeps
-    // the core step on the safe side
-    return 1.05f * lam;
+    __syncwarp();
+    if (lane < n) {  // M = V^T T (row lane)
+        for (int q = 0; q < n; ++q) {
+            float x = 0.f;
+            for (int k = 0; k < n; ++k) x = fmaf(V[k * kTileStride + lane], T[k * kTileStride + q], x);
+            M[lane * kTileStride + q] = x;
+        }
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        float off = 0.f, dia = 0.f;
+        for (int e = lane; e < n * n; e += 32) {
+            const float x = M[(e / n) * kTileStride + e % n];
+            if (e / n != e % n) off += x * x; else dia += x * x;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if (off <= 1e-12f * dia || !(dia > 0.f)) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const float apq = M[p * kTileStride + q];
+                const float app = M[p * kTileStride + p], aqq = M[q * kTileStride + q];
+                if (fabsf(apq) <= 1e-9f * sqrtf(fabsf(app * aqq)) + 1e-30f) continue;
+                const float theta = (aqq - app) / (2.f * apq);
+                const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+                const float cs = rsqrtf(t * t + 1.f), sn = t * cs;
+                if (lane < n) {  // columns p, q
+                    const float akp = M[lane * kTileStride + p], akq = M[lane * kTileStride + q];
+                    M[lane * kTileStride + p] = cs * akp - sn * akq;
+                    M[lane * kTileStride + q] = sn * akp + cs * akq;
+                }
+                __syncwarp();
+                if (lane < n) {  // rows p, q
+                    const float apk = M[p * kTileStride + lane], aqk = M[q * kTileStride + lane];
+                    M[p * kTileStride + lane] = cs * apk - sn * aqk;
+                    M[q * kTileStride + lane] = sn * apk + cs * aqk;
+                    const float vkp = V[lane * kTileStride + p], vkq = V[lane * kTileStride + q];
+                    V[lane * kTileStride + p] = cs * vkp - sn * vkq;
+                    V[lane * kTileStride + q] = sn * vkp + cs * vkq;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    for (int e = lane; e < n * n; e += 32) Vwarm[e] = V[(e / n) * kTileStride + e % n];
+    __syncwarp();
 }
 
 struct DenseArgs {
@@ -286,18 +401,22 @@ struct DenseArgs {
     const int32_t *cnt3;
     float *macc;
     float *gram_in;   // moments used for the curvature (cleared after use)
-    float *eigvec;    // 3 * kMaxRank warm-start vectors
+    float *eigv;      // warm-start eigenvectors of Ma, Mb, Cn (J1^2 + J2^2 + J3^2)
+    float *curv_out;  // platform curvatures for the next wave's rows (I3 J1^2 + I3 J2^2)
     const float *nk;  // entries of this wave per platform
     float n_wave, lam, lr, lam_core;
 };
 
-// The proximal step of the core and the platform rows after a wave (one CTA).
-__device__ void wave_dense(const DenseArgs &A, float *sm) {
+// The core and platform rows after a wave (one CTA), then the platform curvatures
+// C1_k = Gc_k Mb Gc_k^T and C2_k = Gc_k^T Ma Gc_k of the updated G and c_k for the next wave's
+// row steps.  With do_step = 0 only the curvatures are formed.
+__device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
     const Dims &d = A.d;
     const int J1 = d.J1, J2 = d.J2, J3 = d.J3, I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
+    const int TS = kMaxRank * kTileStride;
     float *sG = sm;                  // PI
-    float *sX = sG + PI;             // PI: X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
-    float *sT = sX + PI;             // PI: T[r][p][q] = (Ma G_r Mb)[p][q]
+    float *sX = sG + PI;             // PI (scratch)
+    float *sT = sX + PI;             // PI (scratch)
     float *sC = sT + PI;             // I3*J3
     float *sCn = sC + I3 * J3;       // J3*J3
     float *sH = sCn + J3 * J3;       // J3*J3
@@ -305,85 +424,83 @@ __device__ void wave_dense(const DenseArgs &A, float *sm) {
     float *sDel = sGk + I3 * J3;     // I3*J3 platform steps
     float *sMa = sDel + I3 * J3;     // J1*J1
     float *sMb = sMa + J1 * J1;      // J2*J2
-    float *sEig = sMb + J2 * J2;     // 3
+    float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles for the eigen-decompositions
     const int tid = threadIdx.x;
     for (int s = tid; s < PI; s += blockDim.x) sG[s] = A.G[s];
     for (int s = tid; s < I3 * J3; s += blockDim.x) sC[s] = A.U3[s];
     for (int s = tid; s < J1 * J1; s += blockDim.x) sMa[s] = A.gram_in[s];
     for (int s = tid; s < J2 * J2; s += blockDim.x) sMb[s] = A.gram_in[J1 * J1 + s];
     __syncthreads();
-    for (int s = tid; s < J3 * J3; s += blockDim.x) {
-        const int r = s / J3, t = s % J3;
-        float a = 0.f;
-        for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
-        sCn[s] = a;
-    }
-    for (int s = tid; s < PI; s += blockDim.x) {  // s = (r, p, q')
-        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-        float a = 0.f;
-        for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
-        sX[s] = a;
-    }
-    for (int s = tid; s < I3 * J3; s += blockDim.x) {
-        const int k = s / J3, r = s % J3;
-        float a = 0.f;
-        const float *M = A.macc + (int64_t)k * Q;
-        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
-        const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
-        sGk[s] = fmaf(reg, sC[s], a);
-    }
-    __syncthreads();
-    const int warp = tid >> 5;
-    if (warp < 3) {
-        const float *M = warp == 0 ? sMa : (warp == 1 ? sMb : sCn);
-        const int n = warp == 0 ? J1 : (warp == 1 ? J2 : J3);
-        const float e = warp_top_eig(M, n, A.eigvec + warp * kMaxRank);
-        if ((tid & 31) == 0) sEig[warp] = e;
-    }
-    for (int s = tid; s < PI; s += blockDim.x) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
-        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-        float a = 0.f;
-        for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
-        sT[s] = a;
-    }
-    __syncthreads();
-    for (int s = tid; s < J3 * J3; s += blockDim.x) {  // H[r][t] = sum_pq g(p,q,r) T[t][p][q]
-        const int r = s / J3, t = s % J3;
-        float a = 0.f;
-        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], sT[t * Q + pq], a);
-        sH[s] = a;
-    }
-    __syncthreads();
-    if (tid < I3) {  // platform row k: (nk H + (nk lambda/cnt3 + 1/lr) I) delta = g_k, Cholesky
-        const int k = tid;
-        float *del = sDel + k * J3;
-        const float nk = A.nk[k];
-        if (nk > 0.f) {
-            float Ak[kMaxRank * kMaxRank];  // J3 <= 32; only I3 threads hold one
-            const float reg = A.cnt3[k] > 0 ? nk * A.lam / (float)A.cnt3[k] : 0.f;
-            for (int r = 0; r < J3; ++r)
-                for (int t = 0; t < J3; ++t)
-                    Ak[r * J3 + t] = nk * sH[r * J3 + t] + (r == t ? reg + 1.f / A.lr : 0.f);
-            bool ok = true;
-            for (int j = 0; j < J3 && ok; ++j) {
-                float dd = Ak[j * J3 + j];
-                for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
-                if (!(dd > 0.f)) {
-                    ok = false;
-                    break;
+    if (do_step) {
+        for (int s = tid; s < J3 * J3; s += blockDim.x) {
+            const int r = s / J3, t = s % J3;
+            float a = 0.f;
+            for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
+            sCn[s] = a;
+        }
+        for (int s = tid; s < PI; s += blockDim.x) {  // X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
+            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+            float a = 0.f;
+            for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
+            sX[s] = a;
+        }
+        for (int s = tid; s < I3 * J3; s += blockDim.x) {
+            const int k = s / J3, r = s % J3;
+            float a = 0.f;
+            const float *M = A.macc + (int64_t)k * Q;
+            for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
+            const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
+            sGk[s] = fmaf(reg, sC[s], a);
+        }
+        __syncthreads();
+        const int warp = tid >> 5;
+        if (warp < 3) {  // eigen-decompositions of Ma, Mb, Cn, one warp each
+            const int n = warp == 0 ? J1 : (warp == 1 ? J2 : J3);
+            const float *src = warp == 0 ? sMa : (warp == 1 ? sMb : sCn);
+            float *M = sJ + warp * 3 * TS, *V = M + TS, *T = V + TS;
+            for (int e = (tid & 31); e < n * n; e += 32) M[(e / n) * kTileStride + e % n] = src[e];
+            __syncwarp();
+            float *Vw = A.eigv + (warp == 0 ? 0 : (warp == 1 ? J1 * J1 : J1 * J1 + J2 * J2));
+            warp_jacobi(M, V, T, n, Vw);
+        }
+        for (int s = tid; s < PI; s += blockDim.x) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
+            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+            float a = 0.f;
+            for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
+            sT[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < J3 * J3; s += blockDim.x) {  // H[r][t] = sum_pq g(p,q,r) T[t][p][q]
+            const int r = s / J3, t = s % J3;
+            float a = 0.f;
+            for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], sT[t * Q + pq], a);
+            sH[s] = a;
+        }
+        __syncthreads();
+        if (tid < I3) {  // platform row k: (nk H + (nk lambda/cnt3 + 1/lr) I) delta = g_k
+            const int k = tid;
+            float *del = sDel + k * J3;
+            const float nk = A.nk[k];
+            if (nk > 0.f) {
+                float Ak[kMaxRank * kMaxRank];  // J3 <= 32; only I3 threads hold one
+                const float reg = A.cnt3[k] > 0 ? nk * A.lam / (float)A.cnt3[k] : 0.f;
+                for (int r = 0; r < J3; ++r)
+                    for (int t = 0; t < J3; ++t)
+                        Ak[r * J3 + t] = kBlocks * (nk * sH[r * J3 + t] + (r == t ? reg : 0.f)) +
+                                         (r == t ? 1.f / A.lr : 0.f);
+                for (int j = 0; j < J3; ++j) {
+                    float dd = Ak[j * J3 + j];
+                    for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
+                    dd = sqrtf(fmaxf(dd, 1e-20f));
+                    Ak[j * J3 + j] = dd;
+                    for (int i = j + 1; i < J3; ++i) {
+                        float x = Ak[i * J3 + j];
+                        for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
+                        Ak[i * J3 + j] = x / dd;
+                    }
                 }
-                dd = sqrtf(dd);
-                Ak[j * J3 + j] = dd;
-                for (int i = j + 1; i < J3; ++i) {
-                    float x = Ak[i * J3 + j];
-                    for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
-                    Ak[i * J3 + j] = x / dd;
-                }
-            }
-            for (int i = 0; i < J3; ++i) del[i] = sGk[k * J3 + i];
-            if (ok) {
                 for (int i = 0; i < J3; ++i) {
-                    float x = del[i];
+                    float x = sGk[k * J3 + i];
                     for (int q = 0; q < i; ++q) x -= Ak[i * J3 + q] * del[q];
                     del[i] = x / Ak[i * J3 + i];
                 }
@@ -392,44 +509,143 @@ __device__ void wave_dense(const DenseArgs &A, float *sm) {
                     for (int q = i + 1; q < J3; ++q) x -= Ak[q * J3 + i] * del[q];
                     del[i] = x / Ak[i * J3 + i];
                 }
-            } else {  // not reached for an SPD matrix; the plain summed step
-                for (int i = 0; i < J3; ++i) del[i] *= A.lr;
+            } else {
+                for (int i = 0; i < J3; ++i) del[i] = 0.f;
             }
-        } else {
-            for (int i = 0; i < J3; ++i) del[i] = 0.f;
         }
+        // core gradient D into sX
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int pq = s / J3, r = s % J3;
+            float a = 0.f;
+            for (int k = 0; k < I3; ++k) a = fmaf(A.macc[(int64_t)k * Q + pq], sC[k * J3 + r], a);
+            sX[s] = fmaf(A.n_wave * A.lam_core, sG[s], a);
+        }
+        __syncthreads();
+        const float *Va = sJ + TS, *Vb = sJ + 3 * TS + TS, *Vc = sJ + 6 * TS + TS;
+        const float *Ma_e = sJ, *Mb_e = sJ + 3 * TS, *Mc_e = sJ + 6 * TS;  // eigenvalues on diagonals
+        // D <- D x1 Va^T x2 Vb^T x3 Vc^T   (index s = (p*J2 + q)*J3 + r)
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[pp * kTileStride + p], sX[(pp * J2 + q) * J3 + r], a);
+            sT[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[qq * kTileStride + q], sT[(p * J2 + qq) * J3 + r], a);
+            sX[s] = a;
+        }
+        __syncthreads();
+        const float diag = 1.f / A.lr + kBlocks * A.n_wave * A.lam_core;
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[rr * kTileStride + r], sX[(p * J2 + q) * J3 + rr], a);
+            const float la = fmaxf(Ma_e[p * kTileStride + p], 0.f), lb = fmaxf(Mb_e[q * kTileStride + q], 0.f),
+                        lc = fmaxf(Mc_e[r * kTileStride + r], 0.f);
+            sT[s] = a / (kBlocks * la * lb * lc + diag);
+        }
+        __syncthreads();
+        // back: D <- D x1 Va x2 Vb x3 Vc
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[p * kTileStride + pp], sT[(pp * J2 + q) * J3 + r], a);
+            sX[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[q * kTileStride + qq], sX[(p * J2 + qq) * J3 + r], a);
+            sT[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < PI; s += blockDim.x) {
+            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+            float a = 0.f;
+            for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[r * kTileStride + rr], sT[(p * J2 + q) * J3 + rr], a);
+            sG[s] -= a;
+            A.G[s] = sG[s];
+        }
+        for (int s = tid; s < I3 * J3; s += blockDim.x) {
+            sC[s] -= sDel[s];
+            A.U3[s] = sC[s];
+        }
+        __syncthreads();
+        for (int s = tid; s < I3 * Q; s += blockDim.x) A.macc[s] = 0.f;
     }
-    __syncthreads();
-    const float curv = sEig[0] * sEig[1] * sEig[2];
-    const float eta = 1.f / (1.f / A.lr + curv);
-    for (int s = tid; s < PI; s += blockDim.x) {
-        const int pq = s / J3, r = s % J3;
-        float a = 0.f;
-        for (int k = 0; k < I3; ++k) a = fmaf(A.macc[(int64_t)k * Q + pq], sC[k * J3 + r], a);
-        A.G[s] = sG[s] - eta * fmaf(A.n_wave * A.lam_core, sG[s], a);
+    // platform curvatures for the next wave's row steps (updated G, c; moments of gram_in):
+    // all platforms at once when their Gc and W fit in the two PI-sized scratch buffers
+    float *sGc = sX, *sW = sT;
+    const int kb = (I3 * Q <= PI) ? I3 : 1;  // platforms per batch
+    for (int k0 = 0; k0 < I3; k0 += kb) {
+        const int nkb = min(kb, I3 - k0);
+        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // Gc_k = G x3 c_k
+            const int k = k0 + s / Q, pq = s % Q;
+            float a = 0.f;
+            for (int r = 0; r < J3; ++r) a = fmaf(sG[pq * J3 + r], sC[k * J3 + r], a);
+            sGc[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // W1 = Gc Mb  (J1 x J2)
+            const int b = s / Q, p = (s % Q) / J2, q = s % J2;
+            float a = 0.f;
+            for (int qq = 0; qq < J2; ++qq) a = fmaf(sGc[b * Q + p * J2 + qq], sMb[qq * J2 + q], a);
+            sW[s] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < nkb * J1 * J1; s += blockDim.x) {  // C1 = W1 Gc^T
+            const int b = s / (J1 * J1), p = (s / J1) % J1, t = s % J1;
+            float a = 0.f;
+            for (int q = 0; q < J2; ++q) a = fmaf(sW[b * Q + p * J2 + q], sGc[b * Q + t * J2 + q], a);
+            A.curv_out[(int64_t)(k0 + b) * J1 * J1 + p * J1 + t] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // W2 = Ma Gc  (J1 x J2)
+            const int b = s / Q, p = (s % Q) / J2, q = s % J2;
+            float a = 0.f;
+            for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sGc[b * Q + pp * J2 + q], a);
+            sW[s] = a;
+        }
+        __syncthreads();
+        float *C2 = A.curv_out + (int64_t)I3 * J1 * J1;
+        for (int s = tid; s < nkb * J2 * J2; s += blockDim.x) {  // C2 = Gc^T W2
+            const int b = s / (J2 * J2), q = (s / J2) % J2, t = s % J2;
+            float a = 0.f;
+            for (int p = 0; p < J1; ++p) a = fmaf(sGc[b * Q + p * J2 + q], sW[b * Q + p * J2 + t], a);
+            C2[(int64_t)(k0 + b) * J2 * J2 + q * J2 + t] = a;
+        }
+        __syncthreads();
     }
-    for (int s = tid; s < I3 * J3; s += blockDim.x) A.U3[s] = sC[s] - sDel[s];
-    __syncthreads();
-    for (int s = tid; s < I3 * Q; s += blockDim.x) A.macc[s] = 0.f;
-    for (int s = tid; s < J1 * J1 + J2 * J2; s += blockDim.x) A.gram_in[s] = 0.f;
+    if (do_step)
+        for (int s = tid; s < J1 * J1 + J2 * J2; s += blockDim.x) A.gram_in[s] = 0.f;
 }
 
-// End of a wave: CTA 0 takes the proximal step of the core and platform rows (curvature from
-// the previous wave's moments, gram_prev); CTAs 1.. update the patient and gene rows and
-// accumulate the new moments into gram_next.  With do_dense = 0 only the moments are formed
-// (set-up: every accumulator is zero, so no row moves).
-__global__ void __launch_bounds__(256)
-    k_fast_wave_end(DenseArgs A, int do_dense, float *__restrict__ U1, float *__restrict__ U2,
-                    float *__restrict__ gA, float *__restrict__ gB, const int32_t *__restrict__ cnt1,
-                    const int32_t *__restrict__ cnt2, float inv_n, int32_t nb1,
-                    float *__restrict__ gram_next) {
+struct RowArgs {
+    float *U1, *U2, *gA, *gB;
+    int32_t rs1, rs2;
+    const int32_t *cnt1, *cnt2;
+    float inv_n;
+    int32_t nb1;
+    const float *curv_in;
+    float *gram_out;
+};
+
+// End of a wave.  mode 0: CTA 0 = core and platform rows (curvature from the previous wave's
+// moments) + next curvatures, CTAs 1.. = patient and gene rows (curvatures of the previous
+// wave) + new moments.  mode 1 (set-up): rows form moments only.  mode 2 (set-up): CTA 0
+// forms the curvatures only.
+__global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
     extern __shared__ __align__(16) float smw[];
     if (blockIdx.x == 0) {
-        if (do_dense) wave_dense(A, smw);
+        if (mode != 1) wave_dense(A, mode == 0, smw);
         return;
     }
-    wave_rows(blockIdx.x - 1, U1, U2, gA, gB, cnt1, cnt2, A.d, 1.f / A.lr, inv_n, nb1, gram_next, smw,
-              smw + kGramRows * kMaxRank);
+    wave_rows(blockIdx.x - 1, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, A.d, A.lam,
+              1.f / A.lr, R.inv_n, R.nb1, R.curv_in, R.gram_out, smw);
 }
 
 template <int CJ1, int CJ2, int CJ3>
@@ -454,6 +670,8 @@ cudaError_t init_sweep(Ctx *c) {
     return cudaSuccess;
 }
 
+int row_stride(int J, int I3) { return ((J + 3) & ~3) + ((I3 + 3) & ~3); }
+
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_sweep(Ctx *c, int64_t w) {
     const int64_t t0 = c->wave_tile[w], nt = c->wave_tile[w + 1] - t0;
@@ -475,6 +693,8 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     A.macc = c->macc;
     A.gA = c->gacc[0];
     A.gB = c->gacc[1];
+    A.rs1 = row_stride(c->d.J1, c->d.I3);
+    A.rs2 = row_stride(c->d.J2, c->d.I3);
     if (nt == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(c->fast_grid, nt);
     k_fast_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
@@ -484,34 +704,53 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
 
 size_t wave_end_smem(const Ctx *c) {
     const Dims &d = c->d;
-    const size_t dense = 3 * (size_t)c->PI + 3 * d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + 4;
-    const size_t rows = (size_t)kGramRows * kMaxRank + kGramRows;
+    const size_t tiles = 9 * (size_t)kMaxRank * kTileStride;
+    const size_t dense = 3 * (size_t)c->PI + 3 * d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + tiles;
+    const size_t rows = kRowWarps * ((size_t)kMaxRank * kTileStride + 2 * kMaxRank) +
+                        kRowWarps * (size_t)kMaxRank * kMaxRank + kCkStage;
     return sizeof(float) * std::max(dense, rows);
 }
 
-DenseArgs dense_args(Ctx *c, int64_t w, int parity) {
+int64_t curv_stride(const Ctx *c) {
+    return ((int64_t)c->d.I3 * (c->d.J1 * c->d.J1 + c->d.J2 * c->d.J2) + 3) & ~(int64_t)3;
+}
+
+cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
+    const Dims &d = c->d;
+    const int nb1 = ceil_div(d.I1, kRowsPerCta), nb2 = ceil_div(d.I2, kRowsPerCta);
     DenseArgs A;
-    A.d = c->d;
+    A.d = d;
     A.G = c->G;
     A.U3 = c->U[2];
     A.cnt3 = c->cnt[2];
     A.macc = c->macc;
     A.gram_in = c->gram + (size_t)(parity ^ 1) * c->gram_stride;
-    A.eigvec = c->gram + 2 * (size_t)c->gram_stride;
-    A.nk = c->wave_nk + (w >= 0 ? w : 0) * c->d.I3;
+    A.eigv = c->gram + 2 * (size_t)c->gram_stride;
+    A.curv_out = c->curv + (size_t)parity * curv_stride(c);
+    A.nk = c->wave_nk + (w >= 0 ? w : 0) * d.I3;
     A.n_wave = w >= 0 ? (float)c->wave_len[w] : 0.f;
     A.lam = c->cfg.lambda;
     A.lr = c->cfg.lr;
     A.lam_core = c->nnz ? c->cfg.lambda / (float)c->nnz : 0.f;
-    return A;
-}
-
-cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int do_dense) {
-    const Dims &d = c->d;
-    const int nb1 = ceil_div(d.I1, kGramRows), nb2 = ceil_div(d.I2, kGramRows);
-    k_fast_wave_end<<<1 + nb1 + nb2, 256, wave_end_smem(c), c->stream>>>(
-        dense_args(c, w, parity), do_dense, c->U[0], c->U[1], c->gacc[0], c->gacc[1], c->cnt[0], c->cnt[1],
-        c->nnz ? 1.f / (float)c->nnz : 0.f, nb1, c->gram + (size_t)parity * c->gram_stride);
+    RowArgs R;
+    R.U1 = c->U[0];
+    R.U2 = c->U[1];
+    R.gA = c->gacc[0];
+    R.gB = c->gacc[1];
+    R.rs1 = row_stride(d.J1, d.I3);
+    R.rs2 = row_stride(d.J2, d.I3);
+    R.cnt1 = c->cnt[0];
+    R.cnt2 = c->cnt[1];
+    R.inv_n = c->nnz ? 1.f / (float)c->nnz : 0.f;
+    R.nb1 = nb1;
+    R.curv_in = c->curv + (size_t)(parity ^ 1) * curv_stride(c);
+    R.gram_out = c->gram + (size_t)parity * c->gram_stride;
+    if (mode == 2) {  // set-up: curvatures from the moments just formed into buffer `parity`
+        A.gram_in = c->gram + (size_t)parity * c->gram_stride;
+        A.curv_out = c->curv + (size_t)parity * curv_stride(c);
+    }
+    const unsigned grid = mode == 2 ? 1u : (unsigned)(1 + nb1 + nb2);
+    k_fast_wave_end<<<grid, 256, wave_end_smem(c), c->stream>>>(A, R, mode);
     c->launches++;
     return cudaGetLastError();
 }
@@ -523,21 +762,26 @@ int init_fast(Ctx *c) {
     SNECT_CUDA(c, cudaMalloc((void **)&c->tile_ctr, sizeof(int32_t) * std::max<int64_t>(1, c->n_waves)));
     SNECT_CUDA(c, cudaMalloc((void **)&c->macc, sizeof(float) * d.I3 * d.J1 * d.J2));
     SNECT_CUDA(c, cudaMemsetAsync(c->macc, 0, sizeof(float) * d.I3 * d.J1 * d.J2, c->stream));
-    // moments: two buffers (this wave's, the previous wave's) + 3 eigenvector warm starts
+    // moments: two buffers (this wave's, the previous wave's) + warm-start eigenvectors
     c->gram_stride = ((int64_t)d.J1 * d.J1 + d.J2 * d.J2 + 3) & ~3;
-    const int64_t gf = 2 * c->gram_stride + 3 * kMaxRank;
+    const int64_t gf = 2 * c->gram_stride + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3;
     SNECT_CUDA(c, cudaMalloc((void **)&c->gram, sizeof(float) * gf));
     SNECT_CUDA(c, cudaMemsetAsync(c->gram, 0, sizeof(float) * gf, c->stream));
+    // platform curvatures for the row steps, two buffers
+    SNECT_CUDA(c, cudaMalloc((void **)&c->curv, sizeof(float) * 2 * curv_stride(c)));
+    SNECT_CUDA(c, cudaMemsetAsync(c->curv, 0, sizeof(float) * 2 * curv_stride(c), c->stream));
     for (int n = 0; n < 2; ++n) {
-        const int64_t nf = (int64_t)(n ? d.I2 : d.I1) * ((((n ? d.J2 : d.J1) + 4)) & ~3);
+        const int64_t nf = (int64_t)(n ? d.I2 : d.I1) * row_stride(n ? d.J2 : d.J1, d.I3);
         SNECT_CUDA(c, cudaMalloc((void **)&c->gacc[n], sizeof(float) * nf));
         SNECT_CUDA(c, cudaMemsetAsync(c->gacc[n], 0, sizeof(float) * nf, c->stream));
     }
     SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
     SNECT_CUDA(c, cudaFuncSetAttribute(k_fast_wave_end, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)wave_end_smem(c)));
-    // the first wave's curvature: moments of the initial rows into the odd buffer
-    SNECT_CUDA(c, launch_wave_end(c, -1, 1, 0));
+    // the first wave's curvature: moments of the initial rows into the odd buffer, then the
+    // platform curvatures from them
+    SNECT_CUDA(c, launch_wave_end(c, -1, 1, 1));
+    SNECT_CUDA(c, launch_wave_end(c, -1, 1, 2));
     return timing_events(c, c->n_waves);
 }
 
@@ -550,7 +794,7 @@ int enqueue_fast_epoch(Ctx *c) {
         SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[w], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, run_sweep, c, w));
         SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[w], c->stream, cudaEventRecordExternal));
-        SNECT_CUDA(c, launch_wave_end(c, w, (int)(w & 1), 1));
+        SNECT_CUDA(c, launch_wave_end(c, w, (int)(w & 1), 0));
     }
     return SNECT_OK;
 }
@@ -567,6 +811,7 @@ void free_fast(Ctx *c) {
     f(c->wave_nk);
     f(c->macc);
     f(c->gram);
+    f(c->curv);
     f(c->gacc[0]);
     f(c->gacc[1]);
 }

@@ -1,0 +1,86 @@
+"""Continuous-batching fold-in + top-k service (snect_serve_*), through the C ABI.
+
+Each query's result must be the same alone (snect_foldin + snect_topk on the context) and in
+a mix of concurrent queries: the kernels and their CTA partition depend only on the query, so
+the tolerance is exact equality.  Admission follows the device-memory budget.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import snect_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def request_bytes(n, J1):
+    return 12 * n + 4 * math.ceil(n / 4096) * (J1 * J1 + J1)
+
+
+@pytest.fixture(scope="module")
+def served(gpu_lib):
+    import paper_1711_08095_gb300 as snect
+
+    m = S.serving_model(I=(1200, 3000, 5), J=(16, 16, 5))
+    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
+    c = snect.Snect((1200, 3000, 5), m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32),
+                    np.zeros(0, np.float32), m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
+    queries = [S.serving_query(m, q=q, lo=500, hi=15000) for q in range(40)]
+    alone = []
+    for jk, x, _ in queries:
+        u = c.foldin(jk, x)
+        i, sc = c.topk(u, 10)
+        alone.append((u, i, sc))
+    yield m, c, queries, alone
+    c.close()
+
+
+def test_results_are_the_same_alone_and_in_the_mix(served):
+    m, c, queries, alone = served
+    srv = c.serve(n_slots=6, mem_budget_bytes=64 << 20, max_cells=15000)
+    tickets = [srv.submit(jk, x, 10) for jk, x, _ in queries]
+    for t, (u0, i0, s0) in zip(tickets, alone):
+        u, i, sc, lat = srv.poll(t, 10)
+        assert np.array_equal(u, u0) and np.array_equal(i, i0) and np.array_equal(sc, s0)
+        assert lat > 0
+    st = srv.stats()
+    srv.stop()
+    assert st["admitted"] == st["completed"] == len(queries)
+    assert st["max_concurrent"] > 1  # requests overlapped on the device
+
+
+def test_admission_follows_the_memory_budget(served):
+    m, c, queries, alone = served
+    big = max(len(x) for _, x, _ in queries)
+    # room for exactly one request of the largest size at a time
+    srv = c.serve(n_slots=6, mem_budget_bytes=request_bytes(15000, 16), max_cells=15000)
+    tickets = [srv.submit(jk, x, 10) for jk, x, _ in queries[:12]]
+    for t, (u0, _, _) in zip(tickets, alone[:12]):
+        u, _, _, _ = srv.poll(t, 10)
+        assert np.array_equal(u, u0)
+    st = srv.stats()
+    srv.stop()
+    assert st["completed"] == 12
+    assert big <= 15000
+
+
+def test_bad_requests(served):
+    import paper_1711_08095_gb300 as snect
+
+    m, c, queries, _ = served
+    with pytest.raises(snect.SnectError):
+        c.serve(n_slots=2, mem_budget_bytes=1000, max_cells=15000)  # below one largest request
+    srv = c.serve(n_slots=2, mem_budget_bytes=64 << 20, max_cells=1000)
+    jk, x, _ = queries[0]
+    with pytest.raises(snect.SnectError):
+        srv.submit(jk, x, 10)  # more cells than max_cells
+    bad = jk[:50].copy()
+    bad[3, 0] = 10 ** 6
+    t = srv.submit(bad, x[:50], 10)
+    with pytest.raises(snect.SnectError):
+        srv.poll(t, 10)
+    t = srv.submit(jk[:50], x[:50], 10)  # the server keeps serving
+    u, _, _, _ = srv.poll(t, 10)
+    assert np.isfinite(u).all()
+    srv.stop()
