@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="a small problem of the same shape (for profiling)")
     ap.add_argument("--serve-queries", type=int, default=20000, help="fold-in + top-k queries (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, queries/s")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32 vs BF16 refit at 16x16x5")
     return ap.parse_args()
 
 
@@ -134,6 +135,21 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def aggregate(ms_local, units_local, dist=None, device=None):
+    """Whole-job throughput over the ranks: every rank's units over the slowest rank's time
+    (max over ranks of the timed region).  Returns (max ms, total units, units/s)."""
+    if dist is None:
+        return ms_local, units_local, units_local / (ms_local / 1e3)
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms, units = float(t.item()), float(u.item())
+    return ms, units, units / (ms / 1e3)
 
 
 def dist_setup(n):
@@ -225,6 +241,42 @@ def serving(args, snect):
             "paper_context_ms_per_query": 550.0}
 
 
+def precision_form(p, snect, epochs=10):
+    """Precision form: the same paper-scale tensor refit at core ranks 16 x 16 x 5, the FP32
+    sweep against the BF16 tensor-core sweep (FP32 accumulation, FP32 master factors) from the
+    same start; nnz-updates/s per epoch (CUDA events on the library's stream) and test RMSE."""
+    import snect_synth as S
+    import torch
+
+    G0, U0 = S.init_params(p.I, (16, 16, 5), 2003)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    out = {}
+    for name, prec in (("fp32", snect.FP32), ("bf16", snect.BF16)):
+        c = snect.Snect(p.I, (16, 16, 5), t(p.idx), t(p.val), t(p.edges), t(p.w), t(G0), [t(u) for u in U0],
+                        lam=p.lam, lam_g=p.lam_g, lr=p.lr, batch=0, precision=prec)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.epoch(1)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0.record(st)
+        c.epoch(epochs - 1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (epochs - 1)
+        sw_ms, sw_n = c.sweep_times()
+        l = c.loss(t(p.test_idx), t(p.test_val))
+        out[name] = {"nnz_updates_per_s": p.nnz / (ms / 1e3), "ms_per_epoch": ms,
+                     "sweep_kernel_ms_per_epoch": sw_ms, "rmse_test_after_%d_epochs" % epochs: l["rmse_test"]}
+        c.close()
+    out["bf16_vs_fp32_throughput"] = out["bf16"]["nnz_updates_per_s"] / out["fp32"]["nnz_updates_per_s"]
+    key = "rmse_test_after_%d_epochs" % epochs
+    out["bf16_rmse_relative_to_fp32"] = out["bf16"][key] / out["fp32"][key] - 1.0
+    out["workload"] = ("paper-scale tensor (27M train entries) refit at core 16x16x5, same start for both; "
+                       "%d epochs" % epochs)
+    return out
+
+
 def quality(loss, job_loss, job_epochs, epochs_run, small):
     """Test RMSE of the e2e jobs (10 epochs from the initial factors) beside the oracle's after
     the same 10 sequential epochs (tests/golden/config2_oracle.json, written from oracle/)."""
@@ -304,18 +356,14 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = ctx.launches - l0
-    ms = ev0.elapsed_time(ev1)
+    ms, _, value = aggregate(ev0.elapsed_time(ev1), p.nnz * args.steps, dist, dev)
     if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     sweep_ms, sweep_n = ctx.sweep_times()  # sweep kernels of the last timed epoch
     loss = ctx.loss(t(p.test_idx), t(p.test_val))
     ctx.close()
     del ctx
     torch.cuda.synchronize()
-    value = p.nnz * args.steps * world / (ms / 1e3)
 
     # ---- end to end through the C ABI from pinned host buffers ---------------------------
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
@@ -368,6 +416,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0 and not args.no_precision:
+        line["precision_form"] = precision_form(p, snect)
     if rank == 0 and args.serve_queries > 0:
         line["serving"] = serving(args, snect)
     if rank == 0:

@@ -56,7 +56,9 @@ typedef struct {
                           entries (<= 4096); 0: fast mode (lock-free sweep) */
     int32_t wave;      /* fast mode: entries between two updates of the core and the
                           platform factor (0 = library default) */
-    int32_t precision; /* SNECT_FP32 (SNECT_BF16 reserved) */
+    int32_t precision; /* SNECT_FP32, or SNECT_BF16: fast mode with J1, J2 in {16, 32}; the
+                          sweep's contractions run on the tensor cores with BF16 operands and
+                          FP32 accumulation, every factor stays FP32 */
     uint64_t seed;     /* reserved; the caller supplies the visit order and the init */
 } snect_config;
 

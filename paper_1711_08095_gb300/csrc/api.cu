@@ -101,7 +101,11 @@ int check_config(const snect_config *cfg, std::string *why) {
     if (!isfinite(cfg->lr) || cfg->lr <= 0.f) return *why = "lr must be finite and > 0", SNECT_EINVAL;
     if (cfg->batch < 0 || cfg->batch > kMaxBatch) return *why = "batch must be in [0, 4096]", SNECT_EINVAL;
     if (cfg->wave < 0) return *why = "wave must be >= 0", SNECT_EINVAL;
-    if (cfg->precision != SNECT_FP32) return *why = "only SNECT_FP32 is available", SNECT_EINVAL;
+    if (cfg->precision != SNECT_FP32 && cfg->precision != SNECT_BF16)
+        return *why = "precision must be SNECT_FP32 or SNECT_BF16", SNECT_EINVAL;
+    if (cfg->precision == SNECT_BF16 &&
+        (cfg->batch != 0 || (cfg->J[0] != 16 && cfg->J[0] != 32) || (cfg->J[1] != 16 && cfg->J[1] != 32)))
+        return *why = "SNECT_BF16 needs fast mode (batch = 0) and J1, J2 in {16, 32}", SNECT_EINVAL;
     return SNECT_OK;
 }
 
@@ -375,6 +379,11 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     if (d_val) cudaFreeAsync(d_val, c->stream);
     if (trec) cudaFreeAsync(trec, c->stream);
     if (rc) return rc;
+    if (c->cfg.precision == SNECT_BF16) {  // a tensor-core wait that gave up
+        int32_t tc_err = 0;
+        SNECT_CUDA(c, cudaMemcpy(&tc_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a tensor-core completion wait timed out in the sweep");
+    }
     const double lam = c->cfg.lambda, lg = c->cfg.lambda_g;
     out->data = 0.5 * acc[0];
     out->reg = 0.5 * lam * acc[2];

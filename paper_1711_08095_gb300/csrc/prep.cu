@@ -38,14 +38,28 @@ __global__ void k_pack(const int32_t *__restrict__ idx, const float *__restrict_
     out[e] = r;
 }
 
-__global__ void k_counts(const Rec *__restrict__ rec, int64_t n, int32_t *c1, int32_t *c2,
+// per-row counts; the platform counts (few, heavily shared rows) go through a per-CTA
+// shared-memory histogram first
+__global__ void k_counts(const Rec *__restrict__ rec, int64_t n, int32_t I3, int32_t *c1, int32_t *c2,
                          int32_t *c3) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    Rec r = rec[e];
-    atomicAdd(c1 + r.i, 1);
-    atomicAdd(c2 + r.j, 1);
-    atomicAdd(c3 + r.k, 1);
+    __shared__ int32_t h3[kMaxPlatforms];
+    const bool small3 = I3 <= kMaxPlatforms;
+    for (int t = threadIdx.x; t < kMaxPlatforms; t += blockDim.x) h3[t] = 0;
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) {
+        const Rec r = rec[e];
+        atomicAdd(c1 + r.i, 1);
+        atomicAdd(c2 + r.j, 1);
+        if (small3)
+            atomicAdd(h3 + r.k, 1);
+        else
+            atomicAdd(c3 + r.k, 1);
+    }
+    __syncthreads();
+    if (small3)
+        for (int t = threadIdx.x; t < I3; t += blockDim.x)
+            if (h3[t]) atomicAdd(c3 + t, h3[t]);
 }
 
 // key = (batch << 32) | row of the given mode; value = entry position
@@ -129,11 +143,28 @@ __global__ void k_permute(const Rec *__restrict__ src, const int32_t *__restrict
     dst[e] = src[perm[e]];
 }
 
+// entries per (wave, platform); a CTA's 1,024 entries span at most two waves when
+// wave >= 1,024, so each CTA first counts into a shared histogram of 2 x I3 bins
 __global__ void k_wave_hist(const Rec *__restrict__ rec, int64_t n, int64_t wave, int32_t I3,
                             int32_t *hist) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    atomicAdd(hist + (e / wave) * I3 + rec[e].k, 1);
+    __shared__ int32_t h[2 * kMaxPlatforms];
+    const int64_t e0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t w0 = e0 / wave;
+    for (int t = threadIdx.x; t < 2 * kMaxPlatforms; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const int64_t e = e0 + threadIdx.x;
+    if (e < n) {
+        const int64_t dw = e / wave - w0;
+        if (dw < 2)
+            atomicAdd(h + dw * I3 + rec[e].k, 1);
+        else
+            atomicAdd(hist + (e / wave) * I3 + rec[e].k, 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * I3; t += blockDim.x) {
+        const int64_t w = w0 + t / I3;
+        if (h[t]) atomicAdd(hist + w * I3 + t % I3, h[t]);
+    }
 }
 
 std::string flag_message(int32_t f) {
@@ -202,8 +233,8 @@ int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val) {
         SNECT_CUDA(c, cudaMemsetAsync(c->cnt[md], 0, sizeof(int32_t) * In, c->stream));
     }
     if (c->nnz) {
-        k_counts<<<ceil_div(c->nnz, 256), 256, 0, c->stream>>>(c->rec, c->nnz, c->cnt[0], c->cnt[1],
-                                                               c->cnt[2]);
+        k_counts<<<ceil_div(c->nnz, 1024), 1024, 0, c->stream>>>(c->rec, c->nnz, c->d.I3, c->cnt[0], c->cnt[1],
+                                                                 c->cnt[2]);
         c->launches++;
         SNECT_CUDA(c, cudaGetLastError());
     }
@@ -328,7 +359,7 @@ int prep_fast_tiles(Ctx *c) {
         k_permute<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, vals2, n, tmp);
         cudaMemcpyAsync(c->rec, tmp, sizeof(Rec) * n, cudaMemcpyDeviceToDevice, c->stream);
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * c->n_waves * I3, c->stream);
-        k_wave_hist<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, I3, hist);
+        k_wave_hist<<<ceil_div(n, 1024), 1024, 0, c->stream>>>(c->rec, n, W, I3, hist);
         c->launches += 2;
     }
     std::vector<int32_t> h((size_t)c->n_waves * I3);

@@ -31,6 +31,7 @@
 // M_k is accumulated per CTA in registers over staged tiles (one thread per 2 x 2 block and
 // entry slice) and merged into global memory once per platform change.
 #include "contract.cuh"
+#include "tc.cuh"
 
 namespace snect {
 
@@ -54,6 +55,7 @@ struct FastArgs {
     float *macc;
     float *gA, *gB;  // per row: gradient sums (J_n, padded to 4) + entries per platform
     int32_t rs1, rs2;  // row strides of gA, gB
+    int32_t *err;      // set when a tensor-core wait gives up
 };
 
 template <int CJ1, int CJ2, int CJ3>
@@ -128,23 +130,57 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
             float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
             const float *ua = A.U1 + (int64_t)e.i * J1;
             const float *ub = A.U2 + (int64_t)e.j * J2;
+            // rows of even compile-time length load as float2 (row starts are 8-byte aligned)
+            if constexpr (CJ1 > 0 && CJ1 % 2 == 0) {
 #pragma unroll
-            for (int p = 0; p < J1; ++p) a[p] = __ldcg(ua + p);
+                for (int p = 0; p < CJ1; p += 2) {
+                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ua + p));
+                    a[p] = t2.x;
+                    a[p + 1] = t2.y;
+                }
+            } else {
 #pragma unroll
-            for (int q = 0; q < J2; ++q) {
-                b[q] = __ldcg(ub + q);
-                w2[q] = 0.f;
+                for (int p = 0; p < J1; ++p) a[p] = __ldcg(ua + p);
+            }
+            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {
+#pragma unroll
+                for (int q = 0; q < CJ2; q += 2) {
+                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ub + q));
+                    b[q] = t2.x;
+                    b[q + 1] = t2.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < J2; ++q) b[q] = __ldcg(ub + q);
             }
 #pragma unroll
-            for (int p = 0; p < J1; ++p) {
-                float vp = 0.f;
+            for (int q = 0; q < J2; ++q) w2[q] = 0.f;
+            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {  // Gc read as float2 pairs (broadcast)
 #pragma unroll
-                for (int q = 0; q < J2; ++q) {
-                    const float g = sGc[p * J2 + q];
-                    vp = fmaf(g, b[q], vp);
-                    w2[q] = fmaf(a[p], g, w2[q]);
+                for (int p = 0; p < CJ1; ++p) {
+                    float vp = 0.f;
+#pragma unroll
+                    for (int q = 0; q < CJ2; q += 2) {
+                        const float2 g = *reinterpret_cast<const float2 *>(sGc + p * CJ2 + q);
+                        vp = fmaf(g.x, b[q], vp);
+                        vp = fmaf(g.y, b[q + 1], vp);
+                        w2[q] = fmaf(a[p], g.x, w2[q]);
+                        w2[q + 1] = fmaf(a[p], g.y, w2[q + 1]);
+                    }
+                    v[p] = vp;
                 }
-                v[p] = vp;
+            } else {
+#pragma unroll
+                for (int p = 0; p < J1; ++p) {
+                    float vp = 0.f;
+#pragma unroll
+                    for (int q = 0; q < J2; ++q) {
+                        const float g = sGc[p * J2 + q];
+                        vp = fmaf(g, b[q], vp);
+                        w2[q] = fmaf(a[p], g, w2[q]);
+                    }
+                    v[p] = vp;
+                }
             }
             float xt = 0.f;
 #pragma unroll
@@ -203,6 +239,202 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// BF16 precision form of the sweep on the tensor cores (tcgen05, accumulators in TMEM).
+//
+// Same wave semantics and FP32 accumulators as k_fast_sweep; the three products of a tile
+// of 128 entries run as BF16 x BF16 -> FP32 matrix products:
+//   V  = B_tile Gc^T    (128 x J1, K = J2)      v_e  = Gc b_e
+//   W2 = A_tile Gc      (128 x J2, K = J1)      w2_e = Gc^T a_e
+//   M_k += (r A)^T B    (J1 x J2, K = 128)      accumulated in TMEM across the platform's tiles
+// The gathered rows a, b and Gc = G x3 c_k are rounded to BF16 for the products; x~ = a . v,
+// the residual, the row gradients and every update stay FP32 (FP32 master factors).  One
+// thread issues the MMAs; tcgen05.commit arrives on an mbarrier that all threads wait on.
+template <int CJ1, int CJ2>
+__global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
+    constexpr int J1 = CJ1, J2 = CJ2, M = 128;
+    constexpr int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
+    const int J3 = A.d.J3, PI = J1 * J2 * J3;
+    extern __shared__ __align__(1024) uint8_t smb[];
+    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smb);             // M x J1
+    __nv_bfloat16 *sB = sA + M * J1;                                          // M x J2
+    __nv_bfloat16 *sBT = sB + M * J2;                                         // J2 x M
+    __nv_bfloat16 *sRAT = sBT + J2 * M;                                       // M x M (rows < J1 used)
+    __nv_bfloat16 *bGc = sRAT + M * M;                                        // J1 x J2
+    __nv_bfloat16 *bGcT = bGc + J1 * J2;                                      // J2 x J1
+    float *sG = reinterpret_cast<float *>(bGcT + J2 * J1);                    // PI
+    __shared__ __align__(8) uint64_t mbar_vw, mbar_m;
+    __shared__ uint32_t tmem_base;
+    __shared__ int sTile;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc::smem_u32(&tmem_base)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mbar_vw);
+        tc::mbar_init(&mbar_m);
+    }
+    for (int t = tid; t < PI; t += M) sG[t] = A.G[t];
+    for (int t = tid; t < M * M / 2; t += M) reinterpret_cast<uint32_t *>(sRAT)[t] = 0u;
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t t_v = tmem, t_w = tmem + 32, t_m = tmem + 64;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    uint32_t ph_vw = 0, ph_m = 0;
+    bool m_started = false, failed = false;
+    int cur_k = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sTile = atomicAdd(A.ctr, 1);
+        __syncthreads();
+        const int t = sTile;
+        const bool done = t >= A.n_tiles;
+        const int k = done ? -1 : A.tile_k[t];
+        if (k != cur_k) {
+            if (cur_k >= 0 && m_started) {  // merge this CTA's M_k (rows p < J1 in lanes 0..J1-1)
+                tc::fence_after();
+                if (warp < (J1 + 31) / 32) {
+                    float mv[J2];
+#pragma unroll
+                    for (int c0 = 0; c0 < J2; c0 += 16) tc::ld16(t_m + lane_off + c0, mv + c0);
+                    const int p = warp * 32 + (tid & 31);
+                    if (p < J1)
+#pragma unroll
+                        for (int q = 0; q < J2; ++q) atomicAdd(A.macc + ((int64_t)cur_k * J1 + p) * J2 + q, mv[q]);
+                }
+                m_started = false;
+            }
+            if (done || failed) break;
+            const float *ck = A.U3 + (int64_t)k * J3;
+            for (int s = tid; s < J1 * J2; s += M) {
+                const int p = s / J2, q = s % J2;
+                float g = 0.f;
+                for (int r = 0; r < J3; ++r) g = fmaf(sG[s * J3 + r], ck[r], g);
+                const __nv_bfloat16 gb = __float2bfloat16(g);
+                *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<uint8_t *>(bGc) + tc::kmajor_off(p, q, J2)) = gb;
+                *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<uint8_t *>(bGcT) + tc::kmajor_off(q, p, J1)) = gb;
+            }
+            cur_k = k;
+        }
+        const int n_e = A.tile_len[t];
+        for (int h = 0; h < 2 && h * M < n_e; ++h) {
+            const int el = h * M + tid;
+            const bool valid = el < n_e;
+            float a[J1], b[J2];
+            float x = 0.f;
+            int ei = 0, ej = 0;
+            if (valid) {
+                const Rec e = A.rec[A.tile_start[t] + el];
+                ei = e.i;
+                ej = e.j;
+                x = e.x;
+                const float4 *ua = reinterpret_cast<const float4 *>(A.U1 + (int64_t)e.i * J1);
+                const float4 *ub = reinterpret_cast<const float4 *>(A.U2 + (int64_t)e.j * J2);
+#pragma unroll
+                for (int p = 0; p < J1 / 4; ++p) {
+                    const float4 t4 = __ldcg(ua + p);
+                    a[4 * p] = t4.x, a[4 * p + 1] = t4.y, a[4 * p + 2] = t4.z, a[4 * p + 3] = t4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < J2 / 4; ++q) {
+                    const float4 t4 = __ldcg(ub + q);
+                    b[4 * q] = t4.x, b[4 * q + 1] = t4.y, b[4 * q + 2] = t4.z, b[4 * q + 3] = t4.w;
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < J1; ++p) a[p] = 0.f;
+#pragma unroll
+                for (int q = 0; q < J2; ++q) b[q] = 0.f;
+            }
+            uint8_t *pa = reinterpret_cast<uint8_t *>(sA), *pb = reinterpret_cast<uint8_t *>(sB);
+            uint8_t *pbt = reinterpret_cast<uint8_t *>(sBT), *prt = reinterpret_cast<uint8_t *>(sRAT);
+#pragma unroll
+            for (int p = 0; p < J1; p += 2)
+                *reinterpret_cast<__nv_bfloat162 *>(pa + tc::kmajor_off(tid, p, J1)) = __floats2bfloat162_rn(a[p], a[p + 1]);
+#pragma unroll
+            for (int q = 0; q < J2; q += 2)
+                *reinterpret_cast<__nv_bfloat162 *>(pb + tc::kmajor_off(tid, q, J2)) = __floats2bfloat162_rn(b[q], b[q + 1]);
+#pragma unroll
+            for (int q = 0; q < J2; ++q)
+                *reinterpret_cast<__nv_bfloat16 *>(pbt + tc::kmajor_off(q, tid, M)) = __float2bfloat16(b[q]);
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            if (tid == 0) {
+                tc::mma_kmajor(t_v, tc::smem_u32(sB), tc::smem_u32(bGc), J2, J1, false);
+                tc::mma_kmajor(t_w, tc::smem_u32(sA), tc::smem_u32(bGcT), J1, J2, false);
+                tc::commit(&mbar_vw);
+            }
+            const bool ok1 = tc::mbar_wait(&mbar_vw, ph_vw);
+            ph_vw ^= 1u;
+            tc::fence_after();
+            float v[J1], w2[J2];
+#pragma unroll
+            for (int c0 = 0; c0 < J1; c0 += 16) tc::ld16(t_v + lane_off + c0, v + c0);
+#pragma unroll
+            for (int c0 = 0; c0 < J2; c0 += 16) tc::ld16(t_w + lane_off + c0, w2 + c0);
+            float r = 0.f;
+            if (valid) {
+                float xt = 0.f;
+#pragma unroll
+                for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
+                r = xt - x;
+                const float la = A.lam / (float)A.cnt1[ei], lb = A.lam / (float)A.cnt2[ej];
+                float *ga = A.gA + (int64_t)ei * A.rs1;
+                float *gb = A.gB + (int64_t)ej * A.rs2;
+#pragma unroll
+                for (int p = 0; p < JA; p += 4) {
+                    float g4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) g4[u] = (p + u < J1) ? fmaf(r, v[p + u], la * a[p + u]) : 0.f;
+                    atomicAdd(reinterpret_cast<float4 *>(ga + p), make_float4(g4[0], g4[1], g4[2], g4[3]));
+                }
+#pragma unroll
+                for (int q = 0; q < JB; q += 4) {
+                    float g4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) g4[u] = (q + u < J2) ? fmaf(r, w2[q + u], lb * b[q + u]) : 0.f;
+                    atomicAdd(reinterpret_cast<float4 *>(gb + q), make_float4(g4[0], g4[1], g4[2], g4[3]));
+                }
+                atomicAdd(ga + JA + k, 1.f);
+                atomicAdd(gb + JB + k, 1.f);
+            }
+#pragma unroll
+            for (int p = 0; p < J1; ++p)
+                *reinterpret_cast<__nv_bfloat16 *>(prt + tc::kmajor_off(p, tid, M)) = __float2bfloat16(r * a[p]);
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            if (tid == 0) {
+                tc::mma_kmajor(t_m, tc::smem_u32(sRAT), tc::smem_u32(sBT), M, J2, m_started);
+                tc::commit(&mbar_m);
+            }
+            m_started = true;
+            const bool ok2 = tc::mbar_wait(&mbar_m, ph_m);
+            ph_m ^= 1u;
+            if (__syncthreads_or(!(ok1 && ok2))) {
+                failed = true;
+                if (tid == 0) atomicOr(A.err, 1);
+                break;
+            }
+        }
+        if (failed) {
+            m_started = false;
+            break;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// ---------------------------------------------------------------------------------------
 // End of a wave
 
 // Every entry's residual is fitted by four parameter blocks at once (its patient row, gene row,
@@ -214,17 +446,21 @@ constexpr int kRowWarps = 8;       // warps per CTA of the row step (one row per
 constexpr int kRowsPerCta = 64;    // rows of one mode per CTA
 constexpr int kTileStride = kMaxRank + 1;
 constexpr int kCkStage = 8192;     // platform curvatures staged in shared memory up to this size
+constexpr int kMaccStage = 8192;   // a wave's M_k staged in shared memory up to this size
+// Jacobi sweeps per wave: the eigenbases of the moments drift slowly from wave to wave and
+// each decomposition starts from the previous one, so a couple of sweeps keep it tracking
+constexpr int kJacobiSweeps = 2;
+constexpr int kRowsPerThreadCta = 256;  // rows per CTA of the thread-per-row step
 
 // Patient / gene rows: u <- u - (H + (n lambda/|Omega^{n,i}| + 1/lr) I)^{-1} g with
 // H = sum_k n_ik C_k (C_k = the platform curvature of this mode), accumulators cleared; then
 // the count-weighted second moments of the updated rows (sum_i cnt_i/n u_i u_i^T) into
 // gram_out.  With do_step = 0 only the moments are formed.
-__device__ void wave_rows(int blk, int do_step, float *__restrict__ U1, float *__restrict__ U2,
+__device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ U1, float *__restrict__ U2,
                           float *__restrict__ gA, float *__restrict__ gB, int32_t rs1, int32_t rs2,
                           const int32_t *__restrict__ cnt1, const int32_t *__restrict__ cnt2,
-                          const Dims &d, float lam, float inv_lr, float inv_n, int32_t nb1,
+                          const Dims &d, float lam, float inv_lr, float inv_n,
                           const float *__restrict__ curv_in, float *__restrict__ gram_out, float *sm) {
-    const bool first = blk < nb1;
     const int J = first ? d.J1 : d.J2;
     const int JP = (J + 3) & ~3;
     const int RS = first ? rs1 : rs2;
@@ -234,7 +470,7 @@ __device__ void wave_rows(int blk, int do_step, float *__restrict__ U1, float *_
     float *g = first ? gA : gB;
     const int32_t *cnt = first ? cnt1 : cnt2;
     const float *Ckg = curv_in + (first ? 0 : (int64_t)I3 * d.J1 * d.J1);  // I3 blocks of J x J
-    const int64_t r0 = (int64_t)(first ? blk : blk - nb1) * kRowsPerCta;
+    const int64_t r0 = (int64_t)blk * kRowsPerCta;
     const int64_t left = (int64_t)I - r0;
     const int nr = left < kRowsPerCta ? (int)left : kRowsPerCta;
     if (nr <= 0) return;
@@ -320,6 +556,105 @@ __device__ void wave_rows(int blk, int do_step, float *__restrict__ U1, float *_
     }
 }
 
+// The same row step with one thread per row for a compile-time rank J <= 16: H (packed lower
+// triangle), its Cholesky factor and both triangular solves stay in registers, with no
+// synchronisation inside a row.
+template <int CJ>
+__device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, float *__restrict__ g, int32_t RS,
+                                 const int32_t *__restrict__ cnt, int32_t I, int32_t I3, float lam,
+                                 float inv_lr, float inv_n, const float *__restrict__ Ckg,
+                                 float *__restrict__ gram_out, float *sm) {
+    constexpr int J = CJ, JP = (J + 3) & ~3, NL = J * (J + 1) / 2;
+    const int64_t r0 = (int64_t)blk * kRowsPerThreadCta;
+    if (r0 >= I) return;
+    float *rows = sm;                          // kRowsPerThreadCta x J (updated rows)
+    float *wts = rows + kRowsPerThreadCta * J; // kRowsPerThreadCta
+    float *sCk = wts + kRowsPerThreadCta;      // I3 x J x J, if it fits
+    const bool stage = I3 * J * J <= kCkStage;
+    if (stage && do_step)
+        for (int e = threadIdx.x; e < I3 * J * J; e += blockDim.x) sCk[e] = Ckg[e];
+    __syncthreads();
+    const float *Ck = stage ? sCk : Ckg;
+    const int64_t row = r0 + threadIdx.x;
+    const bool valid = row < I;
+    float u[J];
+#pragma unroll
+    for (int p = 0; p < J; ++p) u[p] = valid ? U[row * J + p] : 0.f;
+    if (valid) {
+        float *acc = g + row * RS;
+        if (do_step) {
+            float n = 0.f;
+            for (int k = 0; k < I3; ++k) n += acc[JP + k];
+            if (n > 0.f) {
+                float L[NL];
+                const float diag = kBlocks * n * lam / (float)max(cnt[row], 1) + inv_lr;
+#pragma unroll
+                for (int p = 0, t = 0; p < J; ++p)
+#pragma unroll
+                    for (int q = 0; q <= p; ++q, ++t) L[t] = p == q ? diag : 0.f;
+                for (int k = 0; k < I3; ++k) {
+                    const float nk = kBlocks * acc[JP + k];
+                    if (nk > 0.f) {
+                        const float *C = Ck + (int64_t)k * J * J;
+#pragma unroll
+                        for (int p = 0, t = 0; p < J; ++p)
+#pragma unroll
+                            for (int q = 0; q <= p; ++q, ++t) L[t] = fmaf(nk, C[p * J + q], L[t]);
+                    }
+                }
+                // Cholesky (packed lower triangle, row p starts at p (p + 1) / 2)
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    float dd = L[j * (j + 1) / 2 + j];
+#pragma unroll
+                    for (int k = 0; k < j; ++k) dd -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+                    dd = sqrtf(fmaxf(dd, 1e-20f));
+                    L[j * (j + 1) / 2 + j] = dd;
+                    const float inv = 1.f / dd;
+#pragma unroll
+                    for (int i = j + 1; i < J; ++i) {
+                        float x = L[i * (i + 1) / 2 + j];
+#pragma unroll
+                        for (int k = 0; k < j; ++k) x -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+                        L[i * (i + 1) / 2 + j] = x * inv;
+                    }
+                }
+                float y[J];
+#pragma unroll
+                for (int i = 0; i < J; ++i) {
+                    float x = acc[i];
+#pragma unroll
+                    for (int k = 0; k < i; ++k) x -= L[i * (i + 1) / 2 + k] * y[k];
+                    y[i] = x / L[i * (i + 1) / 2 + i];
+                }
+#pragma unroll
+                for (int i = J - 1; i >= 0; --i) {
+                    float x = y[i];
+#pragma unroll
+                    for (int k = i + 1; k < J; ++k) x -= L[k * (k + 1) / 2 + i] * y[k];
+                    y[i] = x / L[i * (i + 1) / 2 + i];
+                }
+#pragma unroll
+                for (int p = 0; p < J; ++p) {
+                    u[p] -= y[p];
+                    U[row * J + p] = u[p];
+                }
+            }
+        }
+        for (int e = 0; e < RS; e += 4) *reinterpret_cast<float4 *>(acc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int p = 0; p < J; ++p) rows[threadIdx.x * J + p] = u[p];
+    wts[threadIdx.x] = valid ? (float)cnt[row] * inv_n : 0.f;
+    __syncthreads();
+    for (int s = threadIdx.x; s < J * J; s += blockDim.x) {
+        const int p = s / J, q = s % J;
+        float a = 0.f;
+        for (int i = 0; i < kRowsPerThreadCta; ++i) a = fmaf(wts[i] * rows[i * J + p], rows[i * J + q], a);
+        atomicAdd(gram_out + s, a);
+    }
+}
+
 // Eigen-decomposition of a symmetric n x n matrix (n <= 32) by cyclic Jacobi rotations, one
 // warp.  M (stride kTileStride) is overwritten: its diagonal ends as the eigenvalues; V
 // (stride kTileStride) holds the eigenvectors as columns.  Vwarm (n x n, global) is the
@@ -353,7 +688,7 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm) {
         }
     }
     __syncwarp();
-    for (int sweep = 0; sweep < 8; ++sweep) {
+    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
         float off = 0.f, dia = 0.f;
         for (int e = lane; e < n * n; e += 32) {
             const float x = M[(e / n) * kTileStride + e % n];
@@ -425,7 +760,12 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
     float *sMa = sDel + I3 * J3;     // J1*J1
     float *sMb = sMa + J1 * J1;      // J2*J2
     float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles for the eigen-decompositions
+    float *sMacc = sJ + 9 * kMaxRank * kTileStride;  // the wave's M_k, if they fit
     const int tid = threadIdx.x;
+    const bool stage_m = I3 * Q <= kMaccStage;
+    if (do_step && stage_m)
+        for (int s = tid; s < I3 * Q; s += blockDim.x) sMacc[s] = A.macc[s];
+    const float *Mk = stage_m ? sMacc : A.macc;
     for (int s = tid; s < PI; s += blockDim.x) sG[s] = A.G[s];
     for (int s = tid; s < I3 * J3; s += blockDim.x) sC[s] = A.U3[s];
     for (int s = tid; s < J1 * J1; s += blockDim.x) sMa[s] = A.gram_in[s];
@@ -447,7 +787,7 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
         for (int s = tid; s < I3 * J3; s += blockDim.x) {
             const int k = s / J3, r = s % J3;
             float a = 0.f;
-            const float *M = A.macc + (int64_t)k * Q;
+            const float *M = Mk + (int64_t)k * Q;
             for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
             const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
             sGk[s] = fmaf(reg, sC[s], a);
@@ -517,7 +857,7 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
         for (int s = tid; s < PI; s += blockDim.x) {
             const int pq = s / J3, r = s % J3;
             float a = 0.f;
-            for (int k = 0; k < I3; ++k) a = fmaf(A.macc[(int64_t)k * Q + pq], sC[k * J3 + r], a);
+            for (int k = 0; k < I3; ++k) a = fmaf(Mk[(int64_t)k * Q + pq], sC[k * J3 + r], a);
             sX[s] = fmaf(A.n_wave * A.lam_core, sG[s], a);
         }
         __syncthreads();
@@ -638,14 +978,57 @@ struct RowArgs {
 // moments) + next curvatures, CTAs 1.. = patient and gene rows (curvatures of the previous
 // wave) + new moments.  mode 1 (set-up): rows form moments only.  mode 2 (set-up): CTA 0
 // forms the curvatures only.
+// The row step runs one thread per row when both row ranks are compile-time (CJ1, CJ2 > 0),
+// one warp per row otherwise; R.nb1 CTAs cover the patient rows, the rest the gene rows.
+template <int CJ1, int CJ2>
 __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
     extern __shared__ __align__(16) float smw[];
     if (blockIdx.x == 0) {
         if (mode != 1) wave_dense(A, mode == 0, smw);
         return;
     }
-    wave_rows(blockIdx.x - 1, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, A.d, A.lam,
-              1.f / A.lr, R.inv_n, R.nb1, R.curv_in, R.gram_out, smw);
+    const int blk = blockIdx.x - 1;
+    const bool first = blk < R.nb1;
+    const int mb = first ? blk : blk - R.nb1;
+    const Dims &d = A.d;
+    if constexpr (CJ1 > 0 && CJ2 > 0) {
+        const float *Ckg = R.curv_in + (first ? 0 : (int64_t)d.I3 * d.J1 * d.J1);
+        float *gout = R.gram_out + (first ? 0 : d.J1 * d.J1);
+        if (first)
+            wave_rows_thread<CJ1>(mb, mode == 0, R.U1, R.gA, R.rs1, R.cnt1, d.I1, d.I3, A.lam, 1.f / A.lr,
+                                  R.inv_n, Ckg, gout, smw);
+        else
+            wave_rows_thread<CJ2>(mb, mode == 0, R.U2, R.gB, R.rs2, R.cnt2, d.I2, d.I3, A.lam, 1.f / A.lr,
+                                  R.inv_n, Ckg, gout, smw);
+    } else {
+        wave_rows(first, mb, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, d, A.lam,
+                  1.f / A.lr, R.inv_n, R.curv_in, R.gram_out, smw);
+    }
+}
+
+// compile-time row ranks of the thread-per-row step
+#define SNECT_DISPATCH_ROWS(J1, J2, FN, ...)                           \
+    (((J1) == 5 && (J2) == 5)     ? FN<5, 5>(__VA_ARGS__)              \
+     : ((J1) == 10 && (J2) == 10) ? FN<10, 10>(__VA_ARGS__)            \
+     : ((J1) == 16 && (J2) == 16) ? FN<16, 16>(__VA_ARGS__)            \
+                                  : FN<0, 0>(__VA_ARGS__))
+
+template <int CJ1, int CJ2>
+int rows_per_cta() { return (CJ1 > 0 && CJ2 > 0) ? kRowsPerThreadCta : kRowsPerCta; }
+
+template <int CJ1, int CJ2>
+cudaError_t set_wave_end_attr(Ctx *, size_t smem) {
+    return cudaFuncSetAttribute(k_fast_wave_end<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int CJ1, int CJ2>
+cudaError_t launch_wave_end_k(Ctx *c, const DenseArgs &A, RowArgs R, int mode, size_t smem) {
+    const int rpc = rows_per_cta<CJ1, CJ2>();
+    R.nb1 = ceil_div(c->d.I1, rpc);
+    const int nb2 = ceil_div(c->d.I2, rpc);
+    const unsigned grid = mode == 2 ? 1u : (unsigned)(1 + R.nb1 + nb2);
+    k_fast_wave_end<CJ1, CJ2><<<grid, 256, smem, c->stream>>>(A, R, mode);
+    return cudaGetLastError();
 }
 
 template <int CJ1, int CJ2, int CJ3>
@@ -672,6 +1055,38 @@ cudaError_t init_sweep(Ctx *c) {
 
 int row_stride(int J, int I3) { return ((J + 3) & ~3) + ((I3 + 3) & ~3); }
 
+size_t sweep_tc_smem(const Ctx *c) {
+    const size_t M = 128, J1 = c->d.J1, J2 = c->d.J2;
+    return 2 * (M * J1 + M * J2 + J2 * M + M * M + 2 * J1 * J2) + sizeof(float) * (size_t)c->PI;
+}
+
+template <int CJ1, int CJ2>
+cudaError_t init_sweep_tc(Ctx *c) {
+    const size_t smem = sweep_tc_smem(c);
+    cudaError_t e = cudaFuncSetAttribute(k_fast_sweep_tc<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast_sweep_tc<CJ1, CJ2>, 128, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return e;
+    c->fast_grid = std::max(1, std::min(per_sm, 4)) * sms;  // TMEM: 4 x 128 columns per SM
+    return cudaSuccess;
+}
+
+#define SNECT_DISPATCH_TC(J1, J2, FN, ...)                                  \
+    (((J1) == 16 && (J2) == 16)   ? FN<16, 16>(__VA_ARGS__)                 \
+     : ((J1) == 16 && (J2) == 32) ? FN<16, 32>(__VA_ARGS__)                 \
+     : ((J1) == 32 && (J2) == 16) ? FN<32, 16>(__VA_ARGS__)                 \
+                                  : FN<32, 32>(__VA_ARGS__))
+
+template <int CJ1, int CJ2>
+cudaError_t launch_sweep_tc(Ctx *c, const FastArgs &A, int grid) {
+    k_fast_sweep_tc<CJ1, CJ2><<<grid, 128, sweep_tc_smem(c), c->stream>>>(A);
+    return cudaGetLastError();
+}
+
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_sweep(Ctx *c, int64_t w) {
     const int64_t t0 = c->wave_tile[w], nt = c->wave_tile[w + 1] - t0;
@@ -695,19 +1110,24 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     A.gB = c->gacc[1];
     A.rs1 = row_stride(c->d.J1, c->d.I3);
     A.rs2 = row_stride(c->d.J2, c->d.I3);
+    A.err = c->flag + 3;
     if (nt == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(c->fast_grid, nt);
-    k_fast_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
     c->launches++;
+    if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
+    k_fast_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
     return cudaGetLastError();
 }
 
 size_t wave_end_smem(const Ctx *c) {
     const Dims &d = c->d;
     const size_t tiles = 9 * (size_t)kMaxRank * kTileStride;
-    const size_t dense = 3 * (size_t)c->PI + 3 * d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + tiles;
-    const size_t rows = kRowWarps * ((size_t)kMaxRank * kTileStride + 2 * kMaxRank) +
-                        kRowWarps * (size_t)kMaxRank * kMaxRank + kCkStage;
+    const size_t mstage = std::min<size_t>((size_t)d.I3 * d.J1 * d.J2, kMaccStage);
+    const size_t dense = 3 * (size_t)c->PI + 3 * d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + tiles +
+                         mstage;
+    const size_t rows = std::max<size_t>(kRowWarps * ((size_t)kMaxRank * kTileStride + 2 * kMaxRank) +
+                                             kRowWarps * (size_t)kMaxRank * kMaxRank + kCkStage,
+                                         (size_t)kRowsPerThreadCta * (std::max(d.J1, d.J2) + 1) + kCkStage);
     return sizeof(float) * std::max(dense, rows);
 }
 
@@ -749,10 +1169,9 @@ cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
         A.gram_in = c->gram + (size_t)parity * c->gram_stride;
         A.curv_out = c->curv + (size_t)parity * curv_stride(c);
     }
-    const unsigned grid = mode == 2 ? 1u : (unsigned)(1 + nb1 + nb2);
-    k_fast_wave_end<<<grid, 256, wave_end_smem(c), c->stream>>>(A, R, mode);
+    (void)nb2;
     c->launches++;
-    return cudaGetLastError();
+    return SNECT_DISPATCH_ROWS(d.J1, d.J2, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
 }
 
 }  // namespace
@@ -775,9 +1194,13 @@ int init_fast(Ctx *c) {
         SNECT_CUDA(c, cudaMalloc((void **)&c->gacc[n], sizeof(float) * nf));
         SNECT_CUDA(c, cudaMemsetAsync(c->gacc[n], 0, sizeof(float) * nf, c->stream));
     }
-    SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
-    SNECT_CUDA(c, cudaFuncSetAttribute(k_fast_wave_end, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)wave_end_smem(c)));
+    if (c->cfg.precision == SNECT_BF16) {
+        SNECT_CUDA(c, SNECT_DISPATCH_TC(d.J1, d.J2, init_sweep_tc, c));
+    } else {
+        SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
+    }
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag + 3, 0, sizeof(int32_t), c->stream));
+    SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, set_wave_end_attr, c, wave_end_smem(c)));
     // the first wave's curvature: moments of the initial rows into the odd buffer, then the
     // platform curvatures from them
     SNECT_CUDA(c, launch_wave_end(c, -1, 1, 1));

