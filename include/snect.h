@@ -152,6 +152,23 @@ int snect_serve_stats(snect_server *srv, int64_t *admitted, int64_t *completed, 
 /* Finishes every queued request, stops the scheduler and frees the slots. */
 int snect_serve_stop(snect_server *srv);
 
+/* Batched form: several independent decompositions (e.g. per-cohort sub-tensors, each fitted
+ * for several lambda_g) stepped together.  ctxs: n fast-mode FP32 contexts with the same core
+ * ranks and the same number of waves (a batch does not own them; they must outlive it).  One
+ * epoch of the batch is one CUDA graph: per wave, one sweep launch over the tiles of every
+ * problem and one launch of every problem's wave-end steps, then each problem's network
+ * pass.  Each context then holds its own updated factors (snect_loss, snect_get_factors).
+ * stream: a cudaStream_t or NULL (default stream); snect_batch_epoch is asynchronous.
+ * Errors: SNECT_EINVAL (mismatched contexts), SNECT_ECUDA; messages through
+ * snect_batch_last_error (NULL: the last failing snect_batch_create). */
+typedef struct snect_batch snect_batch;
+int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, void *stream);
+int snect_batch_epoch(snect_batch *batch, int32_t n_epochs);
+/* kernels the batch has launched so far (its graphs' kernel nodes) */
+int64_t snect_batch_launch_count(const snect_batch *batch);
+const char *snect_batch_last_error(const snect_batch *batch);
+void snect_batch_destroy(snect_batch *batch);
+
 /* Fold-in that allocates nothing, for callers that cannot call cudaMalloc (a process that
  * lives inside another framework's memory budget or allocator, a serving loop that must not
  * stall on the allocator, code that keeps every device buffer pre-reserved).  The paper has

@@ -36,6 +36,11 @@ EXPORTS = (
     "snect_foldin",
     "snect_topk",
     "snect_foldin_static",
+    "snect_batch_create",
+    "snect_batch_epoch",
+    "snect_batch_launch_count",
+    "snect_batch_last_error",
+    "snect_batch_destroy",
     "snect_serve_start",
     "snect_serve_submit",
     "snect_serve_poll",
@@ -119,6 +124,11 @@ def load(build_if_missing: bool = False):
         "snect_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64)]),
         "snect_serve_stop": (ctypes.c_int, [P]),
+        "snect_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(P), i32, P]),
+        "snect_batch_epoch": (ctypes.c_int, [P, i32]),
+        "snect_batch_launch_count": (ctypes.c_int64, [P]),
+        "snect_batch_last_error": (ctypes.c_char_p, [P]),
+        "snect_batch_destroy": (None, [P]),
         "snect_foldin_static": (ctypes.c_int, [P, P, P, i32, i32, i32, i32, i32, P, P, i64, ctypes.c_float, P, P]),
         "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
@@ -327,5 +337,40 @@ class Server:
     def __del__(self):
         try:
             self.stop()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several fast-mode contexts stepped together (snect_batch_*): one graph per epoch."""
+
+    def __init__(self, ctxs: Sequence["Snect"], stream=None):
+        self._lib = load()
+        self._ctxs = list(ctxs)  # kept alive while the batch exists
+        arr = (ctypes.c_void_p * len(self._ctxs))(*[c.handle.value for c in self._ctxs])
+        h = ctypes.c_void_p()
+        st = _current_stream() if stream is None else stream
+        rc = self._lib.snect_batch_create(ctypes.byref(h), arr, len(self._ctxs), st)
+        if rc != 0:
+            raise SnectError(rc, self._lib.snect_batch_last_error(None).decode())
+        self._h = h
+
+    def epoch(self, n: int = 1):
+        rc = self._lib.snect_batch_epoch(self._h, int(n))
+        if rc != 0:
+            raise SnectError(rc, self._lib.snect_batch_last_error(self._h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.snect_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.snect_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
         const int t = sTile;
         const bool done = t >= A.n_tiles;
         const int k = done ? -1 : A.tile_k[t];
-        if (k != cur_k) {
+        if (k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
             if (cur_k >= 0) {  // merge this CTA's M_k
                 if (active) {
                     float *o = sRed + (my_s * NB + my_b) * 4;
@@ -112,6 +112,214 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
                 acc0 = acc1 = acc2 = acc3 = 0.f;
             }
             if (done) break;
+            const float *ck = A.U3 + (int64_t)k * J3;
+            for (int s = tid; s < J1 * J2; s += kFastThreads) {
+                float g = 0.f;
+                for (int r = 0; r < J3; ++r) g = fmaf(sG[s * J3 + r], ck[r], g);
+                sGc[s] = g;
+            }
+            cur_k = k;
+            __syncthreads();
+        }
+        const int n_e = A.tile_len[t];
+        float *ra = sRA + tid * J1P;
+        float *bb = sB + tid * J2P;
+        if (tid < n_e) {
+            const Rec e = A.rec[A.tile_start[t] + tid];
+            float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value];
+            float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
+            const float *ua = A.U1 + (int64_t)e.i * J1;
+            const float *ub = A.U2 + (int64_t)e.j * J2;
+            // rows of even compile-time length load as float2 (row starts are 8-byte aligned)
+            if constexpr (CJ1 > 0 && CJ1 % 2 == 0) {
+#pragma unroll
+                for (int p = 0; p < CJ1; p += 2) {
+                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ua + p));
+                    a[p] = t2.x;
+                    a[p + 1] = t2.y;
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < J1; ++p) a[p] = __ldcg(ua + p);
+            }
+            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {
+#pragma unroll
+                for (int q = 0; q < CJ2; q += 2) {
+                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ub + q));
+                    b[q] = t2.x;
+                    b[q + 1] = t2.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < J2; ++q) b[q] = __ldcg(ub + q);
+            }
+#pragma unroll
+            for (int q = 0; q < J2; ++q) w2[q] = 0.f;
+            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {  // Gc read as float2 pairs (broadcast)
+#pragma unroll
+                for (int p = 0; p < CJ1; ++p) {
+                    float vp = 0.f;
+#pragma unroll
+                    for (int q = 0; q < CJ2; q += 2) {
+                        const float2 g = *reinterpret_cast<const float2 *>(sGc + p * CJ2 + q);
+                        vp = fmaf(g.x, b[q], vp);
+                        vp = fmaf(g.y, b[q + 1], vp);
+                        w2[q] = fmaf(a[p], g.x, w2[q]);
+                        w2[q + 1] = fmaf(a[p], g.y, w2[q + 1]);
+                    }
+                    v[p] = vp;
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < J1; ++p) {
+                    float vp = 0.f;
+#pragma unroll
+                    for (int q = 0; q < J2; ++q) {
+                        const float g = sGc[p * J2 + q];
+                        vp = fmaf(g, b[q], vp);
+                        w2[q] = fmaf(a[p], g, w2[q]);
+                    }
+                    v[p] = vp;
+                }
+            }
+            float xt = 0.f;
+#pragma unroll
+            for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
+            const float r = xt - e.x;
+            const float la = A.lam / (float)A.cnt1[e.i], lb = A.lam / (float)A.cnt2[e.j];
+            // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
+            constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
+            const int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
+            float gva[RA], gvb[RB];
+#pragma unroll
+            for (int p = 0; p < J1; ++p) {
+                gva[p] = fmaf(r, v[p], la * a[p]);
+                ra[p] = r * a[p];
+            }
+#pragma unroll
+            for (int p = J1; p < JA; ++p) gva[p] = 0.f;
+#pragma unroll
+            for (int q = 0; q < J2; ++q) {
+                gvb[q] = fmaf(r, w2[q], lb * b[q]);
+                bb[q] = b[q];
+            }
+#pragma unroll
+            for (int q = J2; q < JB; ++q) gvb[q] = 0.f;
+            float *ga = A.gA + (int64_t)e.i * A.rs1;
+            float *gb = A.gB + (int64_t)e.j * A.rs2;
+#pragma unroll
+            for (int t = 0; t < JA / 4; ++t)
+                atomicAdd(reinterpret_cast<float4 *>(ga) + t,
+                          make_float4(gva[4 * t], gva[4 * t + 1], gva[4 * t + 2], gva[4 * t + 3]));
+#pragma unroll
+            for (int t = 0; t < JB / 4; ++t)
+                atomicAdd(reinterpret_cast<float4 *>(gb) + t,
+                          make_float4(gvb[4 * t], gvb[4 * t + 1], gvb[4 * t + 2], gvb[4 * t + 3]));
+            atomicAdd(ga + JA + k, 1.f);
+            atomicAdd(gb + JB + k, 1.f);
+            if (J1P != J1) ra[J1] = 0.f;
+            if (J2P != J2) bb[J2] = 0.f;
+        } else {
+            for (int p = 0; p < J1P; ++p) ra[p] = 0.f;
+            for (int q = 0; q < J2P; ++q) bb[q] = 0.f;
+        }
+        __syncthreads();
+        if (active) {
+            const int e1 = min(kFastThreads, (my_s + 1) * L);
+            for (int e = my_s * L; e < e1; ++e) {
+                const float2 x = *reinterpret_cast<const float2 *>(sRA + e * J1P + bp);
+                const float2 y = *reinterpret_cast<const float2 *>(sB + e * J2P + bq);
+                acc0 = fmaf(x.x, y.x, acc0);
+                acc1 = fmaf(x.x, y.y, acc1);
+                acc2 = fmaf(x.y, y.x, acc2);
+                acc3 = fmaf(x.y, y.y, acc3);
+            }
+        }
+    }
+}
+
+// The sweep of one wave over every problem of a batch: the same tile work as k_fast_sweep;
+// the CTAs claim tiles from the concatenated tile lists of all problems (toff: prefix
+// offsets) and switch problem (arguments and core in shared memory) between tiles.
+template <int CJ1, int CJ2, int CJ3>
+__global__ void __launch_bounds__(kFastThreads)
+    k_batch_sweep(const FastArgs *__restrict__ probs, const int32_t *__restrict__ toff, int32_t P, int32_t *ctr) {
+    __shared__ FastArgs sArgs;  // the problem of the current tile
+    __shared__ int sPid;
+    const FastArgs &A = sArgs;
+    const Dims d0 = probs[0].d;  // every problem of a batch has the same ranks
+    const int J1 = CJ1 ? CJ1 : d0.J1, J2 = CJ2 ? CJ2 : d0.J2, J3 = CJ3 ? CJ3 : d0.J3;
+    const int J1P = even_up(J1), J2P = even_up(J2);
+    const int PI = J1 * J2 * J3;
+    extern __shared__ __align__(16) float sm[];
+    float *sG = sm;                            // PI
+    float *sGc = sG + align4(PI);              // J1*J2 (G x3 c_k)
+    float *sRA = sGc + align4(J1 * J2);        // kFastThreads * J1P : r a  (8-byte aligned rows)
+    float *sB = sRA + kFastThreads * J1P;      // kFastThreads * J2P : b
+    float *sRed = sB + kFastThreads * J2P;     // kFastThreads * 4
+    __shared__ int sTile;
+    const int tid = threadIdx.x;
+
+    // M_k accumulation layout: 2x2 blocks of (p, q), entry slices
+    const int nbq = J2P / 2, NB = (J1P / 2) * nbq;
+    const int S = NB >= kFastThreads ? 1 : kFastThreads / NB;
+    const int L = (kFastThreads + S - 1) / S;
+    const int my_b = tid % NB, my_s = tid / NB;
+    const bool active = my_s < S;
+    const int bp = (my_b / nbq) * 2, bq = (my_b % nbq) * 2;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+
+    int cur_k = -1, cur_pid = -1;
+    for (;;) {
+        __syncthreads();  // previous tile fully consumed (sTile, sPid, sRA, sB, sGc)
+        if (tid == 0) {  // a tile of the batch: problem by binary search over the tile offsets
+            const int g = atomicAdd(ctr, 1);
+            int pid = -1;
+            if (g < toff[P]) {
+                int lo = 0, hi = P - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (toff[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                pid = lo;
+            }
+            sPid = pid;
+            sTile = pid >= 0 ? g - toff[pid] : 0;
+        }
+        __syncthreads();
+        const int pid = sPid, t = sTile;
+        const bool done = pid < 0;
+        const int k = done ? -1 : probs[pid].tile_k[t];
+        if (k != cur_k || pid != cur_pid || done) {
+            if (cur_k >= 0) {  // merge this CTA's M_k
+                if (active) {
+                    float *o = sRed + (my_s * NB + my_b) * 4;
+                    o[0] = acc0;
+                    o[1] = acc1;
+                    o[2] = acc2;
+                    o[3] = acc3;
+                }
+                __syncthreads();
+                for (int s = tid; s < NB * 4; s += kFastThreads) {
+                    const int b = s >> 2, i = s & 3;
+                    const int p = (b / nbq) * 2 + (i >> 1), q = (b % nbq) * 2 + (i & 1);
+                    if (p < J1 && q < J2) {
+                        float sum = 0.f;
+                        for (int sl = 0; sl < S; ++sl) sum += sRed[(sl * NB + b) * 4 + i];
+                        atomicAdd(A.macc + ((int64_t)cur_k * J1 + p) * J2 + q, sum);
+                    }
+                }
+                acc0 = acc1 = acc2 = acc3 = 0.f;
+            }
+            if (done) break;
+            if (pid != cur_pid) {  // the next problem's arguments and core
+                __syncthreads();
+                if (tid == 0) sArgs = probs[pid];
+                __syncthreads();
+                for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
+                __syncthreads();
+                cur_pid = pid;
+            }
             const float *ck = A.U3 + (int64_t)k * J3;
             for (int s = tid; s < J1 * J2; s += kFastThreads) {
                 float g = 0.f;
@@ -294,7 +502,7 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
         const int t = sTile;
         const bool done = t >= A.n_tiles;
         const int k = done ? -1 : A.tile_k[t];
-        if (k != cur_k) {
+        if (k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
             if (cur_k >= 0 && m_started) {  // merge this CTA's M_k (rows p < J1 in lanes 0..J1-1)
                 tc::fence_after();
                 if (warp < (J1 + 31) / 32) {
@@ -450,6 +658,7 @@ constexpr int kMaccStage = 8192;   // a wave's M_k staged in shared memory up to
 // Jacobi sweeps per wave: the eigenbases of the moments drift slowly from wave to wave and
 // each decomposition starts from the previous one, so a couple of sweeps keep it tracking
 constexpr int kJacobiSweeps = 2;
+constexpr int kEigEvery = 4;
 constexpr int kRowsPerThreadCta = 256;  // rows per CTA of the thread-per-row step
 
 // Patient / gene rows: u <- u - (H + (n lambda/|Omega^{n,i}| + 1/lr) I)^{-1} g with
@@ -660,7 +869,7 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
 // (stride kTileStride) holds the eigenvectors as columns.  Vwarm (n x n, global) is the
 // previous decomposition: M is first rotated into that basis, so a slowly changing matrix
 // needs few sweeps; the result is written back to Vwarm.
-__device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm) {
+__device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm, int max_sweeps) {
     const int lane = threadIdx.x & 31;
     // V = Vwarm (identity if it is all zero), M <- V^T M V
     float vsum = 0.f;
@@ -688,7 +897,7 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm) {
         }
     }
     __syncwarp();
-    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         float off = 0.f, dia = 0.f;
         for (int e = lane; e < n * n; e += 32) {
             const float x = M[(e / n) * kTileStride + e % n];
@@ -737,6 +946,7 @@ struct DenseArgs {
     float *macc;
     float *gram_in;   // moments used for the curvature (cleared after use)
     float *eigv;      // warm-start eigenvectors of Ma, Mb, Cn (J1^2 + J2^2 + J3^2)
+    int32_t *wave_counter;  // dense steps taken so far (selects the waves that re-decompose)
     float *curv_out;  // platform curvatures for the next wave's rows (I3 J1^2 + I3 J2^2)
     const float *nk;  // entries of this wave per platform
     float n_wave, lam, lr, lam_core;
@@ -762,6 +972,10 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
     float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles for the eigen-decompositions
     float *sMacc = sJ + 9 * kMaxRank * kTileStride;  // the wave's M_k, if they fit
     const int tid = threadIdx.x;
+    // every kEigEvery-th dense step re-decomposes Ma, Mb, Cn (Jacobi sweeps from the previous
+    // eigenbasis); the others keep the eigenbasis and refresh the eigenvalues as its Rayleigh
+    // quotients
+    const bool full_eig = (*A.wave_counter % kEigEvery) == 0;
     const bool stage_m = I3 * Q <= kMaccStage;
     if (do_step && stage_m)
         for (int s = tid; s < I3 * Q; s += blockDim.x) sMacc[s] = A.macc[s];
@@ -801,7 +1015,7 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
             for (int e = (tid & 31); e < n * n; e += 32) M[(e / n) * kTileStride + e % n] = src[e];
             __syncwarp();
             float *Vw = A.eigv + (warp == 0 ? 0 : (warp == 1 ? J1 * J1 : J1 * J1 + J2 * J2));
-            warp_jacobi(M, V, T, n, Vw);
+            warp_jacobi(M, V, T, n, Vw, full_eig ? kJacobiSweeps : 0);
         }
         for (int s = tid; s < PI; s += blockDim.x) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
             const int r = s / Q, p = (s / J2) % J1, q = s % J2;
@@ -916,6 +1130,7 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
         }
         __syncthreads();
         for (int s = tid; s < I3 * Q; s += blockDim.x) A.macc[s] = 0.f;
+        if (tid == 0) *A.wave_counter += 1;
     }
     // platform curvatures for the next wave's row steps (updated G, c; moments of gram_in):
     // all platforms at once when their Gc and W fit in the two PI-sized scratch buffers
@@ -981,13 +1196,7 @@ struct RowArgs {
 // The row step runs one thread per row when both row ranks are compile-time (CJ1, CJ2 > 0),
 // one warp per row otherwise; R.nb1 CTAs cover the patient rows, the rest the gene rows.
 template <int CJ1, int CJ2>
-__global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
-    extern __shared__ __align__(16) float smw[];
-    if (blockIdx.x == 0) {
-        if (mode != 1) wave_dense(A, mode == 0, smw);
-        return;
-    }
-    const int blk = blockIdx.x - 1;
+__device__ void wave_end_rows(const DenseArgs &A, const RowArgs &R, int blk, int mode, float *smw) {
     const bool first = blk < R.nb1;
     const int mb = first ? blk : blk - R.nb1;
     const Dims &d = A.d;
@@ -1004,6 +1213,44 @@ __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, i
         wave_rows(first, mb, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, d, A.lam,
                   1.f / A.lr, R.inv_n, R.curv_in, R.gram_out, smw);
     }
+}
+
+template <int CJ1, int CJ2>
+__global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
+    extern __shared__ __align__(16) float smw[];
+    if (blockIdx.x == 0) {
+        if (mode != 1) wave_dense(A, mode == 0, smw);
+        return;
+    }
+    wave_end_rows<CJ1, CJ2>(A, R, blockIdx.x - 1, mode, smw);
+}
+
+// The end of one wave for every problem of a batch: per problem one CTA takes the dense step
+// and the next ones its row steps (boff: prefix offsets of the problems' CTAs).
+template <int CJ1, int CJ2>
+__global__ void __launch_bounds__(256)
+    k_batch_wave_end(const DenseArgs *__restrict__ dargs, const RowArgs *__restrict__ rargs,
+                     const int32_t *__restrict__ boff, int32_t P) {
+    extern __shared__ __align__(16) float smw[];
+    __shared__ int sPid;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = P - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (boff[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        sPid = lo;
+    }
+    __syncthreads();
+    const int pid = sPid;
+    const int local = (int)blockIdx.x - boff[pid];
+    const DenseArgs A = dargs[pid];
+    const RowArgs R = rargs[pid];
+    if (local == 0) {
+        wave_dense(A, 1, smw);
+        return;
+    }
+    wave_end_rows<CJ1, CJ2>(A, R, local - 1, 0, smw);
 }
 
 // compile-time row ranks of the thread-per-row step
@@ -1087,8 +1334,7 @@ cudaError_t launch_sweep_tc(Ctx *c, const FastArgs &A, int grid) {
     return cudaGetLastError();
 }
 
-template <int CJ1, int CJ2, int CJ3>
-cudaError_t run_sweep(Ctx *c, int64_t w) {
+FastArgs make_fast_args(Ctx *c, int64_t w) {
     const int64_t t0 = c->wave_tile[w], nt = c->wave_tile[w + 1] - t0;
     FastArgs A;
     A.rec = c->rec;
@@ -1111,6 +1357,13 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     A.rs1 = row_stride(c->d.J1, c->d.I3);
     A.rs2 = row_stride(c->d.J2, c->d.I3);
     A.err = c->flag + 3;
+    return A;
+}
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t run_sweep(Ctx *c, int64_t w) {
+    const FastArgs A = make_fast_args(c, w);
+    const int64_t nt = A.n_tiles;
     if (nt == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(c->fast_grid, nt);
     c->launches++;
@@ -1135,10 +1388,10 @@ int64_t curv_stride(const Ctx *c) {
     return ((int64_t)c->d.I3 * (c->d.J1 * c->d.J1 + c->d.J2 * c->d.J2) + 3) & ~(int64_t)3;
 }
 
-cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
+void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowArgs *Rp) {
     const Dims &d = c->d;
-    const int nb1 = ceil_div(d.I1, kRowsPerCta), nb2 = ceil_div(d.I2, kRowsPerCta);
-    DenseArgs A;
+    DenseArgs &A = *Ap;
+    RowArgs &R = *Rp;
     A.d = d;
     A.G = c->G;
     A.U3 = c->U[2];
@@ -1146,13 +1399,13 @@ cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
     A.macc = c->macc;
     A.gram_in = c->gram + (size_t)(parity ^ 1) * c->gram_stride;
     A.eigv = c->gram + 2 * (size_t)c->gram_stride;
+    A.wave_counter = c->flag + 2;
     A.curv_out = c->curv + (size_t)parity * curv_stride(c);
     A.nk = c->wave_nk + (w >= 0 ? w : 0) * d.I3;
     A.n_wave = w >= 0 ? (float)c->wave_len[w] : 0.f;
     A.lam = c->cfg.lambda;
     A.lr = c->cfg.lr;
     A.lam_core = c->nnz ? c->cfg.lambda / (float)c->nnz : 0.f;
-    RowArgs R;
     R.U1 = c->U[0];
     R.U2 = c->U[1];
     R.gA = c->gacc[0];
@@ -1162,16 +1415,21 @@ cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
     R.cnt1 = c->cnt[0];
     R.cnt2 = c->cnt[1];
     R.inv_n = c->nnz ? 1.f / (float)c->nnz : 0.f;
-    R.nb1 = nb1;
+    R.nb1 = 0;  // set by the launcher for its row step
     R.curv_in = c->curv + (size_t)(parity ^ 1) * curv_stride(c);
     R.gram_out = c->gram + (size_t)parity * c->gram_stride;
     if (mode == 2) {  // set-up: curvatures from the moments just formed into buffer `parity`
         A.gram_in = c->gram + (size_t)parity * c->gram_stride;
         A.curv_out = c->curv + (size_t)parity * curv_stride(c);
     }
-    (void)nb2;
+}
+
+cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
+    DenseArgs A;
+    RowArgs R;
+    make_wave_args(c, w, parity, mode, &A, &R);
     c->launches++;
-    return SNECT_DISPATCH_ROWS(d.J1, d.J2, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
+    return SNECT_DISPATCH_ROWS(c->d.J1, c->d.J2, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
 }
 
 }  // namespace
@@ -1199,7 +1457,7 @@ int init_fast(Ctx *c) {
     } else {
         SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
     }
-    SNECT_CUDA(c, cudaMemsetAsync(c->flag + 3, 0, sizeof(int32_t), c->stream));
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag + 2, 0, 2 * sizeof(int32_t), c->stream));
     SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, set_wave_end_attr, c, wave_end_smem(c)));
     // the first wave's curvature: moments of the initial rows into the odd buffer, then the
     // platform curvatures from them
@@ -1240,3 +1498,243 @@ void free_fast(Ctx *c) {
 }
 
 }  // namespace snect
+
+// ---------------------------------------------------------------------------------------
+// Batched form: many independent decompositions stepped together.  Every wave runs one
+// sweep launch over the tiles of all problems and one wave-end launch over all problems'
+// dense and row steps; an epoch of the whole batch is one CUDA graph.
+
+namespace snect {
+
+struct Batch {
+    std::vector<Ctx *> ctx;
+    int32_t P = 0;
+    int64_t n_waves = 0;
+    Dims d{};
+    FastArgs *d_fast = nullptr;   // [n_waves][P]
+    int32_t *d_toff = nullptr;    // [n_waves][P + 1] tile offsets
+    DenseArgs *d_dense = nullptr; // [n_waves][P]
+    RowArgs *d_rows = nullptr;    // [n_waves][P]
+    int32_t *d_boff = nullptr;    // [P + 1] CTA offsets of the wave end
+    int32_t *d_ctr = nullptr;     // [n_waves]
+    std::vector<int32_t> tiles_per_wave;
+    int32_t wave_end_blocks = 0;
+    int64_t epoch_kernels = 0;  // kernels in one epoch's graph
+    int64_t launches = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
+    Ctx *c0 = b->ctx[0];
+    const int nt = b->tiles_per_wave[w];
+    if (nt == 0) return cudaSuccess;
+    const int grid = std::min(c0->fast_grid, nt);
+    k_batch_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c0), st>>>(
+        b->d_fast + w * b->P, b->d_toff + w * (b->P + 1), b->P, b->d_ctr + w);
+    return cudaGetLastError();
+}
+
+template <int CJ1, int CJ2>
+cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
+    const size_t smem = wave_end_smem(b->ctx[0]);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_wave_end<CJ1, CJ2><<<b->wave_end_blocks, 256, smem, st>>>(b->d_dense + w * b->P, b->d_rows + w * b->P,
+                                                                     b->d_boff, b->P);
+    return cudaGetLastError();
+}
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t batch_sweep_attr(Batch *b) {
+    return cudaFuncSetAttribute(k_batch_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]));
+}
+
+template <int CJ1, int CJ2>
+int batch_rows_per_cta(Batch *) { return rows_per_cta<CJ1, CJ2>(); }
+
+int batch_fail(Batch *b, int code, const std::string &m) {
+    b->err = m;
+    return code;
+}
+
+#define BATCH_CUDA(b, call)                                                                          \
+    do {                                                                                             \
+        cudaError_t e__ = (call);                                                                    \
+        if (e__ != cudaSuccess) return batch_fail((b), SNECT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+int batch_build_graph(Batch *b) {
+    const Dims &d = b->d;
+    cudaStream_t cap = nullptr;
+    BATCH_CUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = SNECT_OK;
+    if (e == cudaSuccess) {
+        e = cudaMemsetAsync(b->d_ctr, 0, sizeof(int32_t) * b->n_waves, cap);
+        b->epoch_kernels = 0;
+        for (int64_t w = 0; w < b->n_waves && e == cudaSuccess; ++w) {
+            e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_sweep_k, b, w, cap);
+            if (e == cudaSuccess) e = SNECT_DISPATCH_ROWS(d.J1, d.J2, batch_wave_end_k, b, w, cap);
+            b->epoch_kernels += (b->tiles_per_wave[w] > 0) + 1;
+        }
+        for (Ctx *c : b->ctx) {  // each problem's network pass
+            if (e != cudaSuccess) break;
+            cudaStream_t orig = c->stream;
+            const int64_t before = c->launches;
+            c->stream = cap;
+            e = launch_edge_pass(c);
+            c->stream = orig;
+            b->epoch_kernels += c->launches - before;
+            c->launches = before;  // counted by the batch
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        rc = batch_fail(b, SNECT_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    return rc;
+}
+
+void batch_free(Batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaFree(b->d_fast);
+    cudaFree(b->d_toff);
+    cudaFree(b->d_dense);
+    cudaFree(b->d_rows);
+    cudaFree(b->d_boff);
+    cudaFree(b->d_ctr);
+}
+
+thread_local std::string g_batch_error;
+
+}  // namespace
+}  // namespace snect
+
+using namespace snect;
+
+extern "C" {
+
+int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, void *stream) {
+    if (!out || !ctxs || n < 1) return g_batch_error = "null argument or empty batch", SNECT_EINVAL;
+    *out = nullptr;
+    Batch *b = new Batch();
+    b->P = n;
+    b->stream = (cudaStream_t)stream;
+    for (int32_t p = 0; p < n; ++p) b->ctx.push_back(reinterpret_cast<Ctx *>(ctxs[p]));
+    Ctx *c0 = b->ctx[0];
+    auto bad = [&](const std::string &m) {
+        g_batch_error = m;
+        batch_free(b);
+        delete b;
+        return SNECT_EINVAL;
+    };
+    for (Ctx *c : b->ctx) {
+        if (!c) return bad("null context");
+        if (c->cfg.batch != 0 || c->cfg.precision != SNECT_FP32)
+            return bad("a batch takes fast-mode FP32 contexts");
+        if (c->d.J1 != c0->d.J1 || c->d.J2 != c0->d.J2 || c->d.J3 != c0->d.J3)
+            return bad("every problem of a batch must have the same core ranks");
+        if (c->n_waves != c0->n_waves) return bad("every problem of a batch must have the same number of waves");
+        if (c->device != c0->device) return bad("every problem of a batch must live on the same device");
+    }
+    b->d = c0->d;
+    b->n_waves = c0->n_waves;
+    const int64_t W = b->n_waves, P = n;
+    std::vector<FastArgs> hf((size_t)(W * P));
+    std::vector<DenseArgs> hd((size_t)(W * P));
+    std::vector<RowArgs> hr((size_t)(W * P));
+    std::vector<int32_t> toff((size_t)(W * (P + 1))), boff((size_t)P + 1);
+    const int rpc = SNECT_DISPATCH_ROWS(b->d.J1, b->d.J2, batch_rows_per_cta, b);
+    boff[0] = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        Ctx *c = b->ctx[p];
+        boff[p + 1] = boff[p] + 1 + ceil_div(c->d.I1, rpc) + ceil_div(c->d.I2, rpc);
+    }
+    b->wave_end_blocks = boff[P];
+    b->tiles_per_wave.assign((size_t)W, 0);
+    for (int64_t w = 0; w < W; ++w) {
+        int32_t acc = 0;
+        for (int64_t p = 0; p < P; ++p) {
+            Ctx *c = b->ctx[p];
+            hf[w * P + p] = make_fast_args(c, w);
+            make_wave_args(c, w, (int)(w & 1), 0, &hd[w * P + p], &hr[w * P + p]);
+            hr[w * P + p].nb1 = ceil_div(c->d.I1, rpc);
+            toff[w * (P + 1) + p] = acc;
+            acc += hf[w * P + p].n_tiles;
+        }
+        toff[w * (P + 1) + P] = acc;
+        b->tiles_per_wave[w] = acc;
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void **dst, const void *src, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(dst, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void **)&b->d_fast, hf.data(), sizeof(FastArgs) * hf.size());
+    up((void **)&b->d_dense, hd.data(), sizeof(DenseArgs) * hd.size());
+    up((void **)&b->d_rows, hr.data(), sizeof(RowArgs) * hr.size());
+    up((void **)&b->d_toff, toff.data(), sizeof(int32_t) * toff.size());
+    up((void **)&b->d_boff, boff.data(), sizeof(int32_t) * boff.size());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctr, sizeof(int32_t) * std::max<int64_t>(1, W));
+    if (e == cudaSuccess) e = SNECT_DISPATCH_RANKS(b->d.J1, b->d.J2, b->d.J3, batch_sweep_attr, b);
+    if (e != cudaSuccess) {
+        g_batch_error = std::string("batch set-up: ") + cudaGetErrorString(e);
+        batch_free(b);
+        delete b;
+        return SNECT_ECUDA;
+    }
+    *out = reinterpret_cast<snect_batch *>(b);
+    return SNECT_OK;
+}
+
+int snect_batch_epoch(snect_batch *h, int32_t n_epochs) {
+    Batch *b = reinterpret_cast<Batch *>(h);
+    if (!b || n_epochs < 0) return SNECT_EINVAL;
+    if (!b->exec) {
+        // the contexts' own set-up work must be finished before the batch graph runs
+        for (Ctx *c : b->ctx)
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return batch_fail(b, SNECT_ECUDA, "context stream");
+        int rc = batch_build_graph(b);
+        if (rc) return rc;
+    }
+    for (int32_t t = 0; t < n_epochs; ++t) {
+        BATCH_CUDA(b, cudaGraphLaunch(b->exec, b->stream));
+        b->launches += b->epoch_kernels;
+    }
+    for (Ctx *c : b->ctx) c->param_version++;
+    return SNECT_OK;
+}
+
+int64_t snect_batch_launch_count(const snect_batch *h) {
+    const Batch *b = reinterpret_cast<const Batch *>(h);
+    return b ? b->launches : 0;
+}
+
+const char *snect_batch_last_error(const snect_batch *h) {
+    const Batch *b = reinterpret_cast<const Batch *>(h);
+    return b ? b->err.c_str() : g_batch_error.c_str();
+}
+
+void snect_batch_destroy(snect_batch *h) {
+    Batch *b = reinterpret_cast<Batch *>(h);
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+}
+
+}  // extern "C"
