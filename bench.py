@@ -55,19 +55,24 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--small", action="store_true", help="a small problem of the same shape (for profiling)")
+    ap.add_argument("--small", action="store_true",
+                    help="a smaller problem of the same shape, 12M entries (for profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="bf16: time the BF16 tensor-core sweep at core 16x16x5 instead (for profiling)")
     ap.add_argument("--serve-queries", type=int, default=20000, help="fold-in + top-k queries (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, queries/s")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 vs BF16 refit at 16x16x5")
+    ap.add_argument("--batched-scale", type=float, default=1.0,
+                    help="entries of the batched form's cohorts times this (0: skip the batched form)")
     return ap.parse_args()
 
 
-def make_problem(small=False):
+def make_problem(small=False, J_fit=(10, 10, 5)):
     import snect_synth as S
 
     if small:
-        return S.config2(n_patients=1500, nnz=6_000_000, n_edges=100_000)
-    return S.config2()
+        return S.config2(n_patients=1800, nnz=12_000_000, n_edges=100_000, J_fit=J_fit)
+    return S.config2(J_fit=J_fit)
 
 
 def peaks():
@@ -277,6 +282,73 @@ def precision_form(p, snect, epochs=10):
     return out
 
 
+def batched_form(args, snect, epochs=5):
+    """Batched form: 12 cohort sub-tensors (150-1,100 patients x 15,000 genes x 5, 0.4M-8M
+    entries each) x 8 graph weights = 96 decompositions at core 16 x 16 x 5, FP32 fast mode.
+    All 96 are stepped by one graph per epoch (per wave: one sweep launch over every
+    problem's tiles, one wave-end launch), timed against the same 96 contexts stepped one
+    after another by their own epoch graphs; both from the same start."""
+    import snect_synth as S
+    import torch
+
+    cohorts, lam_gs = S.config4_cohorts(scale=args.batched_scale)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    dcoh = [dict(idx=t(p.idx), val=t(p.val), edges=t(p.edges), w=t(p.w), G0=t(p.G0), U0=[t(u) for u in p.U0],
+                 tidx=t(p.test_idx), tval=t(p.test_val)) for p in cohorts]
+    nnz = sum(p.nnz for p in cohorts) * len(lam_gs)
+    st = torch.cuda.current_stream()
+
+    def contexts():
+        return [snect.Snect(p.I, p.J, d["idx"], d["val"], d["edges"], d["w"], d["G0"], d["U0"], lam=p.lam,
+                            lam_g=float(lg), lr=p.lr, batch=0)
+                for p, d in zip(cohorts, dcoh) for lg in lam_gs]
+
+    def timed(step, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        step(n)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def rmse(cs):
+        r = [c.loss(d["tidx"], d["tval"])["rmse_test"] for c, (d, _) in
+             zip(cs, [(d, lg) for d in dcoh for lg in lam_gs])]
+        return float(np.mean(r)), float(np.max(r))
+
+    out = {"problems": len(cohorts) * len(lam_gs), "nnz_per_epoch": int(nnz)}
+    cs = contexts()
+    b = snect.Batch(cs)
+    b.epoch(1)  # warm-up (graph capture)
+    l0 = b.launches
+    ms_b = timed(b.epoch, epochs - 1)
+    out["batched"] = {"nnz_updates_per_s": nnz / (ms_b / 1e3), "ms_per_epoch": ms_b,
+                      "launches_per_epoch": (b.launches - l0) / (epochs - 1)}
+    out["batched"]["mean_rmse_test"], out["batched"]["max_rmse_test"] = rmse(cs)
+    b.close()
+    for c in cs:
+        c.close()
+    cs = contexts()
+
+    def one_by_one(n):
+        for c in cs:
+            c.epoch(n)
+
+    one_by_one(1)
+    ms_s = timed(one_by_one, epochs - 1)
+    out["one_by_one"] = {"nnz_updates_per_s": nnz / (ms_s / 1e3), "ms_per_epoch": ms_s}
+    out["one_by_one"]["mean_rmse_test"], out["one_by_one"]["max_rmse_test"] = rmse(cs)
+    for c in cs:
+        c.close()
+    out["batched_vs_one_by_one"] = ms_s / ms_b
+    out["workload"] = ("12 cohorts of 150-1,100 patients x 15,000 genes x 5 (%.2gM-%.2gM entries) x 8 lambda_g in "
+                       "1e-3..1, core 16x16x5, FP32 fast mode; %d epochs from the same start"
+                       % (cohorts[0].nnz / 1e6, cohorts[-1].nnz / 1e6, epochs))
+    return out
+
+
 def quality(loss, job_loss, job_epochs, epochs_run, small):
     """Test RMSE of the e2e jobs (10 epochs from the initial factors) beside the oracle's after
     the same 10 sequential epochs (tests/golden/config2_oracle.json, written from oracle/)."""
@@ -334,14 +406,16 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     snect.load(build_if_missing=True)
-    p = make_problem(args.small)
+    bf16 = args.precision == "bf16"
+    prec = snect.BF16 if bf16 else snect.FP32
+    p = make_problem(args.small, (16, 16, 5) if bf16 else (10, 10, 5))
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
 
     # ---- resident inputs: device tensors -> context; K timed epochs ----------------------
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     ctx = snect.Snect(p.I, p.J, t(p.idx), t(p.val), t(p.edges), t(p.w), t(p.G0), [t(u) for u in p.U0], lam=p.lam,
-                      lam_g=p.lam_g, lr=p.lr, batch=0)
+                      lam_g=p.lam_g, lr=p.lr, batch=0, precision=prec)
     for _ in range(args.warmup):
         ctx.epoch(1)
     torch.cuda.synchronize()
@@ -378,7 +452,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c = snect.Snect(p.I, p.J, h["idx"], h["val"], h["edges"], h["w"], h["G0"], h["U0"], lam=p.lam,
-                        lam_g=p.lam_g, lr=p.lr, batch=0)
+                        lam_g=p.lam_g, lr=p.lr, batch=0, precision=prec)
         c.epoch(job_epochs)
         job_loss = c.loss(h["tidx"], h["tval"])
         c.get_factors()
@@ -395,10 +469,11 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="replicas x%d" % world if world > 1 else "single GPU",
-                       l2="inputs larger than L2: 432 MB of entry records streamed per epoch",
-                       small=bool(args.small)),
+                       l2="inputs larger than L2: %d MB of entry records streamed per epoch" % (p.nnz * 16 // 10 ** 6),
+                       small=bool(args.small), precision=args.precision, I=list(p.I), J=list(p.J),
+                       nnz_train=int(p.nnz)),
         "e2e": {"value": p.nnz * job_epochs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "step": "one training job: snect_init from pinned host buffers, %d epochs, objective and "
@@ -406,18 +481,20 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
                      "frac": (achieved / pk) if achieved else None, "traffic": None,
-                     "kernel": "k_fast_sweep (one launch per wave)",
+                     "kernel": "%s (one launch per wave)" % ("k_fast_sweep_tc" if bf16 else "k_fast_sweep"),
                      "bytes_per_unit": bytes_per_nnz, "units_per_launch": p.nnz / max(sweep_n, 1),
                      "peak_kind": pk_kind,
                      "timing": "CUDA events around each sweep launch inside the last timed epoch (%d launches, "
                                "%.3f ms)" % (sweep_n, sweep_ms)},
         "clocks": clk.summary(),
-        "quality": quality(loss, job_loss, job_epochs, args.warmup + args.steps, args.small),
+        "quality": quality(loss, job_loss, job_epochs, args.warmup + args.steps, args.small or bf16),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0 and not args.no_precision:
         line["precision_form"] = precision_form(p, snect)
+    if rank == 0 and args.batched_scale > 0:
+        line["batched_form"] = batched_form(args, snect)
     if rank == 0 and args.serve_queries > 0:
         line["serving"] = serving(args, snect)
     if rank == 0:
