@@ -128,11 +128,14 @@ __global__ void k_max_degree(const int32_t *__restrict__ ptr, int32_t I2, int32_
 }
 
 // key = (wave << 32) | platform; value = entry position (fast mode grouping)
-__global__ void k_wave_keys(const Rec *__restrict__ rec, int64_t n, int64_t wave, uint64_t *keys,
-                            int32_t *vals) {
+// key (wave, platform, patient): bits [0, bi) patient (0 when bi = 0), [bi, bi + bk) platform,
+// above that the wave
+__global__ void k_wave_keys(const Rec *__restrict__ rec, int64_t n, int64_t wave, int bi, int bk,
+                            uint64_t *keys, int32_t *vals) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
-    keys[e] = ((uint64_t)(e / wave) << 32) | (uint32_t)rec[e].k;
+    const Rec r = rec[e];
+    keys[e] = ((uint64_t)(e / wave) << (bi + bk)) | ((uint64_t)r.k << bi) | (bi ? (uint64_t)r.i : 0u);
     vals[e] = (int32_t)e;
 }
 
@@ -352,9 +355,16 @@ int prep_fast_tiles(Ctx *c) {
     SNECT_CUDA(c, cudaMallocAsync(&vals2, sizeof(int32_t) * n, c->stream));
     SNECT_CUDA(c, cudaMallocAsync(&tmp, sizeof(Rec) * n, c->stream));
     SNECT_CUDA(c, cudaMallocAsync(&hist, sizeof(int32_t) * c->n_waves * I3, c->stream));
-    k_wave_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, keys, vals);
+    // inside a wave and platform the entries are put in patient order (the sweep sums a
+    // patient's neighbouring entries before adding them to its row; gradients inside a wave
+    // all use the wave-start values, so the order inside a wave is free); the stable sort
+    // keeps the visit order among one patient's entries
+    const int bw = bits_for((uint64_t)(c->n_waves - 1)), bk = bits_for((uint64_t)(I3 - 1));
+    int bi = bits_for((uint64_t)(c->d.I1 - 1));
+    if (bw + bk + bi > 64) bi = 0;
+    k_wave_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, bi, bk, keys, vals);
     c->launches++;
-    int rc = sort_pairs(c, keys, vals, keys2, vals2, n, 32 + bits_for((uint64_t)c->n_waves));
+    int rc = sort_pairs(c, keys, vals, keys2, vals2, n, bw + bk + bi);
     if (rc == SNECT_OK) {
         k_permute<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, vals2, n, tmp);
         cudaMemcpyAsync(c->rec, tmp, sizeof(Rec) * n, cudaMemcpyDeviceToDevice, c->stream);

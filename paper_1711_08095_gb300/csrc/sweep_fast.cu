@@ -58,8 +58,227 @@ struct FastArgs {
     int32_t *err;      // set when a tensor-core wait gives up
 };
 
+// Adds each run of equal patient indices in a warp to its patient row once.  The entries of a
+// tile are sorted by patient within their wave and platform, so a patient's entries sit next
+// to each other: segmented suffix sums by shuffles leave each run's total in its first lane,
+// which adds it and the run's length (entries of platform k) to the row accumulator.  iv < 0
+// marks a lane without an entry.  Every lane of the warp calls this.
+template <int RA>
+__device__ __forceinline__ void add_patient_runs(float (&g)[RA], int J, int iv, float *__restrict__ gA, int32_t rs,
+                                                 int k) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int inext = __shfl_down_sync(FULL, iv, 1);
+    if (__any_sync(FULL, lane < 31 && iv >= 0 && inext == iv)) {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int io = __shfl_down_sync(FULL, iv, off);
+            const bool same = lane + off < 32 && io == iv;
+#pragma unroll
+            for (int p = 0; p < RA; ++p) {
+                if (p < J) {
+                    const float o = __shfl_down_sync(FULL, g[p], off);
+                    if (same) g[p] += o;
+                }
+            }
+        }
+    }
+    const int iprev = __shfl_up_sync(FULL, iv, 1);
+    const unsigned run = __match_any_sync(FULL, iv);
+    if (iv >= 0 && (lane == 0 || iprev != iv)) {
+        float *ga = gA + (int64_t)iv * rs;
+        const int JA = (J + 3) & ~3;
+#pragma unroll
+        for (int t = 0; t < RA / 4; ++t)
+            if (4 * t < JA)
+                atomicAdd(reinterpret_cast<float4 *>(ga) + t, make_float4(g[4 * t], g[4 * t + 1], g[4 * t + 2], g[4 * t + 3]));
+        atomicAdd(ga + JA + k, (float)__popc(run));
+    }
+}
+
+// The entries of tile t (platform k), one per thread; every thread of the CTA calls this.
+// Gathers a, b (read-only during the sweep: cached loads), v = Gc b, w2 = Gc^T a, the
+// residual, the row gradients (patient rows by runs, gene rows one atomic per entry), and
+// stages r a and b in shared memory (ra, bb: this thread's rows) for the M_k accumulation.
 template <int CJ1, int CJ2, int CJ3>
-__global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
+__device__ __forceinline__ void tile_entries(const FastArgs &A, int t, int k, const float *__restrict__ sGc,
+                                             float *ra, float *bb) {
+    const int J1 = CJ1 ? CJ1 : A.d.J1, J2 = CJ2 ? CJ2 : A.d.J2;
+    const int J1P = even_up(J1), J2P = even_up(J2);
+    constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
+    const int JB = (J2 + 3) & ~3;
+    const int n_e = A.tile_len[t];
+    float gva[RA];
+#pragma unroll
+    for (int p = 0; p < RA; ++p) gva[p] = 0.f;
+    int iv = -1;
+    if ((int)threadIdx.x < n_e) {
+        const Rec e = A.rec[A.tile_start[t] + threadIdx.x];
+        iv = e.i;
+        float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value];
+        float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
+        const float *ua = A.U1 + (int64_t)e.i * J1;
+        const float *ub = A.U2 + (int64_t)e.j * J2;
+        // rows of even compile-time length load as float2 (row starts are 8-byte aligned)
+        if constexpr (CJ1 > 0 && CJ1 % 2 == 0) {
+#pragma unroll
+            for (int p = 0; p < CJ1; p += 2) {
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(ua + p));
+                a[p] = t2.x;
+                a[p + 1] = t2.y;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < J1; ++p) a[p] = __ldg(ua + p);
+        }
+        if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < CJ2; q += 2) {
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(ub + q));
+                b[q] = t2.x;
+                b[q + 1] = t2.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < J2; ++q) b[q] = __ldg(ub + q);
+        }
+#pragma unroll
+        for (int q = 0; q < J2; ++q) w2[q] = 0.f;
+        if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {  // Gc read as float2 pairs (broadcast)
+#pragma unroll
+            for (int p = 0; p < CJ1; ++p) {
+                float vp = 0.f;
+#pragma unroll
+                for (int q = 0; q < CJ2; q += 2) {
+                    const float2 g = *reinterpret_cast<const float2 *>(sGc + p * CJ2 + q);
+                    vp = fmaf(g.x, b[q], vp);
+                    vp = fmaf(g.y, b[q + 1], vp);
+                    w2[q] = fmaf(a[p], g.x, w2[q]);
+                    w2[q + 1] = fmaf(a[p], g.y, w2[q + 1]);
+                }
+                v[p] = vp;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < J1; ++p) {
+                float vp = 0.f;
+#pragma unroll
+                for (int q = 0; q < J2; ++q) {
+                    const float g = sGc[p * J2 + q];
+                    vp = fmaf(g, b[q], vp);
+                    w2[q] = fmaf(a[p], g, w2[q]);
+                }
+                v[p] = vp;
+            }
+        }
+        float xt = 0.f;
+#pragma unroll
+        for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
+        const float r = xt - e.x;
+        const float la = A.lam / (float)__ldg(A.cnt1 + e.i), lb = A.lam / (float)__ldg(A.cnt2 + e.j);
+        // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
+        float gvb[RB];
+#pragma unroll
+        for (int p = 0; p < J1; ++p) {
+            gva[p] = fmaf(r, v[p], la * a[p]);
+            ra[p] = r * a[p];
+        }
+#pragma unroll
+        for (int q = 0; q < J2; ++q) {
+            gvb[q] = fmaf(r, w2[q], lb * b[q]);
+            bb[q] = b[q];
+        }
+#pragma unroll
+        for (int q = J2; q < JB; ++q) gvb[q] = 0.f;
+        float *gb = A.gB + (int64_t)e.j * A.rs2;
+#pragma unroll
+        for (int t4 = 0; t4 < RB / 4; ++t4)
+            if (4 * t4 < JB)
+                atomicAdd(reinterpret_cast<float4 *>(gb) + t4,
+                          make_float4(gvb[4 * t4], gvb[4 * t4 + 1], gvb[4 * t4 + 2], gvb[4 * t4 + 3]));
+        atomicAdd(gb + JB + k, 1.f);
+        if (J1P != J1) ra[J1] = 0.f;
+        if (J2P != J2) bb[J2] = 0.f;
+    } else {
+        for (int p = 0; p < J1P; ++p) ra[p] = 0.f;
+        for (int q = 0; q < J2P; ++q) bb[q] = 0.f;
+    }
+    add_patient_runs<RA>(gva, J1, iv, A.gA, A.rs1, k);
+}
+
+// M_k accumulation layout: 2 x 2 blocks of (p, q) and slices of the tile's entries.
+struct MLayout {
+    int nbq, NB, S, L, my_b, my_s, bp, bq;
+    bool active;
+    __device__ MLayout(int J1P, int J2P) {
+        nbq = J2P / 2;
+        NB = (J1P / 2) * nbq;
+        S = NB >= kFastThreads ? 1 : kFastThreads / NB;
+        L = (kFastThreads + S - 1) / S;
+        my_b = threadIdx.x % NB;
+        my_s = threadIdx.x / NB;
+        active = my_s < S;
+        bp = (my_b / nbq) * 2;
+        bq = (my_b % nbq) * 2;
+    }
+};
+
+// this thread's 2 x 2 block of M_k over its slice of the staged tile
+__device__ __forceinline__ void m_accumulate(const MLayout &ml, const float *sRA, const float *sB, int J1P, int J2P,
+                                             float &acc0, float &acc1, float &acc2, float &acc3) {
+    if (!ml.active) return;
+    const int e1 = min(kFastThreads, (ml.my_s + 1) * ml.L);
+    for (int e = ml.my_s * ml.L; e < e1; ++e) {
+        const float2 x = *reinterpret_cast<const float2 *>(sRA + e * J1P + ml.bp);
+        const float2 y = *reinterpret_cast<const float2 *>(sB + e * J2P + ml.bq);
+        acc0 = fmaf(x.x, y.x, acc0);
+        acc1 = fmaf(x.x, y.y, acc1);
+        acc2 = fmaf(x.y, y.x, acc2);
+        acc3 = fmaf(x.y, y.y, acc3);
+    }
+}
+
+// merges the CTA's M_k partial (2 x 2 blocks x slices, staged through sRed) into macc
+__device__ __forceinline__ void m_merge(const MLayout &ml, float *sRed, float *__restrict__ macc, int J1, int J2,
+                                        float &acc0, float &acc1, float &acc2, float &acc3) {
+    if (ml.active) {
+        float *o = sRed + (ml.my_s * ml.NB + ml.my_b) * 4;
+        o[0] = acc0;
+        o[1] = acc1;
+        o[2] = acc2;
+        o[3] = acc3;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < ml.NB * 4; s += kFastThreads) {
+        const int b = s >> 2, i = s & 3;
+        const int p = (b / ml.nbq) * 2 + (i >> 1), q = (b % ml.nbq) * 2 + (i & 1);
+        if (p < J1 && q < J2) {
+            float sum = 0.f;
+            for (int sl = 0; sl < ml.S; ++sl) sum += sRed[(sl * ml.NB + b) * 4 + i];
+            atomicAdd(macc + (p * J2 + q), sum);
+        }
+    }
+    acc0 = acc1 = acc2 = acc3 = 0.f;
+}
+
+// Gc = G x3 c_k into shared memory
+__device__ __forceinline__ void form_gc(const float *sG, const float *__restrict__ ck, float *sGc, int J1, int J2,
+                                        int J3) {
+    for (int s = threadIdx.x; s < J1 * J2; s += kFastThreads) {
+        float g = 0.f;
+        for (int r = 0; r < J3; ++r) g = fmaf(sG[s * J3 + r], ck[r], g);
+        sGc[s] = g;
+    }
+}
+
+// CTAs per SM the register budget is cut for (more entries in flight hide the gathers)
+template <int CJ1, int CJ2>
+constexpr int sweep_min_blocks() {
+    return (CJ1 > 0 && CJ2 > 0 && CJ1 * CJ2 <= 100) ? 4 : (CJ1 == 16 && CJ2 == 16) ? 3 : 1;
+}
+
+template <int CJ1, int CJ2, int CJ3>
+__global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_fast_sweep(FastArgs A) {
     const int J1 = CJ1 ? CJ1 : A.d.J1, J2 = CJ2 ? CJ2 : A.d.J2, J3 = CJ3 ? CJ3 : A.d.J3;
     const int J1P = even_up(J1), J2P = even_up(J2);
     const int PI = J1 * J2 * J3;
@@ -72,14 +291,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
     __shared__ int sTile;
     const int tid = threadIdx.x;
     for (int t = tid; t < PI; t += kFastThreads) sG[t] = A.G[t];
-
-    // M_k accumulation layout: 2x2 blocks of (p, q), entry slices
-    const int nbq = J2P / 2, NB = (J1P / 2) * nbq;
-    const int S = NB >= kFastThreads ? 1 : kFastThreads / NB;
-    const int L = (kFastThreads + S - 1) / S;
-    const int my_b = tid % NB, my_s = tid / NB;
-    const bool active = my_s < S;
-    const int bp = (my_b / nbq) * 2, bq = (my_b % nbq) * 2;
+    const MLayout ml(J1P, J2P);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 
     int cur_k = -1;
@@ -91,150 +303,15 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
         const bool done = t >= A.n_tiles;
         const int k = done ? -1 : A.tile_k[t];
         if (k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
-            if (cur_k >= 0) {  // merge this CTA's M_k
-                if (active) {
-                    float *o = sRed + (my_s * NB + my_b) * 4;
-                    o[0] = acc0;
-                    o[1] = acc1;
-                    o[2] = acc2;
-                    o[3] = acc3;
-                }
-                __syncthreads();
-                for (int s = tid; s < NB * 4; s += kFastThreads) {
-                    const int b = s >> 2, i = s & 3;
-                    const int p = (b / nbq) * 2 + (i >> 1), q = (b % nbq) * 2 + (i & 1);
-                    if (p < J1 && q < J2) {
-                        float sum = 0.f;
-                        for (int sl = 0; sl < S; ++sl) sum += sRed[(sl * NB + b) * 4 + i];
-                        atomicAdd(A.macc + ((int64_t)cur_k * J1 + p) * J2 + q, sum);
-                    }
-                }
-                acc0 = acc1 = acc2 = acc3 = 0.f;
-            }
+            if (cur_k >= 0) m_merge(ml, sRed, A.macc + (int64_t)cur_k * J1 * J2, J1, J2, acc0, acc1, acc2, acc3);
             if (done) break;
-            const float *ck = A.U3 + (int64_t)k * J3;
-            for (int s = tid; s < J1 * J2; s += kFastThreads) {
-                float g = 0.f;
-                for (int r = 0; r < J3; ++r) g = fmaf(sG[s * J3 + r], ck[r], g);
-                sGc[s] = g;
-            }
+            form_gc(sG, A.U3 + (int64_t)k * J3, sGc, J1, J2, J3);
             cur_k = k;
             __syncthreads();
         }
-        const int n_e = A.tile_len[t];
-        float *ra = sRA + tid * J1P;
-        float *bb = sB + tid * J2P;
-        if (tid < n_e) {
-            const Rec e = A.rec[A.tile_start[t] + tid];
-            float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value];
-            float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
-            const float *ua = A.U1 + (int64_t)e.i * J1;
-            const float *ub = A.U2 + (int64_t)e.j * J2;
-            // rows of even compile-time length load as float2 (row starts are 8-byte aligned)
-            if constexpr (CJ1 > 0 && CJ1 % 2 == 0) {
-#pragma unroll
-                for (int p = 0; p < CJ1; p += 2) {
-                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ua + p));
-                    a[p] = t2.x;
-                    a[p + 1] = t2.y;
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < J1; ++p) a[p] = __ldcg(ua + p);
-            }
-            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {
-#pragma unroll
-                for (int q = 0; q < CJ2; q += 2) {
-                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ub + q));
-                    b[q] = t2.x;
-                    b[q + 1] = t2.y;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < J2; ++q) b[q] = __ldcg(ub + q);
-            }
-#pragma unroll
-            for (int q = 0; q < J2; ++q) w2[q] = 0.f;
-            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {  // Gc read as float2 pairs (broadcast)
-#pragma unroll
-                for (int p = 0; p < CJ1; ++p) {
-                    float vp = 0.f;
-#pragma unroll
-                    for (int q = 0; q < CJ2; q += 2) {
-                        const float2 g = *reinterpret_cast<const float2 *>(sGc + p * CJ2 + q);
-                        vp = fmaf(g.x, b[q], vp);
-                        vp = fmaf(g.y, b[q + 1], vp);
-                        w2[q] = fmaf(a[p], g.x, w2[q]);
-                        w2[q + 1] = fmaf(a[p], g.y, w2[q + 1]);
-                    }
-                    v[p] = vp;
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < J1; ++p) {
-                    float vp = 0.f;
-#pragma unroll
-                    for (int q = 0; q < J2; ++q) {
-                        const float g = sGc[p * J2 + q];
-                        vp = fmaf(g, b[q], vp);
-                        w2[q] = fmaf(a[p], g, w2[q]);
-                    }
-                    v[p] = vp;
-                }
-            }
-            float xt = 0.f;
-#pragma unroll
-            for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
-            const float r = xt - e.x;
-            const float la = A.lam / (float)A.cnt1[e.i], lb = A.lam / (float)A.cnt2[e.j];
-            // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
-            constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
-            const int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
-            float gva[RA], gvb[RB];
-#pragma unroll
-            for (int p = 0; p < J1; ++p) {
-                gva[p] = fmaf(r, v[p], la * a[p]);
-                ra[p] = r * a[p];
-            }
-#pragma unroll
-            for (int p = J1; p < JA; ++p) gva[p] = 0.f;
-#pragma unroll
-            for (int q = 0; q < J2; ++q) {
-                gvb[q] = fmaf(r, w2[q], lb * b[q]);
-                bb[q] = b[q];
-            }
-#pragma unroll
-            for (int q = J2; q < JB; ++q) gvb[q] = 0.f;
-            float *ga = A.gA + (int64_t)e.i * A.rs1;
-            float *gb = A.gB + (int64_t)e.j * A.rs2;
-#pragma unroll
-            for (int t = 0; t < JA / 4; ++t)
-                atomicAdd(reinterpret_cast<float4 *>(ga) + t,
-                          make_float4(gva[4 * t], gva[4 * t + 1], gva[4 * t + 2], gva[4 * t + 3]));
-#pragma unroll
-            for (int t = 0; t < JB / 4; ++t)
-                atomicAdd(reinterpret_cast<float4 *>(gb) + t,
-                          make_float4(gvb[4 * t], gvb[4 * t + 1], gvb[4 * t + 2], gvb[4 * t + 3]));
-            atomicAdd(ga + JA + k, 1.f);
-            atomicAdd(gb + JB + k, 1.f);
-            if (J1P != J1) ra[J1] = 0.f;
-            if (J2P != J2) bb[J2] = 0.f;
-        } else {
-            for (int p = 0; p < J1P; ++p) ra[p] = 0.f;
-            for (int q = 0; q < J2P; ++q) bb[q] = 0.f;
-        }
+        tile_entries<CJ1, CJ2, CJ3>(A, t, k, sGc, sRA + tid * J1P, sB + tid * J2P);
         __syncthreads();
-        if (active) {
-            const int e1 = min(kFastThreads, (my_s + 1) * L);
-            for (int e = my_s * L; e < e1; ++e) {
-                const float2 x = *reinterpret_cast<const float2 *>(sRA + e * J1P + bp);
-                const float2 y = *reinterpret_cast<const float2 *>(sB + e * J2P + bq);
-                acc0 = fmaf(x.x, y.x, acc0);
-                acc1 = fmaf(x.x, y.y, acc1);
-                acc2 = fmaf(x.y, y.x, acc2);
-                acc3 = fmaf(x.y, y.y, acc3);
-            }
-        }
+        m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
     }
 }
 
@@ -242,10 +319,10 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_sweep(FastArgs A) {
 // the CTAs claim tiles from the concatenated tile lists of all problems (toff: prefix
 // offsets) and switch problem (arguments and core in shared memory) between tiles.
 template <int CJ1, int CJ2, int CJ3>
-__global__ void __launch_bounds__(kFastThreads)
+__global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
     k_batch_sweep(const FastArgs *__restrict__ probs, const int32_t *__restrict__ toff, int32_t P, int32_t *ctr) {
     __shared__ FastArgs sArgs;  // the problem of the current tile
-    __shared__ int sPid;
+    __shared__ int sPid, sTile;
     const FastArgs &A = sArgs;
     const Dims d0 = probs[0].d;  // every problem of a batch has the same ranks
     const int J1 = CJ1 ? CJ1 : d0.J1, J2 = CJ2 ? CJ2 : d0.J2, J3 = CJ3 ? CJ3 : d0.J3;
@@ -257,16 +334,8 @@ __global__ void __launch_bounds__(kFastThreads)
     float *sRA = sGc + align4(J1 * J2);        // kFastThreads * J1P : r a  (8-byte aligned rows)
     float *sB = sRA + kFastThreads * J1P;      // kFastThreads * J2P : b
     float *sRed = sB + kFastThreads * J2P;     // kFastThreads * 4
-    __shared__ int sTile;
     const int tid = threadIdx.x;
-
-    // M_k accumulation layout: 2x2 blocks of (p, q), entry slices
-    const int nbq = J2P / 2, NB = (J1P / 2) * nbq;
-    const int S = NB >= kFastThreads ? 1 : kFastThreads / NB;
-    const int L = (kFastThreads + S - 1) / S;
-    const int my_b = tid % NB, my_s = tid / NB;
-    const bool active = my_s < S;
-    const int bp = (my_b / nbq) * 2, bq = (my_b % nbq) * 2;
+    const MLayout ml(J1P, J2P);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 
     int cur_k = -1, cur_pid = -1;
@@ -291,26 +360,8 @@ __global__ void __launch_bounds__(kFastThreads)
         const bool done = pid < 0;
         const int k = done ? -1 : probs[pid].tile_k[t];
         if (k != cur_k || pid != cur_pid || done) {
-            if (cur_k >= 0) {  // merge this CTA's M_k
-                if (active) {
-                    float *o = sRed + (my_s * NB + my_b) * 4;
-                    o[0] = acc0;
-                    o[1] = acc1;
-                    o[2] = acc2;
-                    o[3] = acc3;
-                }
-                __syncthreads();
-                for (int s = tid; s < NB * 4; s += kFastThreads) {
-                    const int b = s >> 2, i = s & 3;
-                    const int p = (b / nbq) * 2 + (i >> 1), q = (b % nbq) * 2 + (i & 1);
-                    if (p < J1 && q < J2) {
-                        float sum = 0.f;
-                        for (int sl = 0; sl < S; ++sl) sum += sRed[(sl * NB + b) * 4 + i];
-                        atomicAdd(A.macc + ((int64_t)cur_k * J1 + p) * J2 + q, sum);
-                    }
-                }
-                acc0 = acc1 = acc2 = acc3 = 0.f;
-            }
+            // merge into the previous tile's problem (sArgs still holds it)
+            if (cur_k >= 0) m_merge(ml, sRed, A.macc + (int64_t)cur_k * J1 * J2, J1, J2, acc0, acc1, acc2, acc3);
             if (done) break;
             if (pid != cur_pid) {  // the next problem's arguments and core
                 __syncthreads();
@@ -320,129 +371,13 @@ __global__ void __launch_bounds__(kFastThreads)
                 __syncthreads();
                 cur_pid = pid;
             }
-            const float *ck = A.U3 + (int64_t)k * J3;
-            for (int s = tid; s < J1 * J2; s += kFastThreads) {
-                float g = 0.f;
-                for (int r = 0; r < J3; ++r) g = fmaf(sG[s * J3 + r], ck[r], g);
-                sGc[s] = g;
-            }
+            form_gc(sG, A.U3 + (int64_t)k * J3, sGc, J1, J2, J3);
             cur_k = k;
             __syncthreads();
         }
-        const int n_e = A.tile_len[t];
-        float *ra = sRA + tid * J1P;
-        float *bb = sB + tid * J2P;
-        if (tid < n_e) {
-            const Rec e = A.rec[A.tile_start[t] + tid];
-            float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value];
-            float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
-            const float *ua = A.U1 + (int64_t)e.i * J1;
-            const float *ub = A.U2 + (int64_t)e.j * J2;
-            // rows of even compile-time length load as float2 (row starts are 8-byte aligned)
-            if constexpr (CJ1 > 0 && CJ1 % 2 == 0) {
-#pragma unroll
-                for (int p = 0; p < CJ1; p += 2) {
-                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ua + p));
-                    a[p] = t2.x;
-                    a[p + 1] = t2.y;
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < J1; ++p) a[p] = __ldcg(ua + p);
-            }
-            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {
-#pragma unroll
-                for (int q = 0; q < CJ2; q += 2) {
-                    const float2 t2 = __ldcg(reinterpret_cast<const float2 *>(ub + q));
-                    b[q] = t2.x;
-                    b[q + 1] = t2.y;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < J2; ++q) b[q] = __ldcg(ub + q);
-            }
-#pragma unroll
-            for (int q = 0; q < J2; ++q) w2[q] = 0.f;
-            if constexpr (CJ2 > 0 && CJ2 % 2 == 0) {  // Gc read as float2 pairs (broadcast)
-#pragma unroll
-                for (int p = 0; p < CJ1; ++p) {
-                    float vp = 0.f;
-#pragma unroll
-                    for (int q = 0; q < CJ2; q += 2) {
-                        const float2 g = *reinterpret_cast<const float2 *>(sGc + p * CJ2 + q);
-                        vp = fmaf(g.x, b[q], vp);
-                        vp = fmaf(g.y, b[q + 1], vp);
-                        w2[q] = fmaf(a[p], g.x, w2[q]);
-                        w2[q + 1] = fmaf(a[p], g.y, w2[q + 1]);
-                    }
-                    v[p] = vp;
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < J1; ++p) {
-                    float vp = 0.f;
-#pragma unroll
-                    for (int q = 0; q < J2; ++q) {
-                        const float g = sGc[p * J2 + q];
-                        vp = fmaf(g, b[q], vp);
-                        w2[q] = fmaf(a[p], g, w2[q]);
-                    }
-                    v[p] = vp;
-                }
-            }
-            float xt = 0.f;
-#pragma unroll
-            for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
-            const float r = xt - e.x;
-            const float la = A.lam / (float)A.cnt1[e.i], lb = A.lam / (float)A.cnt2[e.j];
-            // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
-            constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
-            const int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
-            float gva[RA], gvb[RB];
-#pragma unroll
-            for (int p = 0; p < J1; ++p) {
-                gva[p] = fmaf(r, v[p], la * a[p]);
-                ra[p] = r * a[p];
-            }
-#pragma unroll
-            for (int p = J1; p < JA; ++p) gva[p] = 0.f;
-#pragma unroll
-            for (int q = 0; q < J2; ++q) {
-                gvb[q] = fmaf(r, w2[q], lb * b[q]);
-                bb[q] = b[q];
-            }
-#pragma unroll
-            for (int q = J2; q < JB; ++q) gvb[q] = 0.f;
-            float *ga = A.gA + (int64_t)e.i * A.rs1;
-            float *gb = A.gB + (int64_t)e.j * A.rs2;
-#pragma unroll
-            for (int t = 0; t < JA / 4; ++t)
-                atomicAdd(reinterpret_cast<float4 *>(ga) + t,
-                          make_float4(gva[4 * t], gva[4 * t + 1], gva[4 * t + 2], gva[4 * t + 3]));
-#pragma unroll
-            for (int t = 0; t < JB / 4; ++t)
-                atomicAdd(reinterpret_cast<float4 *>(gb) + t,
-                          make_float4(gvb[4 * t], gvb[4 * t + 1], gvb[4 * t + 2], gvb[4 * t + 3]));
-            atomicAdd(ga + JA + k, 1.f);
-            atomicAdd(gb + JB + k, 1.f);
-            if (J1P != J1) ra[J1] = 0.f;
-            if (J2P != J2) bb[J2] = 0.f;
-        } else {
-            for (int p = 0; p < J1P; ++p) ra[p] = 0.f;
-            for (int q = 0; q < J2P; ++q) bb[q] = 0.f;
-        }
+        tile_entries<CJ1, CJ2, CJ3>(A, t, k, sGc, sRA + tid * J1P, sB + tid * J2P);
         __syncthreads();
-        if (active) {
-            const int e1 = min(kFastThreads, (my_s + 1) * L);
-            for (int e = my_s * L; e < e1; ++e) {
-                const float2 x = *reinterpret_cast<const float2 *>(sRA + e * J1P + bp);
-                const float2 y = *reinterpret_cast<const float2 *>(sB + e * J2P + bq);
-                acc0 = fmaf(x.x, y.x, acc0);
-                acc1 = fmaf(x.x, y.y, acc1);
-                acc2 = fmaf(x.y, y.x, acc2);
-                acc3 = fmaf(x.y, y.y, acc3);
-            }
-        }
+        m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
     }
 }
 
@@ -544,12 +479,12 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
                 const float4 *ub = reinterpret_cast<const float4 *>(A.U2 + (int64_t)e.j * J2);
 #pragma unroll
                 for (int p = 0; p < J1 / 4; ++p) {
-                    const float4 t4 = __ldcg(ua + p);
+                    const float4 t4 = __ldg(ua + p);
                     a[4 * p] = t4.x, a[4 * p + 1] = t4.y, a[4 * p + 2] = t4.z, a[4 * p + 3] = t4.w;
                 }
 #pragma unroll
                 for (int q = 0; q < J2 / 4; ++q) {
-                    const float4 t4 = __ldcg(ub + q);
+                    const float4 t4 = __ldg(ub + q);
                     b[4 * q] = t4.x, b[4 * q + 1] = t4.y, b[4 * q + 2] = t4.z, b[4 * q + 3] = t4.w;
                 }
             } else {
@@ -587,21 +522,18 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
 #pragma unroll
             for (int c0 = 0; c0 < J2; c0 += 16) tc::ld16(t_w + lane_off + c0, w2 + c0);
             float r = 0.f;
+            float gva[JA];
+#pragma unroll
+            for (int p = 0; p < JA; ++p) gva[p] = 0.f;
             if (valid) {
                 float xt = 0.f;
 #pragma unroll
                 for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
                 r = xt - x;
-                const float la = A.lam / (float)A.cnt1[ei], lb = A.lam / (float)A.cnt2[ej];
-                float *ga = A.gA + (int64_t)ei * A.rs1;
+                const float la = A.lam / (float)__ldg(A.cnt1 + ei), lb = A.lam / (float)__ldg(A.cnt2 + ej);
                 float *gb = A.gB + (int64_t)ej * A.rs2;
 #pragma unroll
-                for (int p = 0; p < JA; p += 4) {
-                    float g4[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) g4[u] = (p + u < J1) ? fmaf(r, v[p + u], la * a[p + u]) : 0.f;
-                    atomicAdd(reinterpret_cast<float4 *>(ga + p), make_float4(g4[0], g4[1], g4[2], g4[3]));
-                }
+                for (int p = 0; p < J1; ++p) gva[p] = fmaf(r, v[p], la * a[p]);
 #pragma unroll
                 for (int q = 0; q < JB; q += 4) {
                     float g4[4];
@@ -609,9 +541,9 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
                     for (int u = 0; u < 4; ++u) g4[u] = (q + u < J2) ? fmaf(r, w2[q + u], lb * b[q + u]) : 0.f;
                     atomicAdd(reinterpret_cast<float4 *>(gb + q), make_float4(g4[0], g4[1], g4[2], g4[3]));
                 }
-                atomicAdd(ga + JA + k, 1.f);
                 atomicAdd(gb + JB + k, 1.f);
             }
+            add_patient_runs<JA>(gva, J1, valid ? ei : -1, A.gA, A.rs1, k);
 #pragma unroll
             for (int p = 0; p < J1; ++p)
                 *reinterpret_cast<__nv_bfloat16 *>(prt + tc::kmajor_off(p, tid, M)) = __float2bfloat16(r * a[p]);
@@ -1290,6 +1222,9 @@ cudaError_t init_sweep(Ctx *c) {
     const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(c);
     cudaError_t e = cudaFuncSetAttribute(k_fast_sweep<CJ1, CJ2, CJ3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fast_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast_sweep<CJ1, CJ2, CJ3>, kFastThreads, smem);
@@ -1312,6 +1247,11 @@ cudaError_t init_sweep_tc(Ctx *c) {
     const size_t smem = sweep_tc_smem(c);
     cudaError_t e = cudaFuncSetAttribute(k_fast_sweep_tc<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    // the largest shared-memory carveout, so that the occupancy query (and the launch) see
+    // room for several CTAs of ~50 KB each
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fast_sweep_tc<CJ1, CJ2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast_sweep_tc<CJ1, CJ2>, 128, smem);
@@ -1552,8 +1492,11 @@ cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
 
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t batch_sweep_attr(Batch *b) {
-    return cudaFuncSetAttribute(k_batch_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]));
+    cudaError_t e = cudaFuncSetAttribute(k_batch_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_batch_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
 }
 
 template <int CJ1, int CJ2>
