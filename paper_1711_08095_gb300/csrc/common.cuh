@@ -121,6 +121,21 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 cudaError_t launch_det_grad(Ctx *c, int64_t first, int64_t len);
 cudaError_t launch_det_apply(Ctx *c, int64_t first, int64_t len);
 cudaError_t launch_edge_pass(Ctx *c);
+
+// one problem's network pass, for the batched pass (all problems of a batch in three
+// launches: snapshot, light rows, hub rows; blockIdx.y = problem)
+struct EdgeArgs {
+    const int32_t *ptr, *col;
+    const float *w;
+    float *snap, *U2;
+    int32_t I2, J2;  // I2 = 0: no network pass for this problem
+    float step;
+    const int32_t *heavy;
+    int64_t n_heavy;
+};
+EdgeArgs make_edge_args(const Ctx *c);
+cudaError_t launch_batch_edge_pass(const EdgeArgs *d_args, int32_t P, int64_t max_cells, int64_t max_heavy,
+                                   cudaStream_t st, int64_t *launches);
 cudaError_t launch_loss(Ctx *c, const Rec *recs, int64_t n, int which);
 cudaError_t launch_loss_reg_graph(Ctx *c);
 

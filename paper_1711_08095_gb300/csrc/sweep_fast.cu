@@ -42,6 +42,45 @@ constexpr int kFastThreads = kFastTile;  // one entry per thread per tile
 __host__ __device__ constexpr int even_up(int x) { return (x + 1) & ~1; }
 __host__ __device__ constexpr int align4(int x) { return (x + 3) & ~3; }
 
+constexpr int kMaccStage = 8192;   // a wave's M_k staged in shared memory up to this size
+
+struct DenseArgs {
+    Dims d;
+    float *G, *U3;
+    const int32_t *cnt3;
+    float *macc;
+    float *gram_in;   // moments of the rows formed at the previous wave end (cleared after use)
+    float *eigv;      // eigenvectors of Ma, Mb, Cn (J1^2 + J2^2 + J3^2), also the next warm start
+    float *eigval;    // their eigenvalues (J1 + J2 + J3)
+    float *ainv;      // inverses of the platform rows' systems (I3 x J3 x J3)
+    int32_t *wave_counter;  // dense steps taken so far (selects the waves that re-decompose)
+    float *curv;      // platform curvatures for this wave's row steps (I3 J1^2 + I3 J2^2)
+    const float *nk;  // entries of this wave per platform
+    float n_wave, lam, lr, lam_core;
+};
+
+// eigen tiles: row stride n_max + 1; the round tables of the Jacobi need 64 floats of scratch
+__host__ __device__ inline int eig_ld(const Dims &d) {
+    const int n = d.J1 > d.J2 ? d.J1 : d.J2;
+    return (n > d.J3 ? n : d.J3) + 1;
+}
+__host__ __device__ inline int eig_tile(const Dims &d) {
+    const int t = (eig_ld(d) - 1) * eig_ld(d);
+    return t < 64 ? 64 : ((t + 3) & ~3);
+}
+
+// floats of shared memory of the two halves of the dense step
+__host__ __device__ inline int64_t dense_pre_floats(const Dims &d) {
+    const int64_t PI = (int64_t)d.J1 * d.J2 * d.J3;
+    return 3 * PI + (int64_t)d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + 9 * (int64_t)eig_tile(d) +
+           (int64_t)d.I3 * d.J3 * d.J3;
+}
+__host__ __device__ inline int64_t dense_post_floats(const Dims &d) {
+    const int64_t PI = (int64_t)d.J1 * d.J2 * d.J3, Q = (int64_t)d.J1 * d.J2;
+    const int64_t stage = (int64_t)d.I3 * Q <= kMaccStage ? (int64_t)d.I3 * Q : 0;
+    return 3 * PI + 3 * (int64_t)d.I3 * d.J3 + (int64_t)(d.J1 + d.J2 + d.J3) * (eig_ld(d) + 1) + stage;
+}
+
 struct FastArgs {
     const Rec *rec;
     const int32_t *tile_start, *tile_len, *tile_k;
@@ -56,7 +95,10 @@ struct FastArgs {
     float *gA, *gB;  // per row: gradient sums (J_n, padded to 4) + entries per platform
     int32_t rs1, rs2;  // row strides of gA, gB
     int32_t *err;      // set when a tensor-core wait gives up
+    DenseArgs pre;     // the wave's dense pre-work (one extra CTA of the launch)
 };
+
+__device__ void dense_pre(const DenseArgs &A, float *sm);
 
 // Adds each run of equal patient indices in a warp to its patient row once.  The entries of a
 // tile are sorted by patient within their wave and platform, so a patient's entries sit next
@@ -96,24 +138,23 @@ __device__ __forceinline__ void add_patient_runs(float (&g)[RA], int J, int iv, 
     }
 }
 
-// The entries of tile t (platform k), one per thread; every thread of the CTA calls this.
+// This thread's entry of a tile of platform k (valid: the tile has an entry for this thread);
+// every thread of the CTA calls this.
 // Gathers a, b (read-only during the sweep: cached loads), v = Gc b, w2 = Gc^T a, the
 // residual, the row gradients (patient rows by runs, gene rows one atomic per entry), and
 // stages r a and b in shared memory (ra, bb: this thread's rows) for the M_k accumulation.
 template <int CJ1, int CJ2, int CJ3>
-__device__ __forceinline__ void tile_entries(const FastArgs &A, int t, int k, const float *__restrict__ sGc,
-                                             float *ra, float *bb) {
+__device__ __forceinline__ void tile_entries(const FastArgs &A, const Rec &e, bool valid, int k,
+                                             const float *__restrict__ sGc, float *ra, float *bb) {
     const int J1 = CJ1 ? CJ1 : A.d.J1, J2 = CJ2 ? CJ2 : A.d.J2;
     const int J1P = even_up(J1), J2P = even_up(J2);
     constexpr int RA = (RankCap<CJ1>::value + 3) & ~3, RB = (RankCap<CJ2>::value + 3) & ~3;
     const int JB = (J2 + 3) & ~3;
-    const int n_e = A.tile_len[t];
     float gva[RA];
 #pragma unroll
     for (int p = 0; p < RA; ++p) gva[p] = 0.f;
     int iv = -1;
-    if ((int)threadIdx.x < n_e) {
-        const Rec e = A.rec[A.tile_start[t] + threadIdx.x];
+    if (valid) {
         iv = e.i;
         float a[RankCap<CJ1>::value], b[RankCap<CJ2>::value];
         float v[RankCap<CJ1>::value], w2[RankCap<CJ2>::value];
@@ -271,6 +312,33 @@ __device__ __forceinline__ void form_gc(const float *sG, const float *__restrict
     }
 }
 
+// a tile's platform and this thread's record (fetched one tile ahead)
+struct TileFetch {
+    Rec e;
+    int k;
+    bool valid;
+};
+
+__device__ __forceinline__ TileFetch fetch_tile(const FastArgs &A, int t) {
+    TileFetch f;
+    f.k = -1;
+    f.valid = false;
+    f.e.i = f.e.j = f.e.k = 0;
+    f.e.x = 0.f;
+    if (t < A.n_tiles) {
+        f.k = A.tile_k[t];
+        f.valid = (int)threadIdx.x < A.tile_len[t];
+        if (f.valid) {  // streamed once per epoch: evict-first
+            const int4 v = __ldcs(reinterpret_cast<const int4 *>(A.rec + A.tile_start[t] + threadIdx.x));
+            f.e.i = v.x;
+            f.e.j = v.y;
+            f.e.k = v.z;
+            f.e.x = __int_as_float(v.w);
+        }
+    }
+    return f;
+}
+
 // CTAs per SM the register budget is cut for (more entries in flight hide the gathers)
 template <int CJ1, int CJ2>
 constexpr int sweep_min_blocks() {
@@ -283,35 +351,46 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
     const int J1P = even_up(J1), J2P = even_up(J2);
     const int PI = J1 * J2 * J3;
     extern __shared__ __align__(16) float sm[];
+    // CTA 0 (dispatched first, so it runs beside the tile CTAs): the wave's dense pre-work
+    if (blockIdx.x == 0) {
+        dense_pre(A.pre, sm);
+        return;
+    }
     float *sG = sm;                            // PI
     float *sGc = sG + align4(PI);              // J1*J2 (G x3 c_k)
     float *sRA = sGc + align4(J1 * J2);        // kFastThreads * J1P : r a  (8-byte aligned rows)
     float *sB = sRA + kFastThreads * J1P;      // kFastThreads * J2P : b
     float *sRed = sB + kFastThreads * J2P;     // kFastThreads * 4
-    __shared__ int sTile;
+    __shared__ int sTile[2];
     const int tid = threadIdx.x;
-    for (int t = tid; t < PI; t += kFastThreads) sG[t] = A.G[t];
+    for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
     const MLayout ml(J1P, J2P);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 
+    // software pipeline: the next tile is claimed, and its records fetched, before the M_k
+    // accumulation of the current one
+    if (tid == 0) sTile[0] = atomicAdd(A.ctr, 1);
+    __syncthreads();
+    int t = sTile[0], par = 0;
+    TileFetch f = fetch_tile(A, t);
     int cur_k = -1;
     for (;;) {
-        __syncthreads();  // previous tile fully consumed (sTile, sRA, sB, sGc)
-        if (tid == 0) sTile = atomicAdd(A.ctr, 1);
-        __syncthreads();
-        const int t = sTile;
         const bool done = t >= A.n_tiles;
-        const int k = done ? -1 : A.tile_k[t];
-        if (k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
+        if (tid == 0 && !done) sTile[par ^ 1] = atomicAdd(A.ctr, 1);
+        if (f.k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
             if (cur_k >= 0) m_merge(ml, sRed, A.macc + (int64_t)cur_k * J1 * J2, J1, J2, acc0, acc1, acc2, acc3);
             if (done) break;
-            form_gc(sG, A.U3 + (int64_t)k * J3, sGc, J1, J2, J3);
-            cur_k = k;
+            form_gc(sG, A.U3 + (int64_t)f.k * J3, sGc, J1, J2, J3);
+            cur_k = f.k;
             __syncthreads();
         }
-        tile_entries<CJ1, CJ2, CJ3>(A, t, k, sGc, sRA + tid * J1P, sB + tid * J2P);
-        __syncthreads();
+        tile_entries<CJ1, CJ2, CJ3>(A, f.e, f.valid, f.k, sGc, sRA + tid * J1P, sB + tid * J2P);
+        __syncthreads();  // tile staged; the next claim is visible
+        t = sTile[par ^ 1];
+        par ^= 1;
+        f = fetch_tile(A, t);
         m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
+        __syncthreads();  // sRA, sB consumed
     }
 }
 
@@ -322,13 +401,17 @@ template <int CJ1, int CJ2, int CJ3>
 __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
     k_batch_sweep(const FastArgs *__restrict__ probs, const int32_t *__restrict__ toff, int32_t P, int32_t *ctr) {
     __shared__ FastArgs sArgs;  // the problem of the current tile
-    __shared__ int sPid, sTile;
+    __shared__ int sPid[2], sTile[2];
     const FastArgs &A = sArgs;
     const Dims d0 = probs[0].d;  // every problem of a batch has the same ranks
     const int J1 = CJ1 ? CJ1 : d0.J1, J2 = CJ2 ? CJ2 : d0.J2, J3 = CJ3 ? CJ3 : d0.J3;
     const int J1P = even_up(J1), J2P = even_up(J2);
     const int PI = J1 * J2 * J3;
     extern __shared__ __align__(16) float sm[];
+    if ((int)blockIdx.x < P) {  // the first P CTAs: each problem's dense pre-work
+        dense_pre(probs[blockIdx.x].pre, sm);
+        return;
+    }
     float *sG = sm;                            // PI
     float *sGc = sG + align4(PI);              // J1*J2 (G x3 c_k)
     float *sRA = sGc + align4(J1 * J2);        // kFastThreads * J1P : r a  (8-byte aligned rows)
@@ -337,29 +420,41 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
     const int tid = threadIdx.x;
     const MLayout ml(J1P, J2P);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    // a tile of the batch: problem by binary search over the tile offsets (pid -1: none left)
+    auto claim = [&](int slot) {
+        const int g = atomicAdd(ctr, 1);
+        int pid = -1;
+        if (g < toff[P]) {
+            int lo = 0, hi = P - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (toff[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            pid = lo;
+        }
+        sPid[slot] = pid;
+        sTile[slot] = pid >= 0 ? g - toff[pid] : 0;
+    };
+    auto fetch = [&](int pid, int t) {
+        if (pid >= 0) return fetch_tile(probs[pid], t);
+        TileFetch f;
+        f.k = -1;
+        f.valid = false;
+        f.e.i = f.e.j = f.e.k = 0;
+        f.e.x = 0.f;
+        return f;
+    };
 
+    // software pipeline as in k_fast_sweep: claim and fetch one tile ahead
+    if (tid == 0) claim(0);
+    __syncthreads();
+    int pid = sPid[0], t = sTile[0], par = 0;
+    TileFetch f = fetch(pid, t);
     int cur_k = -1, cur_pid = -1;
     for (;;) {
-        __syncthreads();  // previous tile fully consumed (sTile, sPid, sRA, sB, sGc)
-        if (tid == 0) {  // a tile of the batch: problem by binary search over the tile offsets
-            const int g = atomicAdd(ctr, 1);
-            int pid = -1;
-            if (g < toff[P]) {
-                int lo = 0, hi = P - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (toff[mid] <= g) lo = mid; else hi = mid - 1;
-                }
-                pid = lo;
-            }
-            sPid = pid;
-            sTile = pid >= 0 ? g - toff[pid] : 0;
-        }
-        __syncthreads();
-        const int pid = sPid, t = sTile;
         const bool done = pid < 0;
-        const int k = done ? -1 : probs[pid].tile_k[t];
-        if (k != cur_k || pid != cur_pid || done) {
+        if (tid == 0 && !done) claim(par ^ 1);
+        if (f.k != cur_k || pid != cur_pid || done) {
             // merge into the previous tile's problem (sArgs still holds it)
             if (cur_k >= 0) m_merge(ml, sRed, A.macc + (int64_t)cur_k * J1 * J2, J1, J2, acc0, acc1, acc2, acc3);
             if (done) break;
@@ -371,13 +466,18 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
                 __syncthreads();
                 cur_pid = pid;
             }
-            form_gc(sG, A.U3 + (int64_t)k * J3, sGc, J1, J2, J3);
-            cur_k = k;
+            form_gc(sG, A.U3 + (int64_t)f.k * J3, sGc, J1, J2, J3);
+            cur_k = f.k;
             __syncthreads();
         }
-        tile_entries<CJ1, CJ2, CJ3>(A, t, k, sGc, sRA + tid * J1P, sB + tid * J2P);
-        __syncthreads();
+        tile_entries<CJ1, CJ2, CJ3>(A, f.e, f.valid, f.k, sGc, sRA + tid * J1P, sB + tid * J2P);
+        __syncthreads();  // tile staged; the next claim is visible
+        pid = sPid[par ^ 1];
+        t = sTile[par ^ 1];
+        par ^= 1;
+        f = fetch(pid, t);
         m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
+        __syncthreads();  // sRA, sB consumed
     }
 }
 
@@ -392,55 +492,110 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
 // The gathered rows a, b and Gc = G x3 c_k are rounded to BF16 for the products; x~ = a . v,
 // the residual, the row gradients and every update stay FP32 (FP32 master factors).  One
 // thread issues the MMAs; tcgen05.commit arrives on an mbarrier that all threads wait on.
+// TMEM columns of one CTA: V (J1), W2 (J2) and M_k (J2), rounded up to a power of two
+template <int CJ1, int CJ2>
+__host__ __device__ constexpr int tc_tmem_cols() { return CJ1 + 2 * CJ2 <= 64 ? 64 : 128; }
+
+// Shared memory of the tensor-core sweep.  (rA)^T is the A operand of the M_k product, an
+// M = 128-row operand of which only rows p < J1 are meaningful (D row p depends only on A row
+// p, and rows >= J1 of D are never read): only its J1 rows are stored, at the start of the
+// buffer, and the descriptor's remaining rows fall on the other buffers that follow; the
+// allocation is padded so that the whole 128-row span stays inside it.
+__host__ __device__ constexpr size_t tc_smem_bytes(int J1, int J2, int PI) {
+    const size_t used = 2 * ((size_t)J1 * 128 + 128 * J1 + 128 * J2 + J2 * 128 + 2 * J1 * J2) + 4 * (size_t)PI;
+    const size_t span = 2 * 128 * 128;  // the (rA)^T operand's 128-row span
+    return used > span ? used : span;
+}
+
 template <int CJ1, int CJ2>
 __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
     constexpr int J1 = CJ1, J2 = CJ2, M = 128;
     constexpr int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
+    constexpr int NC = tc_tmem_cols<CJ1, CJ2>();
     const int J3 = A.d.J3, PI = J1 * J2 * J3;
     extern __shared__ __align__(1024) uint8_t smb[];
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smb);             // M x J1
+    if (blockIdx.x == 0) {  // CTA 0: the wave's dense pre-work (no TMEM)
+        dense_pre(A.pre, reinterpret_cast<float *>(smb));
+        return;
+    }
+    __nv_bfloat16 *sRAT = reinterpret_cast<__nv_bfloat16 *>(smb);           // J1 x M (rows of (rA)^T)
+    __nv_bfloat16 *sA = sRAT + J1 * M;                                        // M x J1
     __nv_bfloat16 *sB = sA + M * J1;                                          // M x J2
     __nv_bfloat16 *sBT = sB + M * J2;                                         // J2 x M
-    __nv_bfloat16 *sRAT = sBT + J2 * M;                                       // M x M (rows < J1 used)
-    __nv_bfloat16 *bGc = sRAT + M * M;                                        // J1 x J2
+    __nv_bfloat16 *bGc = sBT + J2 * M;                                        // J1 x J2
     __nv_bfloat16 *bGcT = bGc + J1 * J2;                                      // J2 x J1
     float *sG = reinterpret_cast<float *>(bGcT + J2 * J1);                    // PI
     __shared__ __align__(8) uint64_t mbar_vw, mbar_m;
     __shared__ uint32_t tmem_base;
-    __shared__ int sTile;
+    __shared__ int sTile[2];
     const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          tc::smem_u32(&tmem_base)),
-                     "r"(128));
+                     "r"(NC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         tc::mbar_init(&mbar_vw);
         tc::mbar_init(&mbar_m);
+        sTile[0] = atomicAdd(A.ctr, 1);
     }
     for (int t = tid; t < PI; t += M) sG[t] = A.G[t];
-    for (int t = tid; t < M * M / 2; t += M) reinterpret_cast<uint32_t *>(sRAT)[t] = 0u;
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t t_v = tmem, t_w = tmem + 32, t_m = tmem + 64;
+    const uint32_t t_v = tmem, t_w = tmem + J1, t_m = tmem + J1 + J2;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     uint32_t ph_vw = 0, ph_m = 0;
-    bool m_started = false, failed = false;
+    bool m_started = false, m_pending = false, failed = false;
+    // the M_k product of the previous half still reads sRAT and sBT: wait for it before they
+    // are rewritten (false: the wait gave up)
+    auto settle_m = [&]() {
+        bool ok = true;
+        if (m_pending) {
+            ok = tc::mbar_wait(&mbar_m, ph_m);
+            ph_m ^= 1u;
+            m_pending = false;
+        }
+        return ok;
+    };
+    // software pipeline: the records of the next tile (both halves) are fetched one tile ahead
+    int t = sTile[0], par = 0;
+    int nk = -1, n_e = 0;
+    Rec rec_next[2];
+    auto fetch = [&](int tt) {
+        nk = -1;
+        n_e = 0;
+        if (tt < A.n_tiles) {
+            nk = A.tile_k[tt];
+            n_e = A.tile_len[tt];
+            const int64_t s0 = A.tile_start[tt];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int el = h * M + tid;
+                if (el < n_e) {
+                    const int4 v4 = __ldcs(reinterpret_cast<const int4 *>(A.rec + s0 + el));
+                    rec_next[h].i = v4.x;
+                    rec_next[h].j = v4.y;
+                    rec_next[h].k = v4.z;
+                    rec_next[h].x = __int_as_float(v4.w);
+                }
+            }
+        }
+    };
+    fetch(t);
     int cur_k = -1;
     for (;;) {
-        __syncthreads();
-        if (tid == 0) sTile = atomicAdd(A.ctr, 1);
-        __syncthreads();
-        const int t = sTile;
         const bool done = t >= A.n_tiles;
-        const int k = done ? -1 : A.tile_k[t];
+        const int k = nk, tile_n = n_e;
+        Rec rec[2] = {rec_next[0], rec_next[1]};
+        if (tid == 0 && !done) sTile[par ^ 1] = atomicAdd(A.ctr, 1);
         if (k != cur_k || done) {  // (a CTA that finds no tile at its first claim leaves too)
             if (cur_k >= 0 && m_started) {  // merge this CTA's M_k (rows p < J1 in lanes 0..J1-1)
+                if (__syncthreads_or(!settle_m())) failed = true;
                 tc::fence_after();
-                if (warp < (J1 + 31) / 32) {
+                if (!failed && warp < (J1 + 31) / 32) {
                     float mv[J2];
 #pragma unroll
                     for (int c0 = 0; c0 < J2; c0 += 16) tc::ld16(t_m + lane_off + c0, mv + c0);
@@ -463,15 +618,14 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
             }
             cur_k = k;
         }
-        const int n_e = A.tile_len[t];
-        for (int h = 0; h < 2 && h * M < n_e; ++h) {
+        for (int h = 0; h < 2 && h * M < tile_n; ++h) {
             const int el = h * M + tid;
-            const bool valid = el < n_e;
+            const bool valid = el < tile_n;
             float a[J1], b[J2];
             float x = 0.f;
             int ei = 0, ej = 0;
             if (valid) {
-                const Rec e = A.rec[A.tile_start[t] + el];
+                const Rec &e = rec[h];
                 ei = e.i;
                 ej = e.j;
                 x = e.x;
@@ -493,6 +647,8 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
 #pragma unroll
                 for (int q = 0; q < J2; ++q) b[q] = 0.f;
             }
+            // the gathers above overlap the previous half's M_k product; sBT is its operand
+            const bool ok0 = settle_m();
             uint8_t *pa = reinterpret_cast<uint8_t *>(sA), *pb = reinterpret_cast<uint8_t *>(sB);
             uint8_t *pbt = reinterpret_cast<uint8_t *>(sBT), *prt = reinterpret_cast<uint8_t *>(sRAT);
 #pragma unroll
@@ -556,22 +712,24 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
                 tc::commit(&mbar_m);
             }
             m_started = true;
-            const bool ok2 = tc::mbar_wait(&mbar_m, ph_m);
-            ph_m ^= 1u;
-            if (__syncthreads_or(!(ok1 && ok2))) {
+            m_pending = true;  // waited for before sRAT / sBT are rewritten, or at the merge
+            if (__syncthreads_or(!(ok0 && ok1))) {
                 failed = true;
-                if (tid == 0) atomicOr(A.err, 1);
                 break;
             }
         }
-        if (failed) {
-            m_started = false;
-            break;
-        }
+        if (failed) break;
+        __syncthreads();  // the next claim is visible
+        t = sTile[par ^ 1];
+        par ^= 1;
+        fetch(t);
     }
+    if (failed && tid == 0) atomicOr(A.err, 1);
+    // nothing may be in flight when TMEM is released: a pending product is waited for (bounded)
+    if (!settle_m() && tid == 0) atomicOr(A.err, 1);
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NC));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -586,7 +744,6 @@ constexpr int kRowWarps = 8;       // warps per CTA of the row step (one row per
 constexpr int kRowsPerCta = 64;    // rows of one mode per CTA
 constexpr int kTileStride = kMaxRank + 1;
 constexpr int kCkStage = 8192;     // platform curvatures staged in shared memory up to this size
-constexpr int kMaccStage = 8192;   // a wave's M_k staged in shared memory up to this size
 // Jacobi sweeps per wave: the eigenbases of the moments drift slowly from wave to wave and
 // each decomposition starts from the previous one, so a couple of sweeps keep it tracking
 constexpr int kJacobiSweeps = 2;
@@ -796,12 +953,17 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
     }
 }
 
-// Eigen-decomposition of a symmetric n x n matrix (n <= 32) by cyclic Jacobi rotations, one
-// warp.  M (stride kTileStride) is overwritten: its diagonal ends as the eigenvalues; V
-// (stride kTileStride) holds the eigenvectors as columns.  Vwarm (n x n, global) is the
-// previous decomposition: M is first rotated into that basis, so a slowly changing matrix
-// needs few sweeps; the result is written back to Vwarm.
-__device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm, int max_sweeps) {
+// Eigen-decomposition of a symmetric n x n matrix (n <= 32) by Jacobi rotations, one warp.
+// M (row stride ld >= n) is overwritten: its diagonal ends as the eigenvalues; V (stride ld)
+// holds the eigenvectors as columns.  Vwarm (n x n, global) is the previous decomposition: M
+// is first rotated into that basis, so a slowly changing matrix needs few sweeps; the result
+// is written back to Vwarm.  T (n x ld, and at least 64 floats) is scratch.
+// A sweep runs in round-robin order: n - 1 rounds (n rounded up to even) of n/2 disjoint
+// pairs, whose rotations are found from the same M and applied together (disjoint Givens
+// rotations commute), so a round costs about as much as one rotation of the cyclic order.
+__device__ __forceinline__ int rr_pos(int i, int r, int np) { return i == 0 ? 0 : 1 + (i - 1 + r) % (np - 1); }
+
+__device__ void warp_jacobi(float *M, float *V, float *T, int n, int ld, float *Vwarm, int max_sweeps) {
     const int lane = threadIdx.x & 31;
     // V = Vwarm (identity if it is all zero), M <- V^T M V
     float vsum = 0.f;
@@ -810,29 +972,31 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm, i
     for (int o = 16; o; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
     for (int e = lane; e < n * n; e += 32) {
         const int p = e / n, q = e % n;
-        V[p * kTileStride + q] = vsum > 0.f ? Vwarm[e] : (p == q ? 1.f : 0.f);
+        V[p * ld + q] = vsum > 0.f ? Vwarm[e] : (p == q ? 1.f : 0.f);
     }
     __syncwarp();
-    if (lane < n) {  // T = M V  (row lane)
-        for (int q = 0; q < n; ++q) {
-            float x = 0.f;
-            for (int k = 0; k < n; ++k) x = fmaf(M[lane * kTileStride + k], V[k * kTileStride + q], x);
-            T[lane * kTileStride + q] = x;
-        }
+    for (int e = lane; e < n * n; e += 32) {  // T = M V
+        const int p = e / n, q = e % n;
+        float x = 0.f;
+        for (int k = 0; k < n; ++k) x = fmaf(M[p * ld + k], V[k * ld + q], x);
+        T[p * ld + q] = x;
     }
     __syncwarp();
-    if (lane < n) {  // M = V^T T (row lane)
-        for (int q = 0; q < n; ++q) {
-            float x = 0.f;
-            for (int k = 0; k < n; ++k) x = fmaf(V[k * kTileStride + lane], T[k * kTileStride + q], x);
-            M[lane * kTileStride + q] = x;
-        }
+    for (int e = lane; e < n * n; e += 32) {  // M = V^T T
+        const int p = e / n, q = e % n;
+        float x = 0.f;
+        for (int k = 0; k < n; ++k) x = fmaf(V[k * ld + p], T[k * ld + q], x);
+        M[p * ld + q] = x;
     }
     __syncwarp();
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    const int np = (n + 1) & ~1, npairs = np / 2;
+    // the round's pairs and rotations, in the scratch tile
+    int *rP = reinterpret_cast<int *>(T), *rQ = rP + 16;
+    float *rC = T + 32, *rS = T + 48;
+    for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
         float off = 0.f, dia = 0.f;
         for (int e = lane; e < n * n; e += 32) {
-            const float x = M[(e / n) * kTileStride + e % n];
+            const float x = M[(e / n) * ld + e % n];
             if (e / n != e % n) off += x * x; else dia += x * x;
         }
 #pragma unroll
@@ -841,265 +1005,203 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, float *Vwarm, i
             dia += __shfl_xor_sync(0xffffffffu, dia, o);
         }
         if (off <= 1e-12f * dia || !(dia > 0.f)) break;
-        for (int p = 0; p < n - 1; ++p) {
-            for (int q = p + 1; q < n; ++q) {
-                const float apq = M[p * kTileStride + q];
-                const float app = M[p * kTileStride + p], aqq = M[q * kTileStride + q];
-                if (fabsf(apq) <= 1e-9f * sqrtf(fabsf(app * aqq)) + 1e-30f) continue;
-                const float theta = (aqq - app) / (2.f * apq);
-                const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-                const float cs = rsqrtf(t * t + 1.f), sn = t * cs;
-                if (lane < n) {  // columns p, q
-                    const float akp = M[lane * kTileStride + p], akq = M[lane * kTileStride + q];
-                    M[lane * kTileStride + p] = cs * akp - sn * akq;
-                    M[lane * kTileStride + q] = sn * akp + cs * akq;
+        for (int r = 0; r < np - 1; ++r) {
+            if (lane < npairs) {
+                const int a = rr_pos(lane, r, np), b = rr_pos(np - 1 - lane, r, np);
+                const int p = min(a, b), q = max(a, b);
+                float cs = 1.f, sn = 0.f;
+                if (q < n) {  // (index n is the padding of an odd n)
+                    const float apq = M[p * ld + q];
+                    const float app = M[p * ld + p], aqq = M[q * ld + q];
+                    if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) + 1e-30f) {
+                        const float theta = (aqq - app) / (2.f * apq);
+                        const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+                        cs = rsqrtf(t * t + 1.f);
+                        sn = t * cs;
+                    }
                 }
-                __syncwarp();
-                if (lane < n) {  // rows p, q
-                    const float apk = M[p * kTileStride + lane], aqk = M[q * kTileStride + lane];
-                    M[p * kTileStride + lane] = cs * apk - sn * aqk;
-                    M[q * kTileStride + lane] = sn * apk + cs * aqk;
-                    const float vkp = V[lane * kTileStride + p], vkq = V[lane * kTileStride + q];
-                    V[lane * kTileStride + p] = cs * vkp - sn * vkq;
-                    V[lane * kTileStride + q] = sn * vkp + cs * vkq;
-                }
-                __syncwarp();
+                rP[lane] = p;
+                rQ[lane] = q < n ? q : p;  // a padded pair rotates nothing (cs = 1, sn = 0)
+                rC[lane] = cs;
+                rS[lane] = sn;
             }
+            __syncwarp();
+            for (int t = lane; t < n * npairs; t += 32) {  // columns p, q of M and of V
+                const int i = t / npairs, k = t % npairs;
+                const int p = rP[k], q = rQ[k];
+                if (p == q) continue;
+                const float cs = rC[k], sn = rS[k];
+                const float mip = M[i * ld + p], miq = M[i * ld + q];
+                M[i * ld + p] = cs * mip - sn * miq;
+                M[i * ld + q] = sn * mip + cs * miq;
+                const float vip = V[i * ld + p], viq = V[i * ld + q];
+                V[i * ld + p] = cs * vip - sn * viq;
+                V[i * ld + q] = sn * vip + cs * viq;
+            }
+            __syncwarp();
+            for (int t = lane; t < npairs * n; t += 32) {  // rows p, q of M
+                const int k = t / n, j = t % n;
+                const int p = rP[k], q = rQ[k];
+                if (p == q) continue;
+                const float cs = rC[k], sn = rS[k];
+                const float mpj = M[p * ld + j], mqj = M[q * ld + j];
+                M[p * ld + j] = cs * mpj - sn * mqj;
+                M[q * ld + j] = sn * mpj + cs * mqj;
+            }
+            __syncwarp();
         }
     }
-    for (int e = lane; e < n * n; e += 32) Vwarm[e] = V[(e / n) * kTileStride + e % n];
+    for (int e = lane; e < n * n; e += 32) Vwarm[e] = V[(e / n) * ld + e % n];
     __syncwarp();
 }
 
-struct DenseArgs {
-    Dims d;
-    float *G, *U3;
-    const int32_t *cnt3;
-    float *macc;
-    float *gram_in;   // moments used for the curvature (cleared after use)
-    float *eigv;      // warm-start eigenvectors of Ma, Mb, Cn (J1^2 + J2^2 + J3^2)
-    int32_t *wave_counter;  // dense steps taken so far (selects the waves that re-decompose)
-    float *curv_out;  // platform curvatures for the next wave's rows (I3 J1^2 + I3 J2^2)
-    const float *nk;  // entries of this wave per platform
-    float n_wave, lam, lr, lam_core;
-};
-
-// The core and platform rows after a wave (one CTA), then the platform curvatures
-// C1_k = Gc_k Mb Gc_k^T and C2_k = Gc_k^T Ma Gc_k of the updated G and c_k for the next wave's
-// row steps.  With do_step = 0 only the curvatures are formed.
-__device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
+// The wave-independent half of the dense step, taken during the wave's sweep by one extra
+// CTA of the sweep launch: it needs only values fixed before the sweep (G, the platform rows,
+// the moments of the previous wave end, the wave's platform counts).
+//   * Cn = sum_k n_k c_k c_k^T and the eigen-decompositions of Ma, Mb, Cn (Jacobi sweeps from
+//     the previous eigenbasis every kEigEvery-th wave; in between the eigenbasis is kept and
+//     the eigenvalues refreshed as its Rayleigh quotients) -> eigv, eigval;
+//   * H = G_(3) (Ma kron Mb) G_(3)^T and the inverse of each platform row's system
+//     (4 (n_k H + n_k lambda/|Omega^{3,k}| I) + I/lr) -> ainv (zero for a platform without
+//     entries in the wave);
+//   * the platform curvatures C1_k = Gc_k Mb Gc_k^T, C2_k = Gc_k^T Ma Gc_k (Gc_k = G x3 c_k)
+//     for the wave's row steps -> curv.
+__device__ void dense_pre(const DenseArgs &A, float *sm) {
     const Dims &d = A.d;
     const int J1 = d.J1, J2 = d.J2, J3 = d.J3, I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
-    const int TS = kMaxRank * kTileStride;
+    const int ld = eig_ld(d), TS = eig_tile(d);
     float *sG = sm;                  // PI
     float *sX = sG + PI;             // PI (scratch)
     float *sT = sX + PI;             // PI (scratch)
     float *sC = sT + PI;             // I3*J3
     float *sCn = sC + I3 * J3;       // J3*J3
     float *sH = sCn + J3 * J3;       // J3*J3
-    float *sGk = sH + J3 * J3;       // I3*J3 platform gradients
-    float *sDel = sGk + I3 * J3;     // I3*J3 platform steps
-    float *sMa = sDel + I3 * J3;     // J1*J1
+    float *sMa = sH + J3 * J3;       // J1*J1
     float *sMb = sMa + J1 * J1;      // J2*J2
-    float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles for the eigen-decompositions
-    float *sMacc = sJ + 9 * kMaxRank * kTileStride;  // the wave's M_k, if they fit
-    const int tid = threadIdx.x;
-    // every kEigEvery-th dense step re-decomposes Ma, Mb, Cn (Jacobi sweeps from the previous
-    // eigenbasis); the others keep the eigenbasis and refresh the eigenvalues as its Rayleigh
-    // quotients
+    float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles
+    float *sAk = sJ + 9 * TS;        // I3 x J3 x J3 platform systems
+    const int tid = threadIdx.x, nt = blockDim.x;
     const bool full_eig = (*A.wave_counter % kEigEvery) == 0;
-    const bool stage_m = I3 * Q <= kMaccStage;
-    if (do_step && stage_m)
-        for (int s = tid; s < I3 * Q; s += blockDim.x) sMacc[s] = A.macc[s];
-    const float *Mk = stage_m ? sMacc : A.macc;
-    for (int s = tid; s < PI; s += blockDim.x) sG[s] = A.G[s];
-    for (int s = tid; s < I3 * J3; s += blockDim.x) sC[s] = A.U3[s];
-    for (int s = tid; s < J1 * J1; s += blockDim.x) sMa[s] = A.gram_in[s];
-    for (int s = tid; s < J2 * J2; s += blockDim.x) sMb[s] = A.gram_in[J1 * J1 + s];
+    for (int s = tid; s < PI; s += nt) sG[s] = A.G[s];
+    for (int s = tid; s < I3 * J3; s += nt) sC[s] = A.U3[s];
+    for (int s = tid; s < J1 * J1; s += nt) sMa[s] = A.gram_in[s];
+    for (int s = tid; s < J2 * J2; s += nt) sMb[s] = A.gram_in[J1 * J1 + s];
     __syncthreads();
-    if (do_step) {
-        for (int s = tid; s < J3 * J3; s += blockDim.x) {
-            const int r = s / J3, t = s % J3;
-            float a = 0.f;
-            for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
-            sCn[s] = a;
-        }
-        for (int s = tid; s < PI; s += blockDim.x) {  // X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
-            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-            float a = 0.f;
-            for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
-            sX[s] = a;
-        }
-        for (int s = tid; s < I3 * J3; s += blockDim.x) {
-            const int k = s / J3, r = s % J3;
-            float a = 0.f;
-            const float *M = Mk + (int64_t)k * Q;
-            for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
-            const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
-            sGk[s] = fmaf(reg, sC[s], a);
-        }
-        __syncthreads();
-        const int warp = tid >> 5;
-        if (warp < 3) {  // eigen-decompositions of Ma, Mb, Cn, one warp each
-            const int n = warp == 0 ? J1 : (warp == 1 ? J2 : J3);
-            const float *src = warp == 0 ? sMa : (warp == 1 ? sMb : sCn);
-            float *M = sJ + warp * 3 * TS, *V = M + TS, *T = V + TS;
-            for (int e = (tid & 31); e < n * n; e += 32) M[(e / n) * kTileStride + e % n] = src[e];
-            __syncwarp();
-            float *Vw = A.eigv + (warp == 0 ? 0 : (warp == 1 ? J1 * J1 : J1 * J1 + J2 * J2));
-            warp_jacobi(M, V, T, n, Vw, full_eig ? kJacobiSweeps : 0);
-        }
-        for (int s = tid; s < PI; s += blockDim.x) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
-            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-            float a = 0.f;
-            for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
-            sT[s] = a;
-        }
-        __syncthreads();
-        for (int s = tid; s < J3 * J3; s += blockDim.x) {  // H[r][t] = sum_pq g(p,q,r) T[t][p][q]
-            const int r = s / J3, t = s % J3;
-            float a = 0.f;
-            for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], sT[t * Q + pq], a);
-            sH[s] = a;
-        }
-        __syncthreads();
-        if (tid < I3) {  // platform row k: (nk H + (nk lambda/cnt3 + 1/lr) I) delta = g_k
-            const int k = tid;
-            float *del = sDel + k * J3;
-            const float nk = A.nk[k];
-            if (nk > 0.f) {
-                float Ak[kMaxRank * kMaxRank];  // J3 <= 32; only I3 threads hold one
-                const float reg = A.cnt3[k] > 0 ? nk * A.lam / (float)A.cnt3[k] : 0.f;
-                for (int r = 0; r < J3; ++r)
-                    for (int t = 0; t < J3; ++t)
-                        Ak[r * J3 + t] = kBlocks * (nk * sH[r * J3 + t] + (r == t ? reg : 0.f)) +
-                                         (r == t ? 1.f / A.lr : 0.f);
-                for (int j = 0; j < J3; ++j) {
-                    float dd = Ak[j * J3 + j];
-                    for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
-                    dd = sqrtf(fmaxf(dd, 1e-20f));
-                    Ak[j * J3 + j] = dd;
-                    for (int i = j + 1; i < J3; ++i) {
-                        float x = Ak[i * J3 + j];
-                        for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
-                        Ak[i * J3 + j] = x / dd;
-                    }
+    for (int s = tid; s < J3 * J3; s += nt) {
+        const int r = s / J3, t = s % J3;
+        float a = 0.f;
+        for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
+        sCn[s] = a;
+    }
+    for (int s = tid; s < PI; s += nt) {  // X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
+        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+        float a = 0.f;
+        for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
+        sX[s] = a;
+    }
+    __syncthreads();
+    const int warp = tid >> 5;
+    if (warp < 3) {  // eigen-decompositions of Ma, Mb, Cn, one warp each
+        const int n = warp == 0 ? J1 : (warp == 1 ? J2 : J3);
+        const float *src = warp == 0 ? sMa : (warp == 1 ? sMb : sCn);
+        float *M = sJ + warp * 3 * TS, *V = M + TS, *T = V + TS;
+        for (int e = (tid & 31); e < n * n; e += 32) M[(e / n) * ld + e % n] = src[e];
+        __syncwarp();
+        const int off = warp == 0 ? 0 : (warp == 1 ? J1 * J1 : J1 * J1 + J2 * J2);
+        warp_jacobi(M, V, T, n, ld, A.eigv + off, full_eig ? kJacobiSweeps : 0);
+        const int eoff = warp == 0 ? 0 : (warp == 1 ? J1 : J1 + J2);
+        for (int p = (tid & 31); p < n; p += 32) A.eigval[eoff + p] = M[p * ld + p];
+    }
+    for (int s = tid; s < PI; s += nt) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
+        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+        float a = 0.f;
+        for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
+        sT[s] = a;
+    }
+    __syncthreads();
+    for (int s = tid; s < J3 * J3; s += nt) {  // H[r][t] = sum_pq g(p,q,r) T[t][p][q]
+        const int r = s / J3, t = s % J3;
+        float a = 0.f;
+        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], sT[t * Q + pq], a);
+        sH[s] = a;
+    }
+    __syncthreads();
+    if (tid < I3) {  // platform row k: the inverse of (4 (n_k H + reg I) + I/lr), by Cholesky
+        const int k = tid;
+        float *Ak = sAk + k * J3 * J3;
+        float *inv = A.ainv + (int64_t)k * J3 * J3;
+        const float nk = A.nk[k];
+        if (nk > 0.f) {
+            const float reg = A.cnt3[k] > 0 ? nk * A.lam / (float)A.cnt3[k] : 0.f;
+            for (int r = 0; r < J3; ++r)
+                for (int t = 0; t < J3; ++t)
+                    Ak[r * J3 + t] =
+                        kBlocks * (nk * sH[r * J3 + t] + (r == t ? reg : 0.f)) + (r == t ? 1.f / A.lr : 0.f);
+            for (int j = 0; j < J3; ++j) {
+                float dd = Ak[j * J3 + j];
+                for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
+                dd = sqrtf(fmaxf(dd, 1e-20f));
+                Ak[j * J3 + j] = dd;
+                for (int i = j + 1; i < J3; ++i) {
+                    float x = Ak[i * J3 + j];
+                    for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
+                    Ak[i * J3 + j] = x / dd;
                 }
+            }
+            for (int c = 0; c < J3; ++c) {  // column c of the inverse: L L^T x = e_c
+                float y[kMaxRank];
                 for (int i = 0; i < J3; ++i) {
-                    float x = sGk[k * J3 + i];
-                    for (int q = 0; q < i; ++q) x -= Ak[i * J3 + q] * del[q];
-                    del[i] = x / Ak[i * J3 + i];
+                    float x = i == c ? 1.f : 0.f;
+                    for (int q = 0; q < i; ++q) x -= Ak[i * J3 + q] * y[q];
+                    y[i] = x / Ak[i * J3 + i];
                 }
                 for (int i = J3 - 1; i >= 0; --i) {
-                    float x = del[i];
-                    for (int q = i + 1; q < J3; ++q) x -= Ak[q * J3 + i] * del[q];
-                    del[i] = x / Ak[i * J3 + i];
+                    float x = y[i];
+                    for (int q = i + 1; q < J3; ++q) x -= Ak[q * J3 + i] * y[q];
+                    y[i] = x / Ak[i * J3 + i];
                 }
-            } else {
-                for (int i = 0; i < J3; ++i) del[i] = 0.f;
+                for (int i = 0; i < J3; ++i) inv[i * J3 + c] = y[i];
             }
+        } else {
+            for (int e = 0; e < J3 * J3; ++e) inv[e] = 0.f;
         }
-        // core gradient D into sX
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int pq = s / J3, r = s % J3;
-            float a = 0.f;
-            for (int k = 0; k < I3; ++k) a = fmaf(Mk[(int64_t)k * Q + pq], sC[k * J3 + r], a);
-            sX[s] = fmaf(A.n_wave * A.lam_core, sG[s], a);
-        }
-        __syncthreads();
-        const float *Va = sJ + TS, *Vb = sJ + 3 * TS + TS, *Vc = sJ + 6 * TS + TS;
-        const float *Ma_e = sJ, *Mb_e = sJ + 3 * TS, *Mc_e = sJ + 6 * TS;  // eigenvalues on diagonals
-        // D <- D x1 Va^T x2 Vb^T x3 Vc^T   (index s = (p*J2 + q)*J3 + r)
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[pp * kTileStride + p], sX[(pp * J2 + q) * J3 + r], a);
-            sT[s] = a;
-        }
-        __syncthreads();
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[qq * kTileStride + q], sT[(p * J2 + qq) * J3 + r], a);
-            sX[s] = a;
-        }
-        __syncthreads();
-        const float diag = 1.f / A.lr + kBlocks * A.n_wave * A.lam_core;
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[rr * kTileStride + r], sX[(p * J2 + q) * J3 + rr], a);
-            const float la = fmaxf(Ma_e[p * kTileStride + p], 0.f), lb = fmaxf(Mb_e[q * kTileStride + q], 0.f),
-                        lc = fmaxf(Mc_e[r * kTileStride + r], 0.f);
-            sT[s] = a / (kBlocks * la * lb * lc + diag);
-        }
-        __syncthreads();
-        // back: D <- D x1 Va x2 Vb x3 Vc
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[p * kTileStride + pp], sT[(pp * J2 + q) * J3 + r], a);
-            sX[s] = a;
-        }
-        __syncthreads();
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[q * kTileStride + qq], sX[(p * J2 + qq) * J3 + r], a);
-            sT[s] = a;
-        }
-        __syncthreads();
-        for (int s = tid; s < PI; s += blockDim.x) {
-            const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
-            float a = 0.f;
-            for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[r * kTileStride + rr], sT[(p * J2 + q) * J3 + rr], a);
-            sG[s] -= a;
-            A.G[s] = sG[s];
-        }
-        for (int s = tid; s < I3 * J3; s += blockDim.x) {
-            sC[s] -= sDel[s];
-            A.U3[s] = sC[s];
-        }
-        __syncthreads();
-        for (int s = tid; s < I3 * Q; s += blockDim.x) A.macc[s] = 0.f;
-        if (tid == 0) *A.wave_counter += 1;
     }
-    // platform curvatures for the next wave's row steps (updated G, c; moments of gram_in):
-    // all platforms at once when their Gc and W fit in the two PI-sized scratch buffers
+    // platform curvatures for the wave's row steps (moments of gram_in): all platforms at once
+    // when their Gc and W fit in the two PI-sized scratch buffers
     float *sGc = sX, *sW = sT;
     const int kb = (I3 * Q <= PI) ? I3 : 1;  // platforms per batch
     for (int k0 = 0; k0 < I3; k0 += kb) {
         const int nkb = min(kb, I3 - k0);
-        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // Gc_k = G x3 c_k
+        for (int s = tid; s < nkb * Q; s += nt) {  // Gc_k = G x3 c_k
             const int k = k0 + s / Q, pq = s % Q;
             float a = 0.f;
             for (int r = 0; r < J3; ++r) a = fmaf(sG[pq * J3 + r], sC[k * J3 + r], a);
             sGc[s] = a;
         }
         __syncthreads();
-        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // W1 = Gc Mb  (J1 x J2)
+        for (int s = tid; s < nkb * Q; s += nt) {  // W1 = Gc Mb  (J1 x J2)
             const int b = s / Q, p = (s % Q) / J2, q = s % J2;
             float a = 0.f;
             for (int qq = 0; qq < J2; ++qq) a = fmaf(sGc[b * Q + p * J2 + qq], sMb[qq * J2 + q], a);
             sW[s] = a;
         }
         __syncthreads();
-        for (int s = tid; s < nkb * J1 * J1; s += blockDim.x) {  // C1 = W1 Gc^T
+        for (int s = tid; s < nkb * J1 * J1; s += nt) {  // C1 = W1 Gc^T
             const int b = s / (J1 * J1), p = (s / J1) % J1, t = s % J1;
             float a = 0.f;
             for (int q = 0; q < J2; ++q) a = fmaf(sW[b * Q + p * J2 + q], sGc[b * Q + t * J2 + q], a);
-            A.curv_out[(int64_t)(k0 + b) * J1 * J1 + p * J1 + t] = a;
+            A.curv[(int64_t)(k0 + b) * J1 * J1 + p * J1 + t] = a;
         }
         __syncthreads();
-        for (int s = tid; s < nkb * Q; s += blockDim.x) {  // W2 = Ma Gc  (J1 x J2)
+        for (int s = tid; s < nkb * Q; s += nt) {  // W2 = Ma Gc  (J1 x J2)
             const int b = s / Q, p = (s % Q) / J2, q = s % J2;
             float a = 0.f;
             for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sGc[b * Q + pp * J2 + q], a);
             sW[s] = a;
         }
         __syncthreads();
-        float *C2 = A.curv_out + (int64_t)I3 * J1 * J1;
-        for (int s = tid; s < nkb * J2 * J2; s += blockDim.x) {  // C2 = Gc^T W2
+        float *C2 = A.curv + (int64_t)I3 * J1 * J1;
+        for (int s = tid; s < nkb * J2 * J2; s += nt) {  // C2 = Gc^T W2
             const int b = s / (J2 * J2), q = (s / J2) % J2, t = s % J2;
             float a = 0.f;
             for (int p = 0; p < J1; ++p) a = fmaf(sGc[b * Q + p * J2 + q], sW[b * Q + p * J2 + t], a);
@@ -1107,8 +1209,111 @@ __device__ void wave_dense(const DenseArgs &A, int do_step, float *sm) {
         }
         __syncthreads();
     }
-    if (do_step)
-        for (int s = tid; s < J1 * J1 + J2 * J2; s += blockDim.x) A.gram_in[s] = 0.f;
+}
+
+// The rest of the dense step at the end of the wave (one CTA), with the wave's M_k:
+//   platform gradients g_k = G_(3) vec(M_k) + reg c_k and steps delta_k = ainv_k g_k;
+//   core gradient D = sum_k M_k kron c_k + n lambda/|Omega| G, solved in the eigenbases:
+//   G <- G - (Va, Vb, Vc) [ (D x1 Va^T x2 Vb^T x3 Vc^T) / (4 la lb lc + diag) ];
+//   then the moments of the previous wave end are cleared for reuse.
+__device__ void dense_post(const DenseArgs &A, float *sm) {
+    const Dims &d = A.d;
+    const int J1 = d.J1, J2 = d.J2, J3 = d.J3, I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
+    const int ld = eig_ld(d);
+    float *sG = sm;                  // PI
+    float *sX = sG + PI;             // PI (scratch)
+    float *sT = sX + PI;             // PI (scratch)
+    float *sC = sT + PI;             // I3*J3
+    float *sGk = sC + I3 * J3;       // I3*J3 platform gradients
+    float *sDel = sGk + I3 * J3;     // I3*J3 platform steps
+    float *Va = sDel + I3 * J3;      // J1 x ld
+    float *Vb = Va + J1 * ld;        // J2 x ld
+    float *Vc = Vb + J2 * ld;        // J3 x ld
+    float *la = Vc + J3 * ld;        // J1 + J2 + J3 eigenvalues
+    float *sMacc = la + J1 + J2 + J3;  // the wave's M_k, if they fit
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const bool stage_m = I3 * Q <= kMaccStage;
+    if (stage_m)
+        for (int s = tid; s < I3 * Q; s += nt) sMacc[s] = A.macc[s];
+    const float *Mk = stage_m ? sMacc : A.macc;
+    for (int s = tid; s < PI; s += nt) sG[s] = A.G[s];
+    for (int s = tid; s < I3 * J3; s += nt) sC[s] = A.U3[s];
+    for (int s = tid; s < J1 * J1; s += nt) Va[(s / J1) * ld + s % J1] = A.eigv[s];
+    for (int s = tid; s < J2 * J2; s += nt) Vb[(s / J2) * ld + s % J2] = A.eigv[J1 * J1 + s];
+    for (int s = tid; s < J3 * J3; s += nt) Vc[(s / J3) * ld + s % J3] = A.eigv[J1 * J1 + J2 * J2 + s];
+    for (int s = tid; s < J1 + J2 + J3; s += nt) la[s] = fmaxf(A.eigval[s], 0.f);
+    __syncthreads();
+    const float *lb = la + J1, *lc = la + J1 + J2;
+    for (int s = tid; s < I3 * J3; s += nt) {  // platform gradients
+        const int k = s / J3, r = s % J3;
+        float a = 0.f;
+        const float *M = Mk + (int64_t)k * Q;
+        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
+        const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
+        sGk[s] = fmaf(reg, sC[s], a);
+    }
+    for (int s = tid; s < PI; s += nt) {  // core gradient D
+        const int pq = s / J3, r = s % J3;
+        float a = 0.f;
+        for (int k = 0; k < I3; ++k) a = fmaf(Mk[(int64_t)k * Q + pq], sC[k * J3 + r], a);
+        sX[s] = fmaf(A.n_wave * A.lam_core, sG[s], a);
+    }
+    __syncthreads();
+    for (int s = tid; s < I3 * J3; s += nt) {  // platform steps
+        const int k = s / J3, r = s % J3;
+        const float *inv = A.ainv + (int64_t)k * J3 * J3 + r * J3;
+        float a = 0.f;
+        for (int t = 0; t < J3; ++t) a = fmaf(inv[t], sGk[k * J3 + t], a);
+        sDel[s] = a;
+    }
+    // D <- D x1 Va^T x2 Vb^T x3 Vc^T   (index s = (p*J2 + q)*J3 + r)
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[pp * ld + p], sX[(pp * J2 + q) * J3 + r], a);
+        sT[s] = a;
+    }
+    __syncthreads();
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[qq * ld + q], sT[(p * J2 + qq) * J3 + r], a);
+        sX[s] = a;
+    }
+    __syncthreads();
+    const float diag = 1.f / A.lr + kBlocks * A.n_wave * A.lam_core;
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[rr * ld + r], sX[(p * J2 + q) * J3 + rr], a);
+        sT[s] = a / (kBlocks * la[p] * lb[q] * lc[r] + diag);
+    }
+    __syncthreads();
+    // back: D <- D x1 Va x2 Vb x3 Vc
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[p * ld + pp], sT[(pp * J2 + q) * J3 + r], a);
+        sX[s] = a;
+    }
+    __syncthreads();
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[q * ld + qq], sX[(p * J2 + qq) * J3 + r], a);
+        sT[s] = a;
+    }
+    __syncthreads();
+    for (int s = tid; s < PI; s += nt) {
+        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        float a = 0.f;
+        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[r * ld + rr], sT[(p * J2 + q) * J3 + rr], a);
+        A.G[s] = sG[s] - a;
+    }
+    for (int s = tid; s < I3 * J3; s += nt) A.U3[s] = sC[s] - sDel[s];
+    for (int s = tid; s < I3 * Q; s += nt) A.macc[s] = 0.f;
+    for (int s = tid; s < J1 * J1 + J2 * J2; s += nt) A.gram_in[s] = 0.f;
+    if (tid == 0) *A.wave_counter += 1;
 }
 
 struct RowArgs {
@@ -1121,10 +1326,9 @@ struct RowArgs {
     float *gram_out;
 };
 
-// End of a wave.  mode 0: CTA 0 = core and platform rows (curvature from the previous wave's
-// moments) + next curvatures, CTAs 1.. = patient and gene rows (curvatures of the previous
-// wave) + new moments.  mode 1 (set-up): rows form moments only.  mode 2 (set-up): CTA 0
-// forms the curvatures only.
+// End of a wave.  mode 0: CTA 0 = the rest of the core and platform-row step (dense_post),
+// CTAs 1.. = patient and gene rows (curvatures from the wave's pre-work) + new moments.
+// mode 1 (set-up): rows form moments only.
 // The row step runs one thread per row when both row ranks are compile-time (CJ1, CJ2 > 0),
 // one warp per row otherwise; R.nb1 CTAs cover the patient rows, the rest the gene rows.
 template <int CJ1, int CJ2>
@@ -1151,7 +1355,7 @@ template <int CJ1, int CJ2>
 __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
     extern __shared__ __align__(16) float smw[];
     if (blockIdx.x == 0) {
-        if (mode != 1) wave_dense(A, mode == 0, smw);
+        if (mode == 0) dense_post(A, smw);
         return;
     }
     wave_end_rows<CJ1, CJ2>(A, R, blockIdx.x - 1, mode, smw);
@@ -1179,7 +1383,7 @@ __global__ void __launch_bounds__(256)
     const DenseArgs A = dargs[pid];
     const RowArgs R = rargs[pid];
     if (local == 0) {
-        wave_dense(A, 1, smw);
+        dense_post(A, smw);
         return;
     }
     wave_end_rows<CJ1, CJ2>(A, R, local - 1, 0, smw);
@@ -1205,16 +1409,17 @@ cudaError_t launch_wave_end_k(Ctx *c, const DenseArgs &A, RowArgs R, int mode, s
     const int rpc = rows_per_cta<CJ1, CJ2>();
     R.nb1 = ceil_div(c->d.I1, rpc);
     const int nb2 = ceil_div(c->d.I2, rpc);
-    const unsigned grid = mode == 2 ? 1u : (unsigned)(1 + R.nb1 + nb2);
+    const unsigned grid = (unsigned)(1 + R.nb1 + nb2);
     k_fast_wave_end<CJ1, CJ2><<<grid, 256, smem, c->stream>>>(A, R, mode);
     return cudaGetLastError();
 }
 
+// the sweep's shared memory, or the dense pre-work's if larger (one CTA of the launch runs it)
 template <int CJ1, int CJ2, int CJ3>
 size_t sweep_smem(const Ctx *c) {
     const int J1P = even_up(c->d.J1), J2P = even_up(c->d.J2);
-    return sizeof(float) * ((size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) +
-                            (size_t)kFastThreads * (J1P + J2P + 4));
+    const size_t sweep = (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) + (size_t)kFastThreads * (J1P + J2P + 4);
+    return sizeof(float) * std::max<size_t>(sweep, (size_t)dense_pre_floats(c->d));
 }
 
 template <int CJ1, int CJ2, int CJ3>
@@ -1238,8 +1443,7 @@ cudaError_t init_sweep(Ctx *c) {
 int row_stride(int J, int I3) { return ((J + 3) & ~3) + ((I3 + 3) & ~3); }
 
 size_t sweep_tc_smem(const Ctx *c) {
-    const size_t M = 128, J1 = c->d.J1, J2 = c->d.J2;
-    return 2 * (M * J1 + M * J2 + J2 * M + M * M + 2 * J1 * J2) + sizeof(float) * (size_t)c->PI;
+    return std::max<size_t>(tc_smem_bytes(c->d.J1, c->d.J2, (int)c->PI), sizeof(float) * dense_pre_floats(c->d));
 }
 
 template <int CJ1, int CJ2>
@@ -1258,7 +1462,8 @@ cudaError_t init_sweep_tc(Ctx *c) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return e;
-    c->fast_grid = std::max(1, std::min(per_sm, 4)) * sms;  // TMEM: 4 x 128 columns per SM
+    // TMEM: 512 columns per SM shared by the resident CTAs
+    c->fast_grid = std::max(1, std::min(per_sm, 512 / tc_tmem_cols<CJ1, CJ2>())) * sms;
     return cudaSuccess;
 }
 
@@ -1273,6 +1478,8 @@ cudaError_t launch_sweep_tc(Ctx *c, const FastArgs &A, int grid) {
     k_fast_sweep_tc<CJ1, CJ2><<<grid, 128, sweep_tc_smem(c), c->stream>>>(A);
     return cudaGetLastError();
 }
+
+void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowArgs *Rp);
 
 FastArgs make_fast_args(Ctx *c, int64_t w) {
     const int64_t t0 = c->wave_tile[w], nt = c->wave_tile[w + 1] - t0;
@@ -1297,6 +1504,8 @@ FastArgs make_fast_args(Ctx *c, int64_t w) {
     A.rs1 = row_stride(c->d.J1, c->d.I3);
     A.rs2 = row_stride(c->d.J2, c->d.I3);
     A.err = c->flag + 3;
+    RowArgs unused;
+    make_wave_args(c, w, (int)(w & 1), 0, &A.pre, &unused);
     return A;
 }
 
@@ -1304,8 +1513,8 @@ template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_sweep(Ctx *c, int64_t w) {
     const FastArgs A = make_fast_args(c, w);
     const int64_t nt = A.n_tiles;
-    if (nt == 0) return cudaSuccess;
-    const int grid = (int)std::min<int64_t>(c->fast_grid, nt);
+    // CTA 0 takes the wave's dense pre-work, the others the tiles (one resident wave of CTAs)
+    const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - 1), nt) + 1;
     c->launches++;
     if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
     k_fast_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
@@ -1314,10 +1523,7 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
 
 size_t wave_end_smem(const Ctx *c) {
     const Dims &d = c->d;
-    const size_t tiles = 9 * (size_t)kMaxRank * kTileStride;
-    const size_t mstage = std::min<size_t>((size_t)d.I3 * d.J1 * d.J2, kMaccStage);
-    const size_t dense = 3 * (size_t)c->PI + 3 * d.I3 * d.J3 + 2 * d.J3 * d.J3 + d.J1 * d.J1 + d.J2 * d.J2 + tiles +
-                         mstage;
+    const size_t dense = (size_t)dense_post_floats(d);
     const size_t rows = std::max<size_t>(kRowWarps * ((size_t)kMaxRank * kTileStride + 2 * kMaxRank) +
                                              kRowWarps * (size_t)kMaxRank * kMaxRank + kCkStage,
                                          (size_t)kRowsPerThreadCta * (std::max(d.J1, d.J2) + 1) + kCkStage);
@@ -1339,8 +1545,10 @@ void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowA
     A.macc = c->macc;
     A.gram_in = c->gram + (size_t)(parity ^ 1) * c->gram_stride;
     A.eigv = c->gram + 2 * (size_t)c->gram_stride;
+    A.eigval = A.eigv + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3;
+    A.ainv = A.eigval + d.J1 + d.J2 + d.J3;
     A.wave_counter = c->flag + 2;
-    A.curv_out = c->curv + (size_t)parity * curv_stride(c);
+    A.curv = c->curv;
     A.nk = c->wave_nk + (w >= 0 ? w : 0) * d.I3;
     A.n_wave = w >= 0 ? (float)c->wave_len[w] : 0.f;
     A.lam = c->cfg.lambda;
@@ -1356,12 +1564,9 @@ void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowA
     R.cnt2 = c->cnt[1];
     R.inv_n = c->nnz ? 1.f / (float)c->nnz : 0.f;
     R.nb1 = 0;  // set by the launcher for its row step
-    R.curv_in = c->curv + (size_t)(parity ^ 1) * curv_stride(c);
+    R.curv_in = c->curv;
     R.gram_out = c->gram + (size_t)parity * c->gram_stride;
-    if (mode == 2) {  // set-up: curvatures from the moments just formed into buffer `parity`
-        A.gram_in = c->gram + (size_t)parity * c->gram_stride;
-        A.curv_out = c->curv + (size_t)parity * curv_stride(c);
-    }
+    (void)mode;
 }
 
 cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
@@ -1381,12 +1586,14 @@ int init_fast(Ctx *c) {
     SNECT_CUDA(c, cudaMemsetAsync(c->macc, 0, sizeof(float) * d.I3 * d.J1 * d.J2, c->stream));
     // moments: two buffers (this wave's, the previous wave's) + warm-start eigenvectors
     c->gram_stride = ((int64_t)d.J1 * d.J1 + d.J2 * d.J2 + 3) & ~3;
-    const int64_t gf = 2 * c->gram_stride + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3;
+    // + eigenvectors and eigenvalues of Ma, Mb, Cn + the platform systems' inverses
+    const int64_t gf = 2 * c->gram_stride + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3 + d.J1 + d.J2 + d.J3 +
+                       (int64_t)d.I3 * d.J3 * d.J3;
     SNECT_CUDA(c, cudaMalloc((void **)&c->gram, sizeof(float) * gf));
     SNECT_CUDA(c, cudaMemsetAsync(c->gram, 0, sizeof(float) * gf, c->stream));
-    // platform curvatures for the row steps, two buffers
-    SNECT_CUDA(c, cudaMalloc((void **)&c->curv, sizeof(float) * 2 * curv_stride(c)));
-    SNECT_CUDA(c, cudaMemsetAsync(c->curv, 0, sizeof(float) * 2 * curv_stride(c), c->stream));
+    // platform curvatures for the row steps (formed by each wave's pre-work)
+    SNECT_CUDA(c, cudaMalloc((void **)&c->curv, sizeof(float) * curv_stride(c)));
+    SNECT_CUDA(c, cudaMemsetAsync(c->curv, 0, sizeof(float) * curv_stride(c), c->stream));
     for (int n = 0; n < 2; ++n) {
         const int64_t nf = (int64_t)(n ? d.I2 : d.I1) * row_stride(n ? d.J2 : d.J1, d.I3);
         SNECT_CUDA(c, cudaMalloc((void **)&c->gacc[n], sizeof(float) * nf));
@@ -1399,10 +1606,9 @@ int init_fast(Ctx *c) {
     }
     SNECT_CUDA(c, cudaMemsetAsync(c->flag + 2, 0, 2 * sizeof(int32_t), c->stream));
     SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, set_wave_end_attr, c, wave_end_smem(c)));
-    // the first wave's curvature: moments of the initial rows into the odd buffer, then the
-    // platform curvatures from them
+    // the first wave's moments: those of the initial rows, into the odd buffer (the first
+    // wave's pre-work forms its curvatures and eigenbases from them)
     SNECT_CUDA(c, launch_wave_end(c, -1, 1, 1));
-    SNECT_CUDA(c, launch_wave_end(c, -1, 1, 2));
     return timing_events(c, c->n_waves);
 }
 
@@ -1457,6 +1663,8 @@ struct Batch {
     RowArgs *d_rows = nullptr;    // [n_waves][P]
     int32_t *d_boff = nullptr;    // [P + 1] CTA offsets of the wave end
     int32_t *d_ctr = nullptr;     // [n_waves]
+    EdgeArgs *d_edge = nullptr;   // [P] network passes
+    int64_t edge_cells = 0, edge_heavy = 0;  // largest I2 * J2 and hub count over the problems
     std::vector<int32_t> tiles_per_wave;
     int32_t wave_end_blocks = 0;
     int64_t epoch_kernels = 0;  // kernels in one epoch's graph
@@ -1472,8 +1680,8 @@ template <int CJ1, int CJ2, int CJ3>
 cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
     Ctx *c0 = b->ctx[0];
     const int nt = b->tiles_per_wave[w];
-    if (nt == 0) return cudaSuccess;
-    const int grid = std::min(c0->fast_grid, nt);
+    // one CTA per problem for its dense pre-work, then the tile CTAs
+    const int grid = std::min(std::max(1, c0->fast_grid - b->P), nt) + b->P;
     k_batch_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c0), st>>>(
         b->d_fast + w * b->P, b->d_toff + w * (b->P + 1), b->P, b->d_ctr + w);
     return cudaGetLastError();
@@ -1526,18 +1734,10 @@ int batch_build_graph(Batch *b) {
         for (int64_t w = 0; w < b->n_waves && e == cudaSuccess; ++w) {
             e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_sweep_k, b, w, cap);
             if (e == cudaSuccess) e = SNECT_DISPATCH_ROWS(d.J1, d.J2, batch_wave_end_k, b, w, cap);
-            b->epoch_kernels += (b->tiles_per_wave[w] > 0) + 1;
+            b->epoch_kernels += 2;
         }
-        for (Ctx *c : b->ctx) {  // each problem's network pass
-            if (e != cudaSuccess) break;
-            cudaStream_t orig = c->stream;
-            const int64_t before = c->launches;
-            c->stream = cap;
-            e = launch_edge_pass(c);
-            c->stream = orig;
-            b->epoch_kernels += c->launches - before;
-            c->launches = before;  // counted by the batch
-        }
+        if (e == cudaSuccess)  // every problem's network pass
+            e = launch_batch_edge_pass(b->d_edge, b->P, b->edge_cells, b->edge_heavy, cap, &b->epoch_kernels);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -1559,6 +1759,7 @@ void batch_free(Batch *b) {
     cudaFree(b->d_rows);
     cudaFree(b->d_boff);
     cudaFree(b->d_ctr);
+    cudaFree(b->d_edge);
 }
 
 thread_local std::string g_batch_error;
@@ -1632,6 +1833,13 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     up((void **)&b->d_rows, hr.data(), sizeof(RowArgs) * hr.size());
     up((void **)&b->d_toff, toff.data(), sizeof(int32_t) * toff.size());
     up((void **)&b->d_boff, boff.data(), sizeof(int32_t) * boff.size());
+    std::vector<EdgeArgs> he;
+    for (Ctx *c : b->ctx) {
+        he.push_back(make_edge_args(c));
+        b->edge_cells = std::max<int64_t>(b->edge_cells, (int64_t)he.back().I2 * he.back().J2);
+        b->edge_heavy = std::max<int64_t>(b->edge_heavy, he.back().n_heavy);
+    }
+    up((void **)&b->d_edge, he.data(), sizeof(EdgeArgs) * he.size());
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctr, sizeof(int32_t) * std::max<int64_t>(1, W));
     if (e == cudaSuccess) e = SNECT_DISPATCH_RANKS(b->d.J1, b->d.J2, b->d.J3, batch_sweep_attr, b);
     if (e != cudaSuccess) {
