@@ -339,6 +339,181 @@ __device__ __forceinline__ TileFetch fetch_tile(const FastArgs &A, int t) {
     return f;
 }
 
+// ---------------------------------------------------------------------------------------
+// Per-patient factoring of a tile's contraction (compile-time J1, J2 <= 16).
+//
+// The entries of a tile share the platform k, and inside a wave and platform they are sorted
+// by patient, so a warp's 32 entries fall into a few runs of one patient i each (a_i fixed).
+// For a run the contraction factors through a_i:
+//   w2 = Gc^T a_i (once per run),  x~_e = a_i^T Gc b_e = w2 . b_e,  r_e = x~_e - x_e
+//   gene rows:    g(b_e) += r_e w2 + lambda/|Omega^{2,j}| b_e          (per entry)
+//   s = sum_e r_e b_e                                                  (run sum)
+//   patient row:  g(a_i) += Gc s + n_run lambda/|Omega^{1,i}| a_i       (= sum_e r_e Gc b_e + ...)
+//   M_k += a_i s^T                                                     (= sum_e r_e a_i b_e^T)
+// so the per-entry work is O(J2) and the J1 x J2 products are paid once per run.  Vectors of
+// the run are spread over the warp (lane l holds component l / 2) by recursive-halving
+// reductions.
+
+template <int CJ1, int CJ2>
+__host__ __device__ constexpr bool runs_path() { return CJ1 > 0 && CJ2 > 0 && CJ1 <= 16 && CJ2 <= 16; }
+
+// sum over the 32 lanes of v[0..16): lane l returns the total of component l >> 1
+__device__ __forceinline__ float reduce_scatter16(const float (&v)[16]) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float h8[8], h4[4], h2[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h8[i] = (b4 ? v[i + 8] : v[i]) + __shfl_xor_sync(FULL, b4 ? v[i] : v[i + 8], 16);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h4[i] = (b3 ? h8[i + 4] : h8[i]) + __shfl_xor_sync(FULL, b3 ? h8[i] : h8[i + 4], 8);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) h2[i] = (b2 ? h4[i + 2] : h4[i]) + __shfl_xor_sync(FULL, b2 ? h4[i] : h4[i + 2], 4);
+    float h = (b1 ? h2[1] : h2[0]) + __shfl_xor_sync(FULL, b1 ? h2[0] : h2[1], 2);
+    return h + __shfl_xor_sync(FULL, h, 1);
+}
+
+// rows of M_k one lane accumulates: column l / 2, rows of parity l % 2
+template <int CJ1>
+struct MRows {
+    static constexpr int n = (CJ1 + 1) / 2;
+};
+
+// This warp's entries of a tile of platform k (e, valid: the lane's entry), run by run.  Every
+// lane of the warp calls this.  mreg: the lane's share of the CTA's M_k.
+template <int CJ1, int CJ2>
+__device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool valid, int k,
+                                          const float *__restrict__ sGc, float (&mreg)[MRows<CJ1>::n]) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int J1 = CJ1, J2 = CJ2;
+    constexpr int JA = (J1 + 3) & ~3, JB = (J2 + 3) & ~3;
+    const int lane = threadIdx.x & 31;
+    const int q = lane >> 1;      // this lane's component of the spread vectors
+    const int par = lane & 1;     // parity of the M_k rows this lane accumulates
+    float b[J2];
+    float x = 0.f;
+    int ej = 0;
+    if (valid) {
+        ej = e.j;
+        x = e.x;
+        const float *ub = A.U2 + (int64_t)e.j * J2;
+        if constexpr (J2 % 2 == 0) {
+#pragma unroll
+            for (int qq = 0; qq < J2; qq += 2) {
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(ub + qq));
+                b[qq] = t2.x;
+                b[qq + 1] = t2.y;
+            }
+        } else {
+#pragma unroll
+            for (int qq = 0; qq < J2; ++qq) b[qq] = __ldg(ub + qq);
+        }
+    } else {
+#pragma unroll
+        for (int qq = 0; qq < J2; ++qq) b[qq] = 0.f;
+    }
+    const int iv = valid ? e.i : -1;
+    unsigned rem = __ballot_sync(FULL, valid);
+    while (rem) {  // warp-uniform: one run (one patient) per pass
+        const int ih = __shfl_sync(FULL, iv, __ffs(rem) - 1);
+        const unsigned run = __ballot_sync(FULL, iv == ih);
+        rem &= ~run;
+        const bool mine = (run >> lane) & 1u;
+        // the run's patient row: one address for the whole warp
+        float a[J1];
+        const float *ua = A.U1 + (int64_t)ih * J1;
+        if constexpr (J1 % 2 == 0) {
+#pragma unroll
+            for (int p = 0; p < J1; p += 2) {
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(ua + p));
+                a[p] = t2.x;
+                a[p + 1] = t2.y;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < J1; ++p) a[p] = __ldg(ua + p);
+        }
+        // w2 = Gc^T a: component q in lanes 2q, 2q + 1, then gathered by every lane
+        float wq = 0.f;
+        if (q < J2) {
+#pragma unroll
+            for (int p = 0; p < J1; ++p) wq = fmaf(sGc[p * J2 + q], a[p], wq);
+        }
+        float w2[J2];
+#pragma unroll
+        for (int qq = 0; qq < J2; ++qq) w2[qq] = __shfl_sync(FULL, wq, 2 * qq);
+        // the lane's entry, if it is in this run: residual and gene-row gradient
+        float r = 0.f;
+        if (mine) {
+            float xt = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < J2; ++qq) xt = fmaf(w2[qq], b[qq], xt);
+            r = xt - x;
+            const float lb = A.lam / (float)__ldg(A.cnt2 + ej);
+            float gvb[JB];
+#pragma unroll
+            for (int qq = 0; qq < JB; ++qq) gvb[qq] = qq < J2 ? fmaf(r, w2[qq], lb * b[qq]) : 0.f;
+            float *gb = A.gB + (int64_t)ej * A.rs2;
+#pragma unroll
+            for (int t4 = 0; t4 < JB / 4; ++t4)
+                atomicAdd(reinterpret_cast<float4 *>(gb) + t4,
+                          make_float4(gvb[4 * t4], gvb[4 * t4 + 1], gvb[4 * t4 + 2], gvb[4 * t4 + 3]));
+            atomicAdd(gb + JB + k, 1.f);
+        }
+        // s = sum over the run of r_e b_e (lanes outside the run give 0): lane l gets s[l / 2]
+        float u[16];
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) u[qq] = qq < J2 ? r * b[qq] : 0.f;
+        const float s_q = reduce_scatter16(u);
+        // M_k += a s^T: rows p = par, par + 2, ... of column q
+        if (q < J2) {
+#pragma unroll
+            for (int t = 0; t < MRows<CJ1>::n; ++t) {
+                const float ap = par ? (2 * t + 1 < J1 ? a[2 * t + 1 < J1 ? 2 * t + 1 : 0] : 0.f) : a[2 * t];
+                mreg[t] = fmaf(ap, s_q, mreg[t]);
+            }
+        }
+        // patient gradient Gc s + n_run la a: (Gc s)[p] = sum_q Gc[p][q] s[q], summed over the
+        // even lanes (one per component q)
+        float tv[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) tv[p] = (p < J1 && q < J2 && !par) ? sGc[p * J2 + (q < J2 ? q : 0)] * s_q : 0.f;
+        const float gcs = reduce_scatter16(tv);  // lane l: (Gc s)[l / 2]
+        if (!par && q < J1) {
+            float aq = 0.f;
+#pragma unroll
+            for (int p = 0; p < J1; ++p) aq = p == q ? a[p] : aq;
+            const float la = A.lam / (float)__ldg(A.cnt1 + ih);
+            float *ga = A.gA + (int64_t)ih * A.rs1;
+            atomicAdd(ga + q, fmaf((float)__popc(run) * la, aq, gcs));
+            if (lane == 0) atomicAdd(ga + JA + k, (float)__popc(run));
+        }
+    }
+}
+
+// merges the warps' shares of M_k (staged through sMw, one J1 x J2 block per warp) into macc
+template <int CJ1, int CJ2>
+__device__ __forceinline__ void runs_merge(float (&mreg)[MRows<CJ1>::n], float *sMw, float *__restrict__ macc) {
+    constexpr int J1 = CJ1, J2 = CJ2, Q = J1 * J2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 1, par = lane & 1;
+    if (q < J2) {
+#pragma unroll
+        for (int t = 0; t < MRows<CJ1>::n; ++t) {
+            const int p = 2 * t + par;
+            if (p < J1) sMw[warp * Q + p * J2 + q] = mreg[t];
+            mreg[t] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < Q; s += kFastThreads) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFastThreads / 32; ++w) sum += sMw[w * Q + s];
+        atomicAdd(macc + s, sum);
+    }
+}
+
 // CTAs per SM the register budget is cut for (more entries in flight hide the gathers)
 template <int CJ1, int CJ2>
 constexpr int sweep_min_blocks() {
@@ -364,6 +539,33 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
     __shared__ int sTile[2];
     const int tid = threadIdx.x;
     for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
+    if constexpr (runs_path<CJ1, CJ2>()) {  // per-patient-run factoring; M_k shares in registers
+        float *sMw = sGc + align4(J1 * J2);    // (kFastThreads / 32) x J1*J2: the M_k merge
+        float mreg[MRows<CJ1>::n];
+#pragma unroll
+        for (int t = 0; t < MRows<CJ1>::n; ++t) mreg[t] = 0.f;
+        if (tid == 0) sTile[0] = atomicAdd(A.ctr, 1);
+        __syncthreads();
+        int t = sTile[0], par = 0;
+        TileFetch f = fetch_tile(A, t);
+        int cur_k = -1;
+        for (;;) {
+            const bool done = t >= A.n_tiles;
+            if (tid == 0 && !done) sTile[par ^ 1] = atomicAdd(A.ctr, 1);
+            if (f.k != cur_k || done) {
+                if (cur_k >= 0) runs_merge<CJ1, CJ2>(mreg, sMw, A.macc + (int64_t)cur_k * J1 * J2);
+                if (done) break;
+                form_gc(sG, A.U3 + (int64_t)f.k * J3, sGc, J1, J2, J3);
+                cur_k = f.k;
+                __syncthreads();
+            }
+            warp_runs<CJ1, CJ2>(A, f.e, f.valid, f.k, sGc, mreg);
+            __syncthreads();  // the next claim is visible; sGc and sMw free for reuse
+            t = sTile[par ^ 1];
+            par ^= 1;
+            f = fetch_tile(A, t);
+        }
+    } else {
     const MLayout ml(J1P, J2P);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 
@@ -391,6 +593,7 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
         f = fetch_tile(A, t);
         m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
         __syncthreads();  // sRA, sB consumed
+    }
     }
 }
 
@@ -451,6 +654,37 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
     int pid = sPid[0], t = sTile[0], par = 0;
     TileFetch f = fetch(pid, t);
     int cur_k = -1, cur_pid = -1;
+    if constexpr (runs_path<CJ1, CJ2>()) {  // per-patient-run factoring, as in k_fast_sweep
+        float *sMw = sGc + align4(J1 * J2);
+        float mreg[MRows<CJ1>::n];
+#pragma unroll
+        for (int i = 0; i < MRows<CJ1>::n; ++i) mreg[i] = 0.f;
+        for (;;) {
+            const bool done = pid < 0;
+            if (tid == 0 && !done) claim(par ^ 1);
+            if (f.k != cur_k || pid != cur_pid || done) {
+                if (cur_k >= 0) runs_merge<CJ1, CJ2>(mreg, sMw, A.macc + (int64_t)cur_k * J1 * J2);
+                if (done) break;
+                if (pid != cur_pid) {
+                    __syncthreads();
+                    if (tid == 0) sArgs = probs[pid];
+                    __syncthreads();
+                    for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
+                    __syncthreads();
+                    cur_pid = pid;
+                }
+                form_gc(sG, A.U3 + (int64_t)f.k * J3, sGc, J1, J2, J3);
+                cur_k = f.k;
+                __syncthreads();
+            }
+            warp_runs<CJ1, CJ2>(A, f.e, f.valid, f.k, sGc, mreg);
+            __syncthreads();
+            pid = sPid[par ^ 1];
+            t = sTile[par ^ 1];
+            par ^= 1;
+            f = fetch(pid, t);
+        }
+    } else {
     for (;;) {
         const bool done = pid < 0;
         if (tid == 0 && !done) claim(par ^ 1);
@@ -478,6 +712,7 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
         f = fetch(pid, t);
         m_accumulate(ml, sRA, sB, J1P, J2P, acc0, acc1, acc2, acc3);
         __syncthreads();  // sRA, sB consumed
+    }
     }
 }
 
@@ -1418,7 +1653,10 @@ cudaError_t launch_wave_end_k(Ctx *c, const DenseArgs &A, RowArgs R, int mode, s
 template <int CJ1, int CJ2, int CJ3>
 size_t sweep_smem(const Ctx *c) {
     const int J1P = even_up(c->d.J1), J2P = even_up(c->d.J2);
-    const size_t sweep = (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) + (size_t)kFastThreads * (J1P + J2P + 4);
+    const size_t sweep = runs_path<CJ1, CJ2>()
+                             ? (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) +
+                                   (size_t)(kFastThreads / 32) * c->d.J1 * c->d.J2
+                             : (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) + (size_t)kFastThreads * (J1P + J2P + 4);
     return sizeof(float) * std::max<size_t>(sweep, (size_t)dense_pre_floats(c->d));
 }
 
@@ -1462,6 +1700,20 @@ cudaError_t init_sweep_tc(Ctx *c) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return e;
+    // The occupancy query has answered 1 CTA per SM for this kernel where registers and shared
+    // memory admit 4 (the profiler's limits); so the CTAs per SM are also counted from the
+    // kernel's own registers and shared memory, and the larger count is taken.
+    cudaFuncAttributes fa;
+    int regs_sm = 0, smem_sm = 0, reserved = 0;
+    e = cudaFuncGetAttributes(&fa, k_fast_sweep_tc<CJ1, CJ2>);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device);
+    if (e != cudaSuccess) return e;
+    const int regs_cta = ((fa.numRegs + 7) & ~7) * 128;
+    const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 1;
+    const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + smem + (size_t)reserved);
+    per_sm = std::max(per_sm, std::min(by_regs, by_smem));
     // TMEM: 512 columns per SM shared by the resident CTAs
     c->fast_grid = std::max(1, std::min(per_sm, 512 / tc_tmem_cols<CJ1, CJ2>())) * sms;
     return cudaSuccess;
