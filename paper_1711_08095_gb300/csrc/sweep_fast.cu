@@ -357,6 +357,9 @@ __device__ __forceinline__ TileFetch fetch_tile(const FastArgs &A, int t) {
 template <int CJ1, int CJ2>
 __host__ __device__ constexpr bool runs_path() { return CJ1 > 0 && CJ2 > 0 && CJ1 <= 16 && CJ2 <= 16; }
 
+// the statically partitioned sweep keeps Gc_k and M_k of every platform in shared memory
+constexpr int kGcAll = 4096;
+
 // sum over the 32 lanes of v[0..16): lane l returns the total of component l >> 1
 __device__ __forceinline__ float reduce_scatter16(const float (&v)[16]) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -514,6 +517,33 @@ __device__ __forceinline__ void runs_merge(float (&mreg)[MRows<CJ1>::n], float *
     }
 }
 
+// a 32-entry unit u of the wave (unit p of tile u / 8): platform (-1: no entry in the unit)
+// and this lane's record; u >= the wave's units gives an empty unit
+__device__ __forceinline__ TileFetch fetch_unit(const FastArgs &A, int64_t u, int lane) {
+    TileFetch f;
+    f.k = -1;
+    f.valid = false;
+    f.e.i = f.e.j = f.e.k = 0;
+    f.e.x = 0.f;
+    const int64_t t = u / (kFastTile / 32);
+    if (t < A.n_tiles) {
+        const int off = (int)(u % (kFastTile / 32)) * 32;
+        const int len = A.tile_len[t];
+        if (off < len) {
+            f.k = A.tile_k[t];
+            f.valid = off + lane < len;
+            if (f.valid) {
+                const int4 v = __ldcs(reinterpret_cast<const int4 *>(A.rec + A.tile_start[t] + off + lane));
+                f.e.i = v.x;
+                f.e.j = v.y;
+                f.e.k = v.z;
+                f.e.x = __int_as_float(v.w);
+            }
+        }
+    }
+    return f;
+}
+
 // CTAs per SM the register budget is cut for (more entries in flight hide the gathers)
 template <int CJ1, int CJ2>
 constexpr int sweep_min_blocks() {
@@ -539,6 +569,62 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
     __shared__ int sTile[2];
     const int tid = threadIdx.x;
     for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
+    if constexpr (runs_path<CJ1, CJ2>()) {
+      if (A.d.I3 * J1 * J2 <= kGcAll) {
+        // Static partition: the wave's tiles are cut into 32-entry units (8 per tile) and each
+        // warp takes a contiguous range of them, so no CTA barrier and no tile claim sit in the
+        // loop.  Gc_k for every platform is formed once per CTA; a warp's M_k shares go to a
+        // per-CTA M (shared atomics) when its platform changes, and that to macc at the end.
+        const int I3 = A.d.I3, Q = J1 * J2;
+        float *sGcAll = sG + align4(PI);       // I3 x J1*J2
+        float *sMacc = sGcAll + I3 * Q;        // I3 x J1*J2
+        __syncthreads();  // sG
+        for (int s = tid; s < I3 * Q; s += kFastThreads) {
+            const int kk = s / Q, pq = s % Q;
+            float g = 0.f;
+            for (int r = 0; r < J3; ++r) g = fmaf(sG[pq * J3 + r], A.U3[(int64_t)kk * J3 + r], g);
+            sGcAll[s] = g;
+            sMacc[s] = 0.f;
+        }
+        __syncthreads();
+        const int lane = tid & 31;
+        const int64_t W = (int64_t)(gridDim.x - 1) * (kFastThreads / 32);
+        const int64_t w = (int64_t)(blockIdx.x - 1) * (kFastThreads / 32) + (tid >> 5);
+        const int64_t U = (int64_t)A.n_tiles * (kFastTile / 32);
+        const int64_t u0 = w * U / W, u1 = (w + 1) * U / W;
+        float mreg[MRows<CJ1>::n];
+#pragma unroll
+        for (int i = 0; i < MRows<CJ1>::n; ++i) mreg[i] = 0.f;
+        int cur_k = -1;
+        auto flush = [&]() {  // this warp's M_k shares into the CTA's M
+            const int q = lane >> 1, par = lane & 1;
+            if (q < J2) {
+#pragma unroll
+                for (int i = 0; i < MRows<CJ1>::n; ++i) {
+                    const int pp = 2 * i + par;
+                    if (pp < J1 && mreg[i] != 0.f) atomicAdd(sMacc + cur_k * Q + pp * J2 + q, mreg[i]);
+                    mreg[i] = 0.f;
+                }
+            }
+        };
+        TileFetch f = fetch_unit(A, u0 < u1 ? u0 : U, lane);
+        for (int64_t u = u0; u < u1; ++u) {
+            const TileFetch cur = f;
+            f = fetch_unit(A, u + 1 < u1 ? u + 1 : U, lane);  // one unit ahead
+            if (cur.k < 0) continue;                          // an empty unit of a short tile
+            if (cur.k != cur_k) {
+                if (cur_k >= 0) flush();
+                cur_k = cur.k;
+            }
+            warp_runs<CJ1, CJ2>(A, cur.e, cur.valid, cur.k, sGcAll + cur.k * Q, mreg);
+        }
+        if (cur_k >= 0) flush();
+        __syncthreads();
+        for (int s = tid; s < I3 * Q; s += kFastThreads)
+            if (sMacc[s] != 0.f) atomicAdd(A.macc + s, sMacc[s]);
+        return;
+      }
+    }
     if constexpr (runs_path<CJ1, CJ2>()) {  // per-patient-run factoring; M_k shares in registers
         float *sMw = sGc + align4(J1 * J2);    // (kFastThreads / 32) x J1*J2: the M_k merge
         float mreg[MRows<CJ1>::n];
@@ -1653,9 +1739,11 @@ cudaError_t launch_wave_end_k(Ctx *c, const DenseArgs &A, RowArgs R, int mode, s
 template <int CJ1, int CJ2, int CJ3>
 size_t sweep_smem(const Ctx *c) {
     const int J1P = even_up(c->d.J1), J2P = even_up(c->d.J2);
+    const size_t Q = (size_t)c->d.J1 * c->d.J2;
     const size_t sweep = runs_path<CJ1, CJ2>()
-                             ? (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) +
-                                   (size_t)(kFastThreads / 32) * c->d.J1 * c->d.J2
+                             ? (size_t)align4(c->PI) +
+                                   std::max(align4((int)Q) + (size_t)(kFastThreads / 32) * Q,
+                                            (size_t)c->d.I3 * Q <= (size_t)kGcAll ? 2 * (size_t)c->d.I3 * Q : 0)
                              : (size_t)align4(c->PI) + align4(c->d.J1 * c->d.J2) + (size_t)kFastThreads * (J1P + J2P + 4);
     return sizeof(float) * std::max<size_t>(sweep, (size_t)dense_pre_floats(c->d));
 }
