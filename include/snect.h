@@ -152,6 +152,14 @@ int snect_serve_stats(snect_server *srv, int64_t *admitted, int64_t *completed, 
 /* Finishes every queued request, stops the scheduler and frees the slots. */
 int snect_serve_stop(snect_server *srv);
 
+/* QR orthogonalisation post-pass (Alg. 1, the step after the sweeps): for each mode n with
+ * J_n <= I_n, U^(n) = Q R (thin QR, R with a positive diagonal), U^(n) <- Q, G <- G x_n R, so
+ * every prediction x~ is unchanged.  Computed as Cholesky-QR applied twice with FP64 Gram
+ * matrices.  A mode with J_n > I_n keeps its factor; its bit (1 << n) is set in
+ * *skipped_modes (may be NULL).  Synchronous.  Errors: SNECT_EINVAL (null context, or a
+ * rank-deficient factor: its Gram matrix is not positive definite), SNECT_ECUDA. */
+int snect_qr_post(snect_ctx *ctx, int32_t *skipped_modes);
+
 /* Batched form: several independent decompositions (e.g. per-cohort sub-tensors, each fitted
  * for several lambda_g) stepped together.  ctxs: n fast-mode FP32 contexts with the same core
  * ranks and the same number of waves (a batch does not own them; they must outlive it).  One

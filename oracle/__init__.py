@@ -214,10 +214,11 @@ def topk(U1, u, k):
 
 
 def qr_post(I, params: Params):
-    """Alg. 1 line 15 in place: U_n <- Q_n, G <- G x_n R_n.  Needs J_n <= I_n."""
+    """Alg. 1's QR post-pass in place: U_n <- Q_n, G <- G x_n R_n for every mode with
+    J_n <= I_n; a mode with J_n > I_n keeps its factor (reading R12).  Returns the bit mask
+    of the modes kept."""
     lib = _load()
     I, Ip = _i32(I)
     J, Jp = _i32(params.J)
-    rc = lib.oracle_qr_post(Ip, Jp, params.G.ctypes.data_as(_f64p), *(u.ctypes.data_as(_f64p) for u in params.U))
-    if rc != 0:
-        raise ValueError("QR post-pass needs J_n <= I_n in every mode")
+    return int(lib.oracle_qr_post(Ip, Jp, params.G.ctypes.data_as(_f64p),
+                                  *(u.ctypes.data_as(_f64p) for u in params.U)))

@@ -403,16 +403,20 @@ void oracle_topk(const double *U1, int64_t I1, int32_t J1, const double *u, int3
     free(score);
 }
 
-/* QR post-pass (Alg. 1 line 15): for each mode, U = Q R (thin, Householder), U <- Q,
- * G <- G x_n R.  Applies only when J_n <= I_n for every mode; returns -1 otherwise. */
+/* QR post-pass (Alg. 1, the step after the sweeps): for each mode, U = Q R (thin,
+ * Householder), U <- Q, G <- G x_n R.  A mode with J_n > I_n has no J_n orthonormal columns
+ * and keeps its factor (reading R12); returns the bit mask of the modes kept. */
 int oracle_qr_post(const int32_t *I, const int32_t *J, double *G, double *U1, double *U2,
                    double *U3) {
     double *U[3] = {U1, U2, U3};
-    for (int md = 0; md < 3; ++md)
-        if (J[md] > I[md]) return -1;
+    int skipped = 0;
     int64_t PI = (int64_t)J[0] * J[1] * J[2];
     double *Gn = (double *)malloc(sizeof(double) * PI);
     for (int md = 0; md < 3; ++md) {
+        if (J[md] > I[md]) {
+            skipped |= 1 << md;
+            continue;
+        }
         int64_t m = I[md];
         int nc = J[md];
         double *A = U[md];
@@ -472,5 +476,5 @@ int oracle_qr_post(const int32_t *I, const int32_t *J, double *G, double *U1, do
         free(R);
     }
     free(Gn);
-    return 0;
+    return skipped;
 }

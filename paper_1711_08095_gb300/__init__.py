@@ -36,6 +36,7 @@ EXPORTS = (
     "snect_foldin",
     "snect_topk",
     "snect_foldin_static",
+    "snect_qr_post",
     "snect_batch_create",
     "snect_batch_epoch",
     "snect_batch_launch_count",
@@ -124,6 +125,7 @@ def load(build_if_missing: bool = False):
         "snect_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64)]),
         "snect_serve_stop": (ctypes.c_int, [P]),
+        "snect_qr_post": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "snect_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(P), i32, P]),
         "snect_batch_epoch": (ctypes.c_int, [P, i32]),
         "snect_batch_launch_count": (ctypes.c_int64, [P]),
@@ -276,6 +278,13 @@ class Snect:
     def serve(self, n_slots: int = 8, mem_budget_bytes: int = 1 << 30, max_cells: int = 75_000):
         """Starts a continuous-batching fold-in + top-k server on this context's factors."""
         return Server(self, n_slots, mem_budget_bytes, max_cells)
+
+    def qr_post(self):
+        """QR orthogonalisation post-pass in place; returns the bit mask of modes left as they
+        were (J_n > I_n)."""
+        sk = ctypes.c_int32(0)
+        self._check(self._lib.snect_qr_post(self._h, ctypes.byref(sk)))
+        return int(sk.value)
 
     @property
     def launches(self) -> int:

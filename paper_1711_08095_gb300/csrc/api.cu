@@ -410,6 +410,15 @@ int snect_get_factors(snect_ctx *h, float *G, float *U1, float *U2, float *U3) {
     return SNECT_OK;
 }
 
+int snect_qr_post(snect_ctx *h, int32_t *skipped_modes) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    int skipped = 0;
+    const int rc = qr_post(c, &skipped);
+    if (skipped_modes) *skipped_modes = skipped;
+    return rc;
+}
+
 int snect_set_factors(snect_ctx *h, const float *G, const float *U1, const float *U2, const float *U3) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c) return SNECT_EINVAL;

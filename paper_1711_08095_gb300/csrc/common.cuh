@@ -121,6 +121,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 cudaError_t launch_det_grad(Ctx *c, int64_t first, int64_t len);
 cudaError_t launch_det_apply(Ctx *c, int64_t first, int64_t len);
 cudaError_t launch_edge_pass(Ctx *c);
+int qr_post(Ctx *c, int *skipped);
 
 // one problem's network pass, for the batched pass (all problems of a batch in three
 // launches: snapshot, light rows, hub rows; blockIdx.y = problem)

@@ -306,6 +306,34 @@ def test_qr_post_pass_keeps_predictions_and_orthonormalises():
         assert np.allclose(np.abs(Qn.T @ P.U[n]), np.eye(p.J[n]), atol=1e-10)
 
 
+def test_qr_post_pass_keeps_a_mode_wider_than_tall():
+    # config 1's shape: J3 = 5 platforms' worth of columns but only 4 platform rows; that mode
+    # has no 5 orthonormal columns and keeps its factor, the others are orthonormalised
+    p = S.tiny_problem(seed=3, I=(8, 9, 4), J=(3, 2, 5))
+    P = oracle.Params(p.G0, p.U0)
+    before = oracle.predict(P, p.idx)
+    skipped = oracle.qr_post(p.I, P)
+    assert skipped == 1 << 2
+    assert np.array_equal(P.U[2], np.asarray(p.U0[2], np.float64))
+    for n in range(2):
+        assert np.allclose(P.U[n].T @ P.U[n], np.eye(p.J[n]), atol=1e-12)
+    assert rel_err(oracle.predict(P, p.idx), before) < 1e-12
+
+
+def test_qr_post_pass_r_is_the_cholesky_factor_up_to_signs():
+    # U = Q R with Q orthonormal means U^T U = R^T R: the oracle's R (recovered as Q^T U)
+    # is the Cholesky factor of the Gram matrix up to the signs of its rows
+    p = S.tiny_problem(seed=5, I=(12, 10, 6), J=(4, 3, 2))
+    P = oracle.Params(p.G0, p.U0)
+    oracle.qr_post(p.I, P)
+    for n in range(3):
+        U0 = np.asarray(p.U0[n], np.float64)
+        R = P.U[n].T @ U0
+        assert np.allclose(np.tril(R, -1), 0.0, atol=1e-12)
+        L = np.linalg.cholesky(U0.T @ U0)
+        assert np.allclose(np.abs(R), np.abs(L.T), atol=1e-10)
+
+
 # ---------------------------------------------------------------------------------------
 # fold-in (Eq. 9) and top-k (Sec. 3.2.1)
 def _fold_problem(seed, n, noise, J=(4, 3, 2), I2=30, I3=3):
