@@ -44,6 +44,11 @@ WORKLOAD = dict(
     I=[4500, 15000, 5], J=[10, 10, 5], nnz_train=27_000_000, edges=300_000, lam=0.01, lam_g=0.1, lr=0.01,
 )
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per training entry of k_fast_sweep, FP32 core 10x10x5, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry case of the same
+# structure (bench.py --small), scaled to a launch by its entries.  To be re-measured, or set to
+# None, whenever the sweep kernel changes.
+SWEEP_DRAM_BYTES_PER_ENTRY = 13.024e6 / 675_000
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
@@ -186,10 +191,20 @@ def cpu_baseline(p, budget_s=15.0):
     t0 = time.perf_counter()
     oracle.sgd_epoch(p.I, P, p.lam, p.lam_g, p.lr, p.idx[:n2], p.val[:n2], p.edges[:0], p.w[:0])
     dt = time.perf_counter() - t0
-    return {"value": n2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, sequential per-entry epoch over the first %d training entries of the "
-                      "workload (%.1f s on one host core; the network pass excluded)" % (n2, dt),
-            "host_cores": os.cpu_count()}
+    out = {"value": n2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "FP64 oracle, sequential per-entry epoch over the first %d training entries of the "
+                     "workload (%.1f s on one host core; the network pass excluded)" % (n2, dt),
+           "host_cores": os.cpu_count()}
+    # the parity workload's mini-batch epochs (the deterministic mode's reference), for context
+    import snect_synth as S
+
+    q = S.config1()
+    P = oracle.Params(q.G0, q.U0)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        oracle.epoch(q.I, P, q.lam, q.lam_g, q.lr, 1024, q.idx, q.val, q.edges, q.w)
+    out["parity_workload_nnz_updates_per_s"] = q.nnz * 3 / (time.perf_counter() - t0)
+    return out
 
 
 def serving(args, snect):
@@ -279,6 +294,57 @@ def precision_form(p, snect, epochs=10):
     out["bf16_rmse_relative_to_fp32"] = out["bf16"][key] / out["fp32"][key] - 1.0
     out["workload"] = ("paper-scale tensor (27M train entries) refit at core 16x16x5, same start for both; "
                        "%d epochs" % epochs)
+    return out
+
+
+def precision_config1(snect):
+    """The precision form's own workload: the parity tensor (200 x 300 x 4) refit at core
+    16x16x5 and 32x32x5, FP32 and BF16 fast mode from the same start for 20 epochs; the
+    objective and test RMSE of each, beside the FP64 oracle's sequential run where it stays
+    finite (at these over-parameterised ranks it can leave the finite range at lr 0.01)."""
+    import snect_synth as S
+
+    out = {}
+    for J in ((16, 16, 5), (32, 32, 5)):
+        p = S.config1(J_fit=J)
+        row = {}
+        for name, prec in (("fp32", snect.FP32), ("bf16", snect.BF16)):
+            c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                            batch=0, precision=prec)
+            c.epoch(p.epochs)
+            l = c.loss(p.test_idx, p.test_val)
+            c.close()
+            row[name] = {"rmse_test": l["rmse_test"], "objective": l["total"]}
+        row["bf16_rmse_relative_to_fp32"] = row["bf16"]["rmse_test"] / row["fp32"]["rmse_test"] - 1.0
+        out["%dx%dx%d" % J] = row
+    return out
+
+
+def parity_config(snect):
+    """The tiny parity workload (200 x 300 x 4, 18,000 training cells, core 5x5x2, 20 epochs in
+    fixed-order mini-batches of 1,024: the deterministic mode the parity tests hold to the
+    oracle): GPU nnz-updates/s over its 20 epochs (one CUDA graph per epoch, launch-bound at
+    this size).  The oracle's time for the same epochs is in cpu_baseline."""
+    import snect_synth as S
+    import torch
+
+    p = S.config1()
+    c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                    batch=1024)
+    st = torch.cuda.current_stream()
+    c.epoch(1)  # graph capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    c.epoch(p.epochs)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / p.epochs
+    rmse = c.loss(p.test_idx, p.test_val)["rmse_test"]
+    c.close()
+    out = {"gpu_nnz_updates_per_s": p.nnz / (ms / 1e3), "gpu_ms_per_epoch": ms,
+           "rmse_test_after_21_epochs": rmse,
+           "workload": "200x300x4, 18,000 train cells, core 5x5x2, deterministic mini-batches of 1,024"}
     return out
 
 
@@ -480,7 +546,10 @@ def main():
                         "factors read back (median of %d jobs, %.1f ms)" % (job_epochs, len(e2e_times), e2e_s * 1e3)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-                     "frac": (achieved / pk) if achieved else None, "traffic": None,
+                     "frac": (achieved / pk) if achieved else None,
+                     "traffic": (SWEEP_DRAM_BYTES_PER_ENTRY * p.nnz / max(sweep_n, 1)
+                                 if (SWEEP_DRAM_BYTES_PER_ENTRY and not bf16 and tuple(p.J) == (10, 10, 5)) else None),
+                     "traffic_unit": "bytes per launch (ncu DRAM read + write, 12M-entry case scaled by entries)",
                      "kernel": "%s (one launch per wave)" % ("k_fast_sweep_tc" if bf16 else "k_fast_sweep"),
                      "bytes_per_unit": bytes_per_nnz, "units_per_launch": p.nnz / max(sweep_n, 1),
                      "peak_kind": pk_kind,
@@ -493,6 +562,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0 and not args.no_precision:
         line["precision_form"] = precision_form(p, snect)
+        line["precision_form"]["config1_refit"] = precision_config1(snect)
+    if rank == 0 and world == 1:
+        line["parity_config"] = parity_config(snect)
     if rank == 0 and args.batched_scale > 0:
         line["batched_form"] = batched_form(args, snect)
     if rank == 0 and args.serve_queries > 0:

@@ -738,15 +738,28 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
             }
             pu = lo;
         }
+        // the problem of a unit, advancing from `from` (units of a warp are visited in order)
+        auto problem_of = [&](int64_t u, int from) {
+            while (from < P - 1 && u >= (int64_t)(kFastTile / 32) * toff[from + 1]) ++from;
+            return from;
+        };
+        pu = problem_of(u0, pu);
+        // records fetched one unit ahead
+        TileFetch fn = fetch_unit(probs[pu], u0 < u1 ? u0 - (int64_t)(kFastTile / 32) * toff[pu] : (int64_t)1 << 40,
+                                  lane);
         for (int64_t u = u0; u < u1; ++u) {
-            while (pu < P - 1 && u >= (int64_t)(kFastTile / 32) * toff[pu + 1]) ++pu;
-            if (pu != pid) {
+            const TileFetch f = fn;
+            const int pthis = pu;
+            if (u + 1 < u1) {
+                pu = problem_of(u + 1, pu);
+                fn = fetch_unit(probs[pu], u + 1 - (int64_t)(kFastTile / 32) * toff[pu], lane);
+            }
+            if (pthis != pid) {
                 if (k_cur >= 0) flush();
-                pid = pu;
+                pid = pthis;
                 k_cur = -1;
             }
             const FastArgs &A = probs[pid];
-            const TileFetch f = fetch_unit(A, u - (int64_t)(kFastTile / 32) * toff[pid], lane);
             if (f.k < 0) continue;
             if (f.k != k_cur) {
                 if (k_cur >= 0) flush();
