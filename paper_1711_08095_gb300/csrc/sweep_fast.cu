@@ -701,82 +701,6 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>())
         dense_pre(probs[blockIdx.x].pre, sm);
         return;
     }
-    if constexpr (runs_path<CJ1, CJ2>()) {
-        // Static partition over the 32-entry units of all problems (problem p owns units
-        // [8 toff[p], 8 toff[p + 1])); each warp takes a contiguous range.  A warp forms Gc_k of
-        // its current problem and platform in its own shared-memory slot, and adds its M_k
-        // shares to that problem's macc when the problem or the platform changes.
-        constexpr int Q = CJ1 * CJ2;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        float *sGcw = sm + warp * Q;
-        const int64_t W = (int64_t)(gridDim.x - P) * (kFastThreads / 32);
-        const int64_t w = (int64_t)(blockIdx.x - P) * (kFastThreads / 32) + warp;
-        const int64_t U = (int64_t)(kFastTile / 32) * toff[P];
-        const int64_t u0 = w * U / W, u1 = (w + 1) * U / W;
-        float mreg[MRows<CJ1>::n];
-#pragma unroll
-        for (int i = 0; i < MRows<CJ1>::n; ++i) mreg[i] = 0.f;
-        int pid = -1, k_cur = -1;
-        auto flush = [&]() {
-            const int q = lane >> 1, par = lane & 1;
-            float *macc = probs[pid].macc + (int64_t)k_cur * Q;
-            if (q < J2) {
-#pragma unroll
-                for (int i = 0; i < MRows<CJ1>::n; ++i) {
-                    const int pp = 2 * i + par;
-                    if (pp < J1 && mreg[i] != 0.f) atomicAdd(macc + pp * J2 + q, mreg[i]);
-                    mreg[i] = 0.f;
-                }
-            }
-        };
-        int pu = 0;  // the problem of unit u (nondecreasing along the warp's range)
-        {
-            int lo = 0, hi = P - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((int64_t)(kFastTile / 32) * toff[mid] <= u0) lo = mid; else hi = mid - 1;
-            }
-            pu = lo;
-        }
-        // the problem of a unit, advancing from `from` (units of a warp are visited in order)
-        auto problem_of = [&](int64_t u, int from) {
-            while (from < P - 1 && u >= (int64_t)(kFastTile / 32) * toff[from + 1]) ++from;
-            return from;
-        };
-        pu = problem_of(u0, pu);
-        // records fetched one unit ahead
-        TileFetch fn = fetch_unit(probs[pu], u0 < u1 ? u0 - (int64_t)(kFastTile / 32) * toff[pu] : (int64_t)1 << 40,
-                                  lane);
-        for (int64_t u = u0; u < u1; ++u) {
-            const TileFetch f = fn;
-            const int pthis = pu;
-            if (u + 1 < u1) {
-                pu = problem_of(u + 1, pu);
-                fn = fetch_unit(probs[pu], u + 1 - (int64_t)(kFastTile / 32) * toff[pu], lane);
-            }
-            if (pthis != pid) {
-                if (k_cur >= 0) flush();
-                pid = pthis;
-                k_cur = -1;
-            }
-            const FastArgs &A = probs[pid];
-            if (f.k < 0) continue;
-            if (f.k != k_cur) {
-                if (k_cur >= 0) flush();
-                __syncwarp();
-                for (int s = lane; s < Q; s += 32) {
-                    float g = 0.f;
-                    for (int r = 0; r < J3; ++r) g = fmaf(A.G[s * J3 + r], A.U3[(int64_t)f.k * J3 + r], g);
-                    sGcw[s] = g;
-                }
-                __syncwarp();
-                k_cur = f.k;
-            }
-            warp_runs<CJ1, CJ2>(A, f.e, f.valid, f.k, sGcw, mreg);
-        }
-        if (k_cur >= 0) flush();
-        return;
-    }
     float *sG = sm;                            // PI
     float *sGc = sG + align4(PI);              // J1*J2 (G x3 c_k)
     float *sRA = sGc + align4(J1 * J2);        // kFastThreads * J1P : r a  (8-byte aligned rows)
