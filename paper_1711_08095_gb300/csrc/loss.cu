@@ -109,8 +109,61 @@ __global__ void __launch_bounds__(256)
 
 int loss_grid(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(ceil_div(n, 256), 1), 4096); }
 
+// The same squared residuals through Gc_k = G x3 c_k of every platform, formed once per CTA in
+// shared memory (when I3 J1 J2 floats fit): x~ = a^T Gc_k b, J1 J2 products per entry instead
+// of the full contraction.  A grid-stride loop amortises the set-up over many entries.
+constexpr int kLossGcMax = 12288;  // floats of Gc in shared memory (48 KB)
+
+template <int CJ1, int CJ2>
+__global__ void __launch_bounds__(256)
+    k_loss_entries_gc(const Rec *__restrict__ rec, int64_t n, Dims d, const float *__restrict__ Gg,
+                      const float *__restrict__ U1, const float *__restrict__ U2,
+                      const float *__restrict__ U3, double *acc) {
+    constexpr int J1 = CJ1, J2 = CJ2, Q = CJ1 * CJ2;
+    const int J3 = d.J3, I3 = d.I3;
+    extern __shared__ float sGc[];  // I3 x J1 x J2
+    __shared__ double red[8];
+    for (int s = threadIdx.x; s < I3 * Q; s += blockDim.x) {
+        const int k = s / Q, pq = s % Q;
+        float g = 0.f;
+        for (int r = 0; r < J3; ++r) g = fmaf(Gg[pq * J3 + r], U3[(int64_t)k * J3 + r], g);
+        sGc[s] = g;
+    }
+    __syncthreads();
+    double local = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const Rec r = rec[e];
+        float b[J2];
+#pragma unroll
+        for (int q = 0; q < J2; ++q) b[q] = __ldg(U2 + (int64_t)r.j * J2 + q);
+        const float *gc = sGc + r.k * Q;
+        float xt = 0.f;
+#pragma unroll
+        for (int p = 0; p < J1; ++p) {
+            float vp = 0.f;
+#pragma unroll
+            for (int q = 0; q < J2; ++q) vp = fmaf(gc[p * J2 + q], b[q], vp);
+            xt = fmaf(__ldg(U1 + (int64_t)r.i * J1 + p), vp, xt);
+        }
+        const double res = (double)r.x - (double)xt;
+        local += res * res;
+    }
+    const double s = block_sum(local, red);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_loss(Ctx *c, const Rec *recs, int64_t n, int which) {
+    if constexpr (CJ1 > 0 && CJ2 > 0) {
+        const int64_t gcf = (int64_t)c->d.I3 * CJ1 * CJ2;
+        if (gcf <= kLossGcMax) {
+            const int grid = (int)std::min<int64_t>(ceil_div(n, 256), 8 * 152);
+            k_loss_entries_gc<CJ1, CJ2><<<grid, 256, sizeof(float) * gcf, c->stream>>>(
+                recs, n, c->d, c->G, c->U[0], c->U[1], c->U[2], c->lacc + which);
+            c->launches++;
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = sizeof(float) * c->PI;
     k_loss_entries<CJ1, CJ2, CJ3><<<ceil_div(n, 256), 256, smem, c->stream>>>(
         recs, n, c->d, c->G, c->U[0], c->U[1], c->U[2], c->lacc + which);

@@ -62,6 +62,33 @@ __global__ void k_counts(const Rec *__restrict__ rec, int64_t n, int32_t I3, int
             if (h3[t]) atomicAdd(c3 + t, h3[t]);
 }
 
+// the same counts with every mode's histogram in shared memory (when I1 + I2 + I3 bins fit):
+// a grid-stride loop counts many entries per CTA with shared atomics, then each nonzero bin
+// goes to global memory once per CTA
+constexpr int kCountBins = 24576;  // ints of shared memory (96 KB)
+
+__global__ void __launch_bounds__(1024) k_counts_smem(const Rec *__restrict__ rec, int64_t n, int32_t I1, int32_t I2,
+                                                      int32_t I3, int32_t *c1, int32_t *c2, int32_t *c3) {
+    extern __shared__ int32_t hs[];  // I1 | I2 | I3
+    const int nb = I1 + I2 + I3;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) hs[t] = 0;
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const Rec r = rec[e];
+        atomicAdd(hs + r.i, 1);
+        atomicAdd(hs + I1 + r.j, 1);
+        atomicAdd(hs + I1 + I2 + r.k, 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const int v = hs[t];
+        if (v == 0) continue;
+        if (t < I1) atomicAdd(c1 + t, v);
+        else if (t < I1 + I2) atomicAdd(c2 + (t - I1), v);
+        else atomicAdd(c3 + (t - I1 - I2), v);
+    }
+}
+
 // key = (batch << 32) | row of the given mode; value = entry position
 __global__ void k_group_keys(const Rec *__restrict__ rec, int64_t n, int32_t batch, int mode,
                              uint64_t *keys, int32_t *vals) {
@@ -236,8 +263,19 @@ int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val) {
         SNECT_CUDA(c, cudaMemsetAsync(c->cnt[md], 0, sizeof(int32_t) * In, c->stream));
     }
     if (c->nnz) {
-        k_counts<<<ceil_div(c->nnz, 1024), 1024, 0, c->stream>>>(c->rec, c->nnz, c->d.I3, c->cnt[0], c->cnt[1],
-                                                                 c->cnt[2]);
+        const int64_t bins = (int64_t)c->d.I1 + c->d.I2 + c->d.I3;
+        if (bins <= kCountBins) {
+            const size_t smem = sizeof(int32_t) * (size_t)bins;
+            SNECT_CUDA(c, cudaFuncSetAttribute(k_counts_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int sms = 0;
+            SNECT_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+            const int grid = (int)std::min<int64_t>(ceil_div(c->nnz, 1024), 2 * (int64_t)sms);
+            k_counts_smem<<<grid, 1024, smem, c->stream>>>(c->rec, c->nnz, c->d.I1, c->d.I2, c->d.I3, c->cnt[0],
+                                                           c->cnt[1], c->cnt[2]);
+        } else {
+            k_counts<<<ceil_div(c->nnz, 1024), 1024, 0, c->stream>>>(c->rec, c->nnz, c->d.I3, c->cnt[0], c->cnt[1],
+                                                                     c->cnt[2]);
+        }
         c->launches++;
         SNECT_CUDA(c, cudaGetLastError());
     }

@@ -23,7 +23,8 @@
 // Inside a wave the entries are grouped by platform, so within a tile c_k is fixed and the
 // contraction uses Gc = G x3 c_k (J1 x J2):
 //   v  = Gc b,  w2 = Gc^T a,  x~ = a . v,  r = x~ - x
-//   g(u^(1)_i) += r v + lambda/|Omega^{1,i}| a,   g(u^(2)_j) += r w2 + lambda/|Omega^{2,j}| b
+//   g(u^(1)_i) += r v,   g(u^(2)_j) += r w2   (the data term; a row's L2 term, the same for
+//   each of its n entries in the wave, is added once at the wave end as n lambda/|Omega| u)
 // and both dense gradients come from one J1 x J2 matrix per platform,
 //   M_k = sum_{entries of platform k} r a b^T:
 //   dG_pqr = sum_k M_k[p,q] c_k[r] + n lambda/|Omega| g_pqr
@@ -216,17 +217,17 @@ __device__ __forceinline__ void tile_entries(const FastArgs &A, const Rec &e, bo
 #pragma unroll
         for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
         const float r = xt - e.x;
-        const float la = A.lam / (float)__ldg(A.cnt1 + e.i), lb = A.lam / (float)__ldg(A.cnt2 + e.j);
-        // row accumulators: [gradient (J, padded to 4), entries per platform (I3, padded)]
+        // row accumulators: [data-term gradient (J, padded to 4), entries per platform (I3,
+        // padded)]; the L2 term n lambda/|Omega| u of a row is added by the wave end
         float gvb[RB];
 #pragma unroll
         for (int p = 0; p < J1; ++p) {
-            gva[p] = fmaf(r, v[p], la * a[p]);
+            gva[p] = r * v[p];
             ra[p] = r * a[p];
         }
 #pragma unroll
         for (int q = 0; q < J2; ++q) {
-            gvb[q] = fmaf(r, w2[q], lb * b[q]);
+            gvb[q] = r * w2[q];
             bb[q] = b[q];
         }
 #pragma unroll
@@ -346,10 +347,11 @@ __device__ __forceinline__ TileFetch fetch_tile(const FastArgs &A, int t) {
 // by patient, so a warp's 32 entries fall into a few runs of one patient i each (a_i fixed).
 // For a run the contraction factors through a_i:
 //   w2 = Gc^T a_i (once per run),  x~_e = a_i^T Gc b_e = w2 . b_e,  r_e = x~_e - x_e
-//   gene rows:    g(b_e) += r_e w2 + lambda/|Omega^{2,j}| b_e          (per entry)
+//   gene rows:    g(b_e) += r_e w2                                    (per entry)
 //   s = sum_e r_e b_e                                                  (run sum)
-//   patient row:  g(a_i) += Gc s + n_run lambda/|Omega^{1,i}| a_i       (= sum_e r_e Gc b_e + ...)
+//   patient row:  g(a_i) += Gc s                                      (= sum_e r_e Gc b_e)
 //   M_k += a_i s^T                                                     (= sum_e r_e a_i b_e^T)
+// (the rows' L2 terms are added at the wave end)
 // so the per-entry work is O(J2) and the J1 x J2 products are paid once per run.  Vectors of
 // the run are spread over the warp (lane l holds component l / 2) by recursive-halving
 // reductions.
@@ -452,10 +454,9 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
 #pragma unroll
             for (int qq = 0; qq < J2; ++qq) xt = fmaf(w2[qq], b[qq], xt);
             r = xt - x;
-            const float lb = A.lam / (float)__ldg(A.cnt2 + ej);
             float gvb[JB];
 #pragma unroll
-            for (int qq = 0; qq < JB; ++qq) gvb[qq] = qq < J2 ? fmaf(r, w2[qq], lb * b[qq]) : 0.f;
+            for (int qq = 0; qq < JB; ++qq) gvb[qq] = qq < J2 ? r * w2[qq] : 0.f;
             float *gb = A.gB + (int64_t)ej * A.rs2;
 #pragma unroll
             for (int t4 = 0; t4 < JB / 4; ++t4)
@@ -476,19 +477,15 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
                 mreg[t] = fmaf(ap, s_q, mreg[t]);
             }
         }
-        // patient gradient Gc s + n_run la a: (Gc s)[p] = sum_q Gc[p][q] s[q], summed over the
+        // patient gradient Gc s: (Gc s)[p] = sum_q Gc[p][q] s[q], summed over the
         // even lanes (one per component q)
         float tv[16];
 #pragma unroll
         for (int p = 0; p < 16; ++p) tv[p] = (p < J1 && q < J2 && !par) ? sGc[p * J2 + (q < J2 ? q : 0)] * s_q : 0.f;
         const float gcs = reduce_scatter16(tv);  // lane l: (Gc s)[l / 2]
         if (!par && q < J1) {
-            float aq = 0.f;
-#pragma unroll
-            for (int p = 0; p < J1; ++p) aq = p == q ? a[p] : aq;
-            const float la = A.lam / (float)__ldg(A.cnt1 + ih);
             float *ga = A.gA + (int64_t)ih * A.rs1;
-            atomicAdd(ga + q, fmaf((float)__popc(run) * la, aq, gcs));
+            atomicAdd(ga + q, gcs);
             if (lane == 0) atomicAdd(ga + JA + k, (float)__popc(run));
         }
     }
@@ -1007,15 +1004,14 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
 #pragma unroll
                 for (int p = 0; p < J1; ++p) xt = fmaf(a[p], v[p], xt);
                 r = xt - x;
-                const float la = A.lam / (float)__ldg(A.cnt1 + ei), lb = A.lam / (float)__ldg(A.cnt2 + ej);
                 float *gb = A.gB + (int64_t)ej * A.rs2;
 #pragma unroll
-                for (int p = 0; p < J1; ++p) gva[p] = fmaf(r, v[p], la * a[p]);
+                for (int p = 0; p < J1; ++p) gva[p] = r * v[p];
 #pragma unroll
                 for (int q = 0; q < JB; q += 4) {
                     float g4[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) g4[u] = (q + u < J2) ? fmaf(r, w2[q + u], lb * b[q + u]) : 0.f;
+                    for (int u = 0; u < 4; ++u) g4[u] = (q + u < J2) ? r * w2[q + u] : 0.f;
                     atomicAdd(reinterpret_cast<float4 *>(gb + q), make_float4(g4[0], g4[1], g4[2], g4[3]));
                 }
                 atomicAdd(gb + JB + k, 1.f);
@@ -1140,7 +1136,9 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
                 __syncwarp();
             }
             // L y = g, then L^T x = y; lane l holds component l, columns broadcast by shuffles
-            float gl = lane < J ? acc[lane] : 0.f;
+            // the data term summed by the sweep, plus the wave's L2 term n lambda/|Omega| u
+            const float nreg = n * lam / (float)max(cnt[row], 1);
+            float gl = lane < J ? fmaf(nreg, su[lane], acc[lane]) : 0.f;
             for (int i = 0; i < J; ++i) {
                 const float xi = __shfl_sync(0xffffffffu, gl, i) / sH[i * kTileStride + i];
                 if (lane == i) gl = xi;
@@ -1206,7 +1204,8 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
             for (int k = 0; k < I3; ++k) n += acc[JP + k];
             if (n > 0.f) {
                 float L[NL];
-                const float diag = kBlocks * n * lam / (float)max(cnt[row], 1) + inv_lr;
+                const float nreg = n * lam / (float)max(cnt[row], 1);  // the wave's L2 weight
+                const float diag = kBlocks * nreg + inv_lr;
 #pragma unroll
                 for (int p = 0, t = 0; p < J; ++p)
 #pragma unroll
@@ -1241,7 +1240,8 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
                 float y[J];
 #pragma unroll
                 for (int i = 0; i < J; ++i) {
-                    float x = acc[i];
+                    // the data term summed by the sweep, plus the wave's L2 term n lambda/|Omega| u
+                    float x = fmaf(nreg, u[i], acc[i]);
 #pragma unroll
                     for (int k = 0; k < i; ++k) x -= L[i * (i + 1) / 2 + k] * y[k];
                     y[i] = x / L[i * (i + 1) / 2 + i];
