@@ -82,7 +82,10 @@ typedef struct {
  *   G0, U1, U2, U3  any, initial core and factors (layouts above)
  *   stream  a cudaStream_t, or NULL for the default stream
  * Validates ranges (indices, sizes, finite values, self loops); computes the counts
- * |Omega^{n,i}| and the per-batch row grouping on the GPU.  On failure *out is NULL. */
+ * |Omega^{n,i}| and the per-batch row grouping on the GPU.  On failure *out is NULL.
+ * Temporary set-up memory (staging, sort buffers) comes from a memory pool the library owns
+ * on each device; memory freed back to that pool stays reserved (its high-water mark, about
+ * 40 bytes per training entry) until the process exits, so later set-ups reuse it. */
 int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, const float *val,
                int64_t nnz, const int32_t *edges, const float *w, int64_t m, const float *G0,
                const float *U1, const float *U2, const float *U3, void *stream);

@@ -1,4 +1,5 @@
 // C ABI entry points (include/snect.h): argument checks, device buffers, the epoch graph.
+#include <mutex>
 #include <math.h>
 
 #include <algorithm>
@@ -38,7 +39,7 @@ int stage(Ctx *c, T **dst, const T *src, int64_t count) {
     *dst = nullptr;
     if (count <= 0) return SNECT_OK;
     if (!src) return fail(c, SNECT_EINVAL, "null input pointer");
-    SNECT_CUDA(c, cudaMallocAsync((void **)dst, sizeof(T) * (size_t)count, c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, (void **)dst, sizeof(T) * (size_t)count));
     SNECT_CUDA(c, cudaMemcpyAsync(*dst, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, c->stream));
     return SNECT_OK;
 }
@@ -208,6 +209,34 @@ int fail(Ctx *c, int code, const std::string &msg) {
     return code;
 }
 
+cudaMemPool_t scratch_pool(int device) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) {
+        cudaMemPool_t def = nullptr;
+        cudaDeviceGetDefaultMemPool(&def, device);
+        return def;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {  // the device's default pool
+            cudaGetLastError();
+            cudaDeviceGetDefaultMemPool(&pool, device);
+        }
+        pools[device] = pool;
+    }
+    return pools[device];
+}
+
 }  // namespace snect
 
 using namespace snect;
@@ -358,7 +387,7 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     if (n_test > 0) {
         if ((rc = stage(c, &d_idx, test_idx, n_test * 3)) || (rc = stage(c, &d_val, test_val, n_test)))
             return rc;
-        SNECT_CUDA(c, cudaMallocAsync((void **)&trec, sizeof(Rec) * n_test, c->stream));
+        SNECT_CUDA(c, scratch_alloc(c, (void **)&trec, sizeof(Rec) * n_test));
         rc = pack_records(c, d_idx, d_val, n_test, trec, true, 3);
         if (rc == SNECT_OK) {
             cudaError_t e = launch_loss(c, trec, n_test, 1);

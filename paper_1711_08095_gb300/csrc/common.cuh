@@ -12,6 +12,7 @@
 
 namespace snect {
 
+constexpr int kMaxDevices = 64;  // devices with a library scratch pool
 constexpr int kMaxRank = 32;      // largest J_n
 constexpr int kMaxCore = 5120;    // largest J1*J2*J3
 constexpr int kMaxBatch = 4096;   // largest deterministic mini-batch
@@ -107,6 +108,16 @@ struct Ctx {
 
 // error helpers ---------------------------------------------------------------------------
 int fail(Ctx *c, int code, const std::string &msg);
+
+// Stream-ordered scratch for set-up and queries comes from a memory pool the library owns on
+// each device, which keeps the memory it has handed out mapped after it is freed (its
+// high-water mark stays reserved until the process exits), so repeated set-ups do not pay
+// to map and unmap hundreds of megabytes.
+cudaMemPool_t scratch_pool(int device);
+template <typename T>
+cudaError_t scratch_alloc(Ctx *c, T **p, size_t bytes) {
+    return cudaMallocFromPoolAsync((void **)p, bytes, scratch_pool(c->device), c->stream);
+}
 #define SNECT_CUDA(c, call)                                                                  \
     do {                                                                                     \
         cudaError_t e__ = (call);                                                            \

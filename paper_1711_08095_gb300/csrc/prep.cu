@@ -155,6 +155,16 @@ __global__ void k_max_degree(const int32_t *__restrict__ ptr, int32_t I2, int32_
 }
 
 // key = (wave << 32) | platform; value = entry position (fast mode grouping)
+// the same key in 32 bits, when it fits
+__global__ void k_wave_keys32(const Rec *__restrict__ rec, int64_t n, int64_t wave, int bi, int bk,
+                              uint32_t *keys, int32_t *vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const Rec r = rec[e];
+    keys[e] = ((uint32_t)(e / wave) << (bi + bk)) | ((uint32_t)r.k << bi) | (bi ? (uint32_t)r.i : 0u);
+    vals[e] = (int32_t)e;
+}
+
 // key (wave, platform, patient): bits [0, bi) patient (0 when bi = 0), [bi, bi + bk) platform,
 // above that the wave
 __global__ void k_wave_keys(const Rec *__restrict__ rec, int64_t n, int64_t wave, int bi, int bk,
@@ -214,13 +224,13 @@ int read_flag(Ctx *c, int32_t *out) {
 }
 
 // stable radix sort of (key, value) pairs; temporary buffers allocated here
-int sort_pairs(Ctx *c, uint64_t *keys, int32_t *vals, uint64_t *keys_out, int32_t *vals_out,
-               int64_t n, int end_bit) {
+template <typename K>
+int sort_pairs(Ctx *c, K *keys, int32_t *vals, K *keys_out, int32_t *vals_out, int64_t n, int end_bit) {
     size_t tmp_bytes = 0;
     SNECT_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys_out, vals, vals_out,
                                                    n, 0, end_bit, c->stream));
     void *tmp = nullptr;
-    SNECT_CUDA(c, cudaMallocAsync(&tmp, tmp_bytes, c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, &tmp, tmp_bytes));
     cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys_out, vals, vals_out, n,
                                                     0, end_bit, c->stream);
     c->launches += 4;  // radix passes (an estimate; set-up only)
@@ -287,9 +297,9 @@ int prep_det_groups(Ctx *c) {
     if (n == 0) return SNECT_OK;
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int32_t *vals = nullptr;
-    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * n, c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, &keys, sizeof(uint64_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &keys2, sizeof(uint64_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &vals, sizeof(int32_t) * n));
     int rc = SNECT_OK;
     int end_bit = 32 + bits_for((uint64_t)c->n_batches);
     for (int md = 0; md < 3 && rc == SNECT_OK; ++md) {
@@ -319,10 +329,10 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     }
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int32_t *vals = nullptr, *vals2 = nullptr;
-    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * 2 * m, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * 2 * m, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * 2 * m, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&vals2, sizeof(int32_t) * 2 * m, c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, &keys, sizeof(uint64_t) * 2 * m));
+    SNECT_CUDA(c, scratch_alloc(c, &keys2, sizeof(uint64_t) * 2 * m));
+    SNECT_CUDA(c, scratch_alloc(c, &vals, sizeof(int32_t) * 2 * m));
+    SNECT_CUDA(c, scratch_alloc(c, &vals2, sizeof(int32_t) * 2 * m));
     k_half_edges<<<ceil_div(m, 256), 256, 0, c->stream>>>(d_edges, d_w, m, I2, keys, vals, c->edges,
                                                           c->ew, c->flag);
     c->launches++;
@@ -387,12 +397,12 @@ int prep_fast_tiles(Ctx *c) {
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int32_t *vals = nullptr, *vals2 = nullptr, *hist = nullptr;
     Rec *tmp = nullptr;
-    SNECT_CUDA(c, cudaMallocAsync(&keys, sizeof(uint64_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&keys2, sizeof(uint64_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&vals, sizeof(int32_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&vals2, sizeof(int32_t) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&tmp, sizeof(Rec) * n, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync(&hist, sizeof(int32_t) * c->n_waves * I3, c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, &keys, sizeof(uint64_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &keys2, sizeof(uint64_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &vals, sizeof(int32_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &vals2, sizeof(int32_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &tmp, sizeof(Rec) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &hist, sizeof(int32_t) * c->n_waves * I3));
     // inside a wave and platform the entries are put in patient order (the sweep sums a
     // patient's neighbouring entries before adding them to its row; gradients inside a wave
     // all use the wave-start values, so the order inside a wave is free); the stable sort
@@ -400,9 +410,17 @@ int prep_fast_tiles(Ctx *c) {
     const int bw = bits_for((uint64_t)(c->n_waves - 1)), bk = bits_for((uint64_t)(I3 - 1));
     int bi = bits_for((uint64_t)(c->d.I1 - 1));
     if (bw + bk + bi > 64) bi = 0;
-    k_wave_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, bi, bk, keys, vals);
-    c->launches++;
-    int rc = sort_pairs(c, keys, vals, keys2, vals2, n, bw + bk + bi);
+    int rc;
+    if (bw + bk + bi <= 32) {  // 32-bit keys: half the key traffic of the radix passes
+        uint32_t *k32 = reinterpret_cast<uint32_t *>(keys), *k32b = reinterpret_cast<uint32_t *>(keys2);
+        k_wave_keys32<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, bi, bk, k32, vals);
+        c->launches++;
+        rc = sort_pairs(c, k32, vals, k32b, vals2, n, bw + bk + bi);
+    } else {
+        k_wave_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, bi, bk, keys, vals);
+        c->launches++;
+        rc = sort_pairs(c, keys, vals, keys2, vals2, n, bw + bk + bi);
+    }
     if (rc == SNECT_OK) {
         k_permute<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, vals2, n, tmp);
         cudaMemcpyAsync(c->rec, tmp, sizeof(Rec) * n, cudaMemcpyDeviceToDevice, c->stream);
@@ -425,6 +443,10 @@ int prep_fast_tiles(Ctx *c) {
     cudaFreeAsync(hist, c->stream);
     if (rc) return rc;
     std::vector<int32_t> ts, tl, tk;
+    const size_t tiles_max = (size_t)(n / kFastTile) + (size_t)c->n_waves * I3 + 1;
+    ts.reserve(tiles_max);
+    tl.reserve(tiles_max);
+    tk.reserve(tiles_max);
     std::vector<float> nk((size_t)c->n_waves * I3);
     for (int64_t w = 0; w < c->n_waves; ++w) {
         int64_t pos = std::min<int64_t>(w * W, n);

@@ -119,8 +119,8 @@ int qr_post(Ctx *c, int *skipped) {
     double *buf = nullptr;
     int *status = nullptr;
     // gram, R, Rinv, Rtot (J x J each, J <= 32)
-    SNECT_CUDA(c, cudaMallocAsync((void **)&buf, sizeof(double) * 4 * kMaxRank * kMaxRank, c->stream));
-    SNECT_CUDA(c, cudaMallocAsync((void **)&status, sizeof(int), c->stream));
+    SNECT_CUDA(c, scratch_alloc(c, (void **)&buf, sizeof(double) * 4 * kMaxRank * kMaxRank));
+    SNECT_CUDA(c, scratch_alloc(c, (void **)&status, sizeof(int)));
     SNECT_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int), c->stream));
     double *gram = buf, *R = buf + kMaxRank * kMaxRank, *Rinv = R + kMaxRank * kMaxRank, *Rtot = Rinv + kMaxRank * kMaxRank;
     cudaError_t e = cudaSuccess;
