@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry case of the same
 # structure (bench.py --small), scaled to a launch by its entries.  To be re-measured, or set to
 # None, whenever the sweep kernel changes.
-SWEEP_DRAM_BYTES_PER_ENTRY = 13.024e6 / 675_000
+SWEEP_DRAM_BYTES_PER_ENTRY = 12.955e6 / 675_000
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
@@ -563,7 +563,7 @@ def main():
     if rank == 0 and not args.no_precision:
         line["precision_form"] = precision_form(p, snect)
         line["precision_form"]["config1_refit"] = precision_config1(snect)
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.small:
         line["parity_config"] = parity_config(snect)
     if rank == 0 and args.batched_scale > 0:
         line["batched_form"] = batched_form(args, snect)
