@@ -79,6 +79,9 @@ struct Ctx {
     int64_t gram_stride = 0;
     int32_t fast_grid = 0;          // persistent CTAs of the wave kernel (occupancy)
     float *gacc[2] = {};            // per patient / gene row: gradient sums + entries per platform
+    // entries per (wave, row, platform), fixed at set-up: n_waves x (I1 + I2) x I3, patients
+    // before genes in each wave (null: the sweep counts with atomics instead)
+    float *wcnt = nullptr;
     float *curv = nullptr;          // platform curvatures of the row steps (two buffers)
     // fold-in / top-k
     float *wtable = nullptr;        // I2*I3*J1: w_jk = G x2 u2_j x3 u3_k

@@ -155,6 +155,27 @@ __global__ void k_max_degree(const int32_t *__restrict__ ptr, int32_t I2, int32_
 }
 
 // key = (wave << 32) | platform; value = entry position (fast mode grouping)
+// entries per (wave, row, platform) of the two row modes, from the wave-grouped order (wave w
+// holds positions [w W, (w + 1) W)).  A patient's entries inside a wave and platform sit next
+// to each other, so each run in a warp adds its length once; gene rows add one per entry.
+__global__ void k_wave_row_counts(const Rec *__restrict__ rec, int64_t n, int64_t W, int32_t I1, int32_t I2,
+                                  int32_t I3, float *tab) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = e < n;
+    Rec r;
+    r.i = r.j = r.k = 0;
+    r.x = 0.f;
+    if (ok) r = rec[e];
+    const int64_t w = ok ? e / W : 0;
+    float *t = tab + w * ((int64_t)I1 + I2) * I3;
+    const unsigned long long key =
+        ok ? (((unsigned long long)w << 40) | ((unsigned long long)r.k << 32) | (unsigned)r.i) : ~0ull;
+    const unsigned run = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    if (ok && __ffs(run) - 1 == lane) atomicAdd(t + (int64_t)r.i * I3 + r.k, (float)__popc(run));
+    if (ok) atomicAdd(t + ((int64_t)I1 + r.j) * I3 + r.k, 1.f);
+}
+
 // the same key in 32 bits, when it fits
 __global__ void k_wave_keys32(const Rec *__restrict__ rec, int64_t n, int64_t wave, int bi, int bk,
                               uint32_t *keys, int32_t *vals) {
@@ -427,6 +448,20 @@ int prep_fast_tiles(Ctx *c) {
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * c->n_waves * I3, c->stream);
         k_wave_hist<<<ceil_div(n, 1024), 1024, 0, c->stream>>>(c->rec, n, W, I3, hist);
         c->launches += 2;
+        // the row steps' per-platform entry counts, fixed for every wave, when the table is no
+        // larger than the entries themselves (else the sweep counts them with atomics)
+        const int64_t cells = c->n_waves * ((int64_t)c->d.I1 + c->d.I2) * I3;
+        if ((size_t)cells * sizeof(float) <= std::max<size_t>((size_t)64 << 20, sizeof(Rec) * (size_t)n)) {
+            if (cudaMalloc((void **)&c->wcnt, sizeof(float) * cells) == cudaSuccess) {
+                cudaMemsetAsync(c->wcnt, 0, sizeof(float) * cells, c->stream);
+                k_wave_row_counts<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, c->d.I1, c->d.I2, I3,
+                                                                           c->wcnt);
+                c->launches++;
+            } else {
+                cudaGetLastError();
+                c->wcnt = nullptr;
+            }
+        }
     }
     std::vector<int32_t> h((size_t)c->n_waves * I3);
     if (rc == SNECT_OK) {

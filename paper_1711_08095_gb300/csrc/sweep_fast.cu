@@ -97,6 +97,7 @@ struct FastArgs {
     int32_t rs1, rs2;  // row strides of gA, gB
     int32_t *err;      // set when a tensor-core wait gives up
     DenseArgs pre;     // the wave's dense pre-work (one extra CTA of the launch)
+    int32_t count_atomics;  // 1: count each row's entries per platform with atomics (no table)
 };
 
 __device__ void dense_pre(const DenseArgs &A, float *sm);
@@ -108,7 +109,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm);
 // marks a lane without an entry.  Every lane of the warp calls this.
 template <int RA>
 __device__ __forceinline__ void add_patient_runs(float (&g)[RA], int J, int iv, float *__restrict__ gA, int32_t rs,
-                                                 int k) {
+                                                 int k, bool count) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int inext = __shfl_down_sync(FULL, iv, 1);
@@ -135,7 +136,7 @@ __device__ __forceinline__ void add_patient_runs(float (&g)[RA], int J, int iv, 
         for (int t = 0; t < RA / 4; ++t)
             if (4 * t < JA)
                 atomicAdd(reinterpret_cast<float4 *>(ga) + t, make_float4(g[4 * t], g[4 * t + 1], g[4 * t + 2], g[4 * t + 3]));
-        atomicAdd(ga + JA + k, (float)__popc(run));
+        if (count) atomicAdd(ga + JA + k, (float)__popc(run));
     }
 }
 
@@ -238,14 +239,14 @@ __device__ __forceinline__ void tile_entries(const FastArgs &A, const Rec &e, bo
             if (4 * t4 < JB)
                 atomicAdd(reinterpret_cast<float4 *>(gb) + t4,
                           make_float4(gvb[4 * t4], gvb[4 * t4 + 1], gvb[4 * t4 + 2], gvb[4 * t4 + 3]));
-        atomicAdd(gb + JB + k, 1.f);
+        if (A.count_atomics) atomicAdd(gb + JB + k, 1.f);
         if (J1P != J1) ra[J1] = 0.f;
         if (J2P != J2) bb[J2] = 0.f;
     } else {
         for (int p = 0; p < J1P; ++p) ra[p] = 0.f;
         for (int q = 0; q < J2P; ++q) bb[q] = 0.f;
     }
-    add_patient_runs<RA>(gva, J1, iv, A.gA, A.rs1, k);
+    add_patient_runs<RA>(gva, J1, iv, A.gA, A.rs1, k, A.count_atomics);
 }
 
 // M_k accumulation layout: 2 x 2 blocks of (p, q) and slices of the tile's entries.
@@ -462,7 +463,7 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
             for (int t4 = 0; t4 < JB / 4; ++t4)
                 atomicAdd(reinterpret_cast<float4 *>(gb) + t4,
                           make_float4(gvb[4 * t4], gvb[4 * t4 + 1], gvb[4 * t4 + 2], gvb[4 * t4 + 3]));
-            atomicAdd(gb + JB + k, 1.f);
+            if (A.count_atomics) atomicAdd(gb + JB + k, 1.f);
         }
         // s = sum over the run of r_e b_e (lanes outside the run give 0): lane l gets s[l / 2]
         float u[16];
@@ -486,7 +487,7 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
         if (!par && q < J1) {
             float *ga = A.gA + (int64_t)ih * A.rs1;
             atomicAdd(ga + q, gcs);
-            if (lane == 0) atomicAdd(ga + JA + k, (float)__popc(run));
+            if (lane == 0 && A.count_atomics) atomicAdd(ga + JA + k, (float)__popc(run));
         }
     }
 }
@@ -1014,9 +1015,9 @@ __global__ void __launch_bounds__(128) k_fast_sweep_tc(FastArgs A) {
                     for (int u = 0; u < 4; ++u) g4[u] = (q + u < J2) ? r * w2[q + u] : 0.f;
                     atomicAdd(reinterpret_cast<float4 *>(gb + q), make_float4(g4[0], g4[1], g4[2], g4[3]));
                 }
-                atomicAdd(gb + JB + k, 1.f);
+                if (A.count_atomics) atomicAdd(gb + JB + k, 1.f);
             }
-            add_patient_runs<JA>(gva, J1, valid ? ei : -1, A.gA, A.rs1, k);
+            add_patient_runs<JA>(gva, J1, valid ? ei : -1, A.gA, A.rs1, k, A.count_atomics);
 #pragma unroll
             for (int p = 0; p < J1; ++p)
                 *reinterpret_cast<__nv_bfloat16 *>(prt + tc::kmajor_off(p, tid, M)) = __float2bfloat16(r * a[p]);
@@ -1066,6 +1067,7 @@ constexpr int kCkStage = 8192;     // platform curvatures staged in shared memor
 constexpr int kJacobiSweeps = 2;
 constexpr int kEigEvery = 4;
 constexpr int kRowsPerThreadCta = 256;  // rows per CTA of the thread-per-row step
+__host__ __device__ constexpr int pow2_floor(int x) { return x >= 2 ? 2 * pow2_floor(x / 2) : 1; }
 
 // Patient / gene rows: u <- u - (H + (n lambda/|Omega^{n,i}| + 1/lr) I)^{-1} g with
 // H = sum_k n_ik C_k (C_k = the platform curvature of this mode), accumulators cleared; then
@@ -1075,7 +1077,8 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
                           float *__restrict__ gA, float *__restrict__ gB, int32_t rs1, int32_t rs2,
                           const int32_t *__restrict__ cnt1, const int32_t *__restrict__ cnt2,
                           const Dims &d, float lam, float inv_lr, float inv_n,
-                          const float *__restrict__ curv_in, float *__restrict__ gram_out, float *sm) {
+                          const float *__restrict__ curv_in, float *__restrict__ gram_out,
+                          const float *__restrict__ wc1, const float *__restrict__ wc2, float *sm) {
     const int J = first ? d.J1 : d.J2;
     const int JP = (J + 3) & ~3;
     const int RS = first ? rs1 : rs2;
@@ -1084,6 +1087,7 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
     float *U = first ? U1 : U2;
     float *g = first ? gA : gB;
     const int32_t *cnt = first ? cnt1 : cnt2;
+    const float *wc = first ? wc1 : wc2;
     const float *Ckg = curv_in + (first ? 0 : (int64_t)I3 * d.J1 * d.J1);  // I3 blocks of J x J
     const int64_t r0 = (int64_t)blk * kRowsPerCta;
     const int64_t left = (int64_t)I - r0;
@@ -1106,8 +1110,10 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
     for (int ri = warp; ri < nr; ri += kRowWarps) {
         const int64_t row = r0 + ri;
         float *acc = g + row * RS;
+        // the row's entries per platform in this wave: the set-up table, or the sweep's counts
+        const float *wn = wc ? wc + row * I3 : acc + JP;
         float n = 0.f;
-        for (int k = 0; k < I3; ++k) n += acc[JP + k];
+        for (int k = 0; k < I3; ++k) n += wn[k];
         if (lane < J) su[lane] = U[row * J + lane];
         __syncwarp();
         if (do_step && n > 0.f) {
@@ -1116,7 +1122,7 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
                 const int p = e / J, q = e % J;
                 float h = p == q ? diag : 0.f;
                 for (int k = 0; k < I3; ++k) {
-                    const float nk = acc[JP + k];
+                    const float nk = wn[k];
                     if (nk > 0.f) h = fmaf(kBlocks * nk, Ck[(int64_t)k * J * J + e], h);
                 }
                 sH[p * kTileStride + q] = h;
@@ -1180,7 +1186,7 @@ template <int CJ>
 __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, float *__restrict__ g, int32_t RS,
                                  const int32_t *__restrict__ cnt, int32_t I, int32_t I3, float lam,
                                  float inv_lr, float inv_n, const float *__restrict__ Ckg,
-                                 float *__restrict__ gram_out, float *sm) {
+                                 float *__restrict__ gram_out, const float *__restrict__ wc, float *sm) {
     constexpr int J = CJ, JP = (J + 3) & ~3, NL = J * (J + 1) / 2;
     const int64_t r0 = (int64_t)blk * kRowsPerThreadCta;
     if (r0 >= I) return;
@@ -1199,9 +1205,11 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
     for (int p = 0; p < J; ++p) u[p] = valid ? U[row * J + p] : 0.f;
     if (valid) {
         float *acc = g + row * RS;
+        // the row's entries per platform in this wave: the set-up table, or the sweep's counts
+        const float *wn = wc ? wc + row * I3 : acc + JP;
         if (do_step) {
             float n = 0.f;
-            for (int k = 0; k < I3; ++k) n += acc[JP + k];
+            for (int k = 0; k < I3; ++k) n += wn[k];
             if (n > 0.f) {
                 float L[NL];
                 const float nreg = n * lam / (float)max(cnt[row], 1);  // the wave's L2 weight
@@ -1211,7 +1219,7 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
 #pragma unroll
                     for (int q = 0; q <= p; ++q, ++t) L[t] = p == q ? diag : 0.f;
                 for (int k = 0; k < I3; ++k) {
-                    const float nk = kBlocks * acc[JP + k];
+                    const float nk = kBlocks * wn[k];
                     if (nk > 0.f) {
                         const float *C = Ck + (int64_t)k * J * J;
 #pragma unroll
@@ -1266,11 +1274,24 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
     for (int p = 0; p < J; ++p) rows[threadIdx.x * J + p] = u[p];
     wts[threadIdx.x] = valid ? (float)cnt[row] * inv_n : 0.f;
     __syncthreads();
-    for (int s = threadIdx.x; s < J * J; s += blockDim.x) {
-        const int p = s / J, q = s % J;
-        float a = 0.f;
-        for (int i = 0; i < kRowsPerThreadCta; ++i) a = fmaf(wts[i] * rows[i * J + p], rows[i * J + q], a);
-        atomicAdd(gram_out + s, a);
+    // moments: each of the J*J outputs is split over R threads (a slice of the rows each),
+    // with four independent partial sums per thread
+    constexpr int R = pow2_floor((J * J >= kRowsPerThreadCta) ? 1 : kRowsPerThreadCta / (J * J));
+    constexpr int SL = kRowsPerThreadCta / R;  // a multiple of 4 (R <= 64)
+    static_assert(SL * R == kRowsPerThreadCta && SL % 4 == 0, "row slices");
+    for (int s = threadIdx.x; s < J * J * R; s += blockDim.x) {
+        const int e = s % (J * J), h = s / (J * J);
+        const int p = e / J, q = e % J;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int i0 = h * SL;
+#pragma unroll 2
+        for (int i = i0; i < i0 + SL; i += 4) {
+            a0 = fmaf(wts[i] * rows[i * J + p], rows[i * J + q], a0);
+            a1 = fmaf(wts[i + 1] * rows[(i + 1) * J + p], rows[(i + 1) * J + q], a1);
+            a2 = fmaf(wts[i + 2] * rows[(i + 2) * J + p], rows[(i + 2) * J + q], a2);
+            a3 = fmaf(wts[i + 3] * rows[(i + 3) * J + p], rows[(i + 3) * J + q], a3);
+        }
+        atomicAdd(gram_out + e, (a0 + a1) + (a2 + a3));
     }
 }
 
@@ -1554,15 +1575,47 @@ __device__ void dense_post(const DenseArgs &A, float *sm) {
     float *sMacc = la + J1 + J2 + J3;  // the wave's M_k, if they fit
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool stage_m = I3 * Q <= kMaccStage;
-    if (stage_m)
-        for (int s = tid; s < I3 * Q; s += nt) sMacc[s] = A.macc[s];
     const float *Mk = stage_m ? sMacc : A.macc;
-    for (int s = tid; s < PI; s += nt) sG[s] = A.G[s];
-    for (int s = tid; s < I3 * J3; s += nt) sC[s] = A.U3[s];
-    for (int s = tid; s < J1 * J1; s += nt) Va[(s / J1) * ld + s % J1] = A.eigv[s];
-    for (int s = tid; s < J2 * J2; s += nt) Vb[(s / J2) * ld + s % J2] = A.eigv[J1 * J1 + s];
-    for (int s = tid; s < J3 * J3; s += nt) Vc[(s / J3) * ld + s % J3] = A.eigv[J1 * J1 + J2 * J2 + s];
-    for (int s = tid; s < J1 + J2 + J3; s += nt) la[s] = fmaxf(A.eigval[s], 0.f);
+    {  // the step's inputs, four loads per thread in flight at a time
+        const int o1 = stage_m ? I3 * Q : 0, o2 = o1 + PI, o3 = o2 + I3 * J3, o4 = o3 + J1 * J1,
+                  o5 = o4 + J2 * J2, o6 = o5 + J3 * J3, N = o6 + J1 + J2 + J3;
+        for (int base = tid; base < N; base += 4 * nt) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = base + u * nt;
+                v[u] = t >= N ? 0.f
+                       : t < o1 ? A.macc[t]
+                       : t < o2 ? A.G[t - o1]
+                       : t < o3 ? A.U3[t - o2]
+                       : t < o6 ? A.eigv[t - o3]  // Ma, Mb, Cn eigenvectors, contiguous
+                                : A.eigval[t - o6];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = base + u * nt;
+                if (t >= N) continue;
+                if (t < o1) {
+                    sMacc[t] = v[u];
+                } else if (t < o2) {
+                    sG[t - o1] = v[u];
+                } else if (t < o3) {
+                    sC[t - o2] = v[u];
+                } else if (t < o4) {
+                    const int e = t - o3;
+                    Va[(e / J1) * ld + e % J1] = v[u];
+                } else if (t < o5) {
+                    const int e = t - o4;
+                    Vb[(e / J2) * ld + e % J2] = v[u];
+                } else if (t < o6) {
+                    const int e = t - o5;
+                    Vc[(e / J3) * ld + e % J3] = v[u];
+                } else {
+                    la[t - o6] = fmaxf(v[u], 0.f);
+                }
+            }
+        }
+    }
     __syncthreads();
     const float *lb = la + J1, *lc = la + J1 + J2;
     for (int s = tid; s < I3 * J3; s += nt) {  // platform gradients
@@ -1645,6 +1698,7 @@ struct RowArgs {
     int32_t nb1;
     const float *curv_in;
     float *gram_out;
+    const float *wc1, *wc2;  // this wave's entries per (row, platform) of each mode, or null
 };
 
 // End of a wave.  mode 0: CTA 0 = the rest of the core and platform-row step (dense_post),
@@ -1662,13 +1716,13 @@ __device__ void wave_end_rows(const DenseArgs &A, const RowArgs &R, int blk, int
         float *gout = R.gram_out + (first ? 0 : d.J1 * d.J1);
         if (first)
             wave_rows_thread<CJ1>(mb, mode == 0, R.U1, R.gA, R.rs1, R.cnt1, d.I1, d.I3, A.lam, 1.f / A.lr,
-                                  R.inv_n, Ckg, gout, smw);
+                                  R.inv_n, Ckg, gout, R.wc1, smw);
         else
             wave_rows_thread<CJ2>(mb, mode == 0, R.U2, R.gB, R.rs2, R.cnt2, d.I2, d.I3, A.lam, 1.f / A.lr,
-                                  R.inv_n, Ckg, gout, smw);
+                                  R.inv_n, Ckg, gout, R.wc2, smw);
     } else {
         wave_rows(first, mb, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, d, A.lam,
-                  1.f / A.lr, R.inv_n, R.curv_in, R.gram_out, smw);
+                  1.f / A.lr, R.inv_n, R.curv_in, R.gram_out, R.wc1, R.wc2, smw);
     }
 }
 
@@ -1844,6 +1898,7 @@ FastArgs make_fast_args(Ctx *c, int64_t w) {
     A.rs1 = row_stride(c->d.J1, c->d.I3);
     A.rs2 = row_stride(c->d.J2, c->d.I3);
     A.err = c->flag + 3;
+    A.count_atomics = c->wcnt ? 0 : 1;
     RowArgs unused;
     make_wave_args(c, w, (int)(w & 1), 0, &A.pre, &unused);
     return A;
@@ -1906,6 +1961,11 @@ void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowA
     R.nb1 = 0;  // set by the launcher for its row step
     R.curv_in = c->curv;
     R.gram_out = c->gram + (size_t)parity * c->gram_stride;
+    R.wc1 = R.wc2 = nullptr;
+    if (c->wcnt && w >= 0) {
+        R.wc1 = c->wcnt + (size_t)w * ((size_t)d.I1 + d.I2) * d.I3;
+        R.wc2 = R.wc1 + (size_t)d.I1 * d.I3;
+    }
     (void)mode;
 }
 
@@ -1981,6 +2041,7 @@ void free_fast(Ctx *c) {
     f(c->curv);
     f(c->gacc[0]);
     f(c->gacc[1]);
+    f(c->wcnt);
 }
 
 }  // namespace snect
