@@ -387,7 +387,7 @@ struct MRows {
 
 // This warp's entries of a tile of platform k (e, valid: the lane's entry), run by run.  Every
 // lane of the warp calls this.  mreg: the lane's share of the CTA's M_k.
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, bool CNT = true>
 __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool valid, int k,
                                           const float *__restrict__ sGc, float (&mreg)[MRows<CJ1>::n]) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -463,7 +463,7 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
             for (int t4 = 0; t4 < JB / 4; ++t4)
                 atomicAdd(reinterpret_cast<float4 *>(gb) + t4,
                           make_float4(gvb[4 * t4], gvb[4 * t4 + 1], gvb[4 * t4 + 2], gvb[4 * t4 + 3]));
-            if (A.count_atomics) atomicAdd(gb + JB + k, 1.f);
+            if (CNT && A.count_atomics) atomicAdd(gb + JB + k, 1.f);
         }
         // s = sum over the run of r_e b_e (lanes outside the run give 0): lane l gets s[l / 2]
         float u[16];
@@ -487,7 +487,7 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
         if (!par && q < J1) {
             float *ga = A.gA + (int64_t)ih * A.rs1;
             atomicAdd(ga + q, gcs);
-            if (lane == 0 && A.count_atomics) atomicAdd(ga + JA + k, (float)__popc(run));
+            if (CNT && lane == 0 && A.count_atomics) atomicAdd(ga + JA + k, (float)__popc(run));
         }
     }
 }
@@ -548,7 +548,8 @@ constexpr int sweep_min_blocks() {
     return (CJ1 > 0 && CJ2 > 0 && CJ1 * CJ2 <= 100) ? 4 : (CJ1 == 16 && CJ2 == 16) ? 3 : 1;
 }
 
-template <int CJ1, int CJ2, int CJ3>
+// CNT: the sweep counts each row's entries per platform with atomics (no set-up table)
+template <int CJ1, int CJ2, int CJ3, bool CNT>
 __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_fast_sweep(FastArgs A) {
     const int J1 = CJ1 ? CJ1 : A.d.J1, J2 = CJ2 ? CJ2 : A.d.J2, J3 = CJ3 ? CJ3 : A.d.J3;
     const int J1P = even_up(J1), J2P = even_up(J2);
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
                 if (cur_k >= 0) flush();
                 cur_k = cur.k;
             }
-            warp_runs<CJ1, CJ2>(A, cur.e, cur.valid, cur.k, sGcAll + cur.k * Q, mreg);
+            warp_runs<CJ1, CJ2, CNT>(A, cur.e, cur.valid, cur.k, sGcAll + cur.k * Q, mreg);
         }
         if (cur_k >= 0) flush();
         __syncthreads();
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
                 cur_k = f.k;
                 __syncthreads();
             }
-            warp_runs<CJ1, CJ2>(A, f.e, f.valid, f.k, sGc, mreg);
+            warp_runs<CJ1, CJ2, CNT>(A, f.e, f.valid, f.k, sGc, mreg);
             __syncthreads();  // the next claim is visible; sGc and sMw free for reuse
             t = sTile[par ^ 1];
             par ^= 1;
@@ -1805,14 +1806,15 @@ size_t sweep_smem(const Ctx *c) {
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t init_sweep(Ctx *c) {
     const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(c);
-    cudaError_t e = cudaFuncSetAttribute(k_fast_sweep<CJ1, CJ2, CJ3>,
+    auto kern = c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fast_sweep<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast_sweep<CJ1, CJ2, CJ3>, kFastThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFastThreads, smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return e;
@@ -1912,7 +1914,10 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - 1), nt) + 1;
     c->launches++;
     if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
-    k_fast_sweep<CJ1, CJ2, CJ3><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
+    if (c->wcnt)
+        k_fast_sweep<CJ1, CJ2, CJ3, false><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
+    else
+        k_fast_sweep<CJ1, CJ2, CJ3, true><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
     return cudaGetLastError();
 }
 
