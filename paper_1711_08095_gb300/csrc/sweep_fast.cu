@@ -545,7 +545,7 @@ __device__ __forceinline__ TileFetch fetch_unit(const FastArgs &A, int64_t u, in
 // CTAs per SM the register budget is cut for (more entries in flight hide the gathers)
 template <int CJ1, int CJ2>
 constexpr int sweep_min_blocks() {
-    return (CJ1 > 0 && CJ2 > 0 && CJ1 * CJ2 <= 100) ? 4 : (CJ1 == 16 && CJ2 == 16) ? 3 : 1;
+    return (CJ1 > 0 && CJ2 > 0 && CJ1 * CJ2 <= 100) ? 4 : (CJ1 == 16 && CJ2 == 16) ? 2 : 1;
 }
 
 // CNT: the sweep counts each row's entries per platform with atomics (no set-up table)
