@@ -223,7 +223,8 @@ def serving(args, snect):
     pool = [S.serving_query(m, q=q) for q in range(pool_n)]  # distinct queries, resubmitted in turn
     arrivals = S.poisson_arrivals(args.serve_queries, args.serve_rate)
     srv = ctx.serve(n_slots=16, mem_budget_bytes=512 << 20, max_cells=75_000)
-    for jk, x, _ in pool[:8]:  # warm-up
+    # warm-up: every query of the pool once (every kernel and size path loaded and touched)
+    for jk, x, _ in pool:
         srv.poll(srv.submit(jk, x, 10), 10)
     tickets = [None] * len(arrivals)
     t0 = time.perf_counter()
