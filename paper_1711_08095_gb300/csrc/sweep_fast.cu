@@ -90,10 +90,10 @@ struct FastArgs {
     Dims d;
     const float *G;
     const float *U1, *U2, *U3;
-    const int32_t *cnt1, *cnt2;
-    float lam;
     float *macc;
-    float *gA, *gB;  // per row: gradient sums (J_n, padded to 4) + entries per platform
+    // per row: data-term gradient sums (J_n, padded to 4), then entries per platform (written
+    // only when count_atomics is set)
+    float *gA, *gB;
     int32_t rs1, rs2;  // row strides of gA, gB
     int32_t *err;      // set when a tensor-core wait gives up
     DenseArgs pre;     // the wave's dense pre-work (one extra CTA of the launch)
@@ -1891,9 +1891,6 @@ FastArgs make_fast_args(Ctx *c, int64_t w) {
     A.U1 = c->U[0];
     A.U2 = c->U[1];
     A.U3 = c->U[2];
-    A.cnt1 = c->cnt[0];
-    A.cnt2 = c->cnt[1];
-    A.lam = c->cfg.lambda;
     A.macc = c->macc;
     A.gA = c->gacc[0];
     A.gB = c->gacc[1];
