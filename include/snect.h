@@ -200,11 +200,20 @@ int snect_foldin_static(const float *G, const float *U2, const float *U3, int32_
                         int32_t J1, int32_t J2, int32_t J3, const int32_t *jk, const float *val,
                         int64_t n, float lambda, float *u_out, void *stream);
 
-/* Device time of the entry-sweep kernels of the most recent epoch (fast mode: one launch per
- * wave), measured with CUDA events recorded on the context's stream immediately before and
- * after each launch.  *ms_total = summed milliseconds, *n_launches = launches timed.
- * Deterministic mode reports the gradient kernels of its batches.  Synchronises. */
-int snect_sweep_times(snect_ctx *ctx, double *ms_total, int64_t *n_launches);
+/* Which entry-sweep launches of an epoch carry CUDA timing events (fast mode: one sweep
+ * launch per wave; deterministic mode: the gradient kernel of each batch).  mode 0 (the
+ * default): none; 1: one launch per epoch, the middle one; -1: every launch.  Each timed
+ * launch adds two event nodes to the epoch's CUDA graph, which cost the epoch several
+ * microseconds each, so timing is off unless asked for.  A change takes effect at the next
+ * snect_epoch (the epoch graph is captured again).  Errors: SNECT_EINVAL for another mode. */
+int snect_set_sweep_timing(snect_ctx *ctx, int32_t mode);
+
+/* Device time of the timed entry-sweep launches (snect_set_sweep_timing) of the most recent
+ * epoch, measured with CUDA events recorded on the context's stream immediately before and
+ * after each of them.  *ms_total = summed milliseconds, *n_launches = launches timed,
+ * *n_entries (may be NULL) = training entries those launches processed.  All zero when no
+ * epoch has run with timing on.  Synchronises. */
+int snect_sweep_times(snect_ctx *ctx, double *ms_total, int64_t *n_launches, int64_t *n_entries);
 
 /* Number of kernel launches the context has issued so far (for launch accounting). */
 int64_t snect_launch_count(const snect_ctx *ctx);

@@ -47,6 +47,7 @@ EXPORTS = (
     "snect_serve_poll",
     "snect_serve_stats",
     "snect_serve_stop",
+    "snect_set_sweep_timing",
     "snect_sweep_times",
     "snect_launch_count",
     "snect_last_error",
@@ -132,7 +133,9 @@ def load(build_if_missing: bool = False):
         "snect_batch_last_error": (ctypes.c_char_p, [P]),
         "snect_batch_destroy": (None, [P]),
         "snect_foldin_static": (ctypes.c_int, [P, P, P, i32, i32, i32, i32, i32, P, P, i64, ctypes.c_float, P, P]),
-        "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "snect_set_sweep_timing": (ctypes.c_int, [P, ctypes.c_int32]),
+        "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
         "snect_last_error": (ctypes.c_char_p, [P]),
         "snect_destroy": (None, [P]),
@@ -268,12 +271,17 @@ class Snect:
                                          sc.ctypes.data))
         return idx, sc
 
+    def set_sweep_timing(self, mode: int):
+        """Sweep launches timed per epoch: 0 none (default), 1 the middle one, -1 all."""
+        self._check(self._lib.snect_set_sweep_timing(self._h, int(mode)))
+
     def sweep_times(self):
-        """(summed ms, launches) of the sweep kernels of the most recent epoch."""
+        """(summed ms, launches, entries) of the timed sweep kernels of the most recent epoch."""
         ms = ctypes.c_double()
         n = ctypes.c_int64()
-        self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n)))
-        return ms.value, n.value
+        e = ctypes.c_int64()
+        self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(e)))
+        return ms.value, n.value, e.value
 
     def serve(self, n_slots: int = 8, mem_budget_bytes: int = 1 << 30, max_cells: int = 75_000):
         """Starts a continuous-batching fold-in + top-k server on this context's factors."""

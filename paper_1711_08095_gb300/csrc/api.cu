@@ -114,9 +114,10 @@ int enqueue_det_epoch(Ctx *c) {
     const int64_t B = c->cfg.batch;
     for (int64_t b = 0; b < c->n_batches; ++b) {
         const int64_t first = b * B, len = std::min<int64_t>(B, c->nnz - first);
-        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[b], c->stream, cudaEventRecordExternal));
+        const bool tm = c->time_launch(b, c->n_batches, len);
+        if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[b], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_det_grad(c, first, len));
-        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[b], c->stream, cudaEventRecordExternal));
+        if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[b], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_det_apply(c, first, len));
     }
     return SNECT_OK;
@@ -136,6 +137,8 @@ int build_epoch_graph(Ctx *c) {
     SNECT_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     c->stream = cap;
     const int64_t before = c->launches;
+    c->timed_idx.clear();
+    c->timed_len.clear();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int rc = SNECT_OK;
@@ -501,18 +504,37 @@ int snect_topk(snect_ctx *h, const float *u, int32_t k, int32_t *idx_out, float 
     return SNECT_OK;
 }
 
-int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches) {
+int snect_set_sweep_timing(snect_ctx *h, int32_t mode) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (mode < -1 || mode > 1) return fail(c, SNECT_EINVAL, "sweep timing mode must be -1, 0 or 1");
+    if (mode == c->timed) return SNECT_OK;
+    c->timed = mode;
+    if (c->epoch_exec) {  // the next epoch captures a graph with the new event nodes
+        SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaGraphExecDestroy(c->epoch_exec);
+        c->epoch_exec = nullptr;
+    }
+    c->timed_idx.clear();
+    c->timed_len.clear();
+    return SNECT_OK;
+}
+
+int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches, int64_t *n_entries) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c || !ms_total || !n_launches) return SNECT_EINVAL;
     *ms_total = 0.0;
     *n_launches = 0;
-    if (!c->epoch_exec) return SNECT_OK;  // no epoch has run yet
+    if (n_entries) *n_entries = 0;
+    if (!c->epoch_exec) return SNECT_OK;  // no epoch has run with the current setting
     SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (size_t i = 0; i < c->ev_begin.size(); ++i) {
+    for (size_t t = 0; t < c->timed_idx.size(); ++t) {
+        const int64_t i = c->timed_idx[t];
         float ms = 0.f;
         SNECT_CUDA(c, cudaEventElapsedTime(&ms, c->ev_begin[i], c->ev_end[i]));
         *ms_total += ms;
         ++*n_launches;
+        if (n_entries) *n_entries += c->timed_len[t];
     }
     return SNECT_OK;
 }

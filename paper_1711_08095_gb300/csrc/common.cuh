@@ -103,8 +103,20 @@ struct Ctx {
     // CUDA graph of one epoch
     cudaGraphExec_t epoch_exec = nullptr;
     int64_t epoch_kernels = 0;      // kernels in one replay of the graph
-    // events around the sweep launches of one epoch (recorded inside the epoch graph)
+    // events around the sweep launches of one epoch (recorded inside the epoch graph); each
+    // recorded event is a graph node that costs several microseconds of the epoch, so only
+    // the launches chosen by `timed` carry them (0: none, 1: the middle one, -1: all)
     std::vector<cudaEvent_t> ev_begin, ev_end;
+    int32_t timed = 0;
+    std::vector<int64_t> timed_idx, timed_len;  // event pairs recorded by the epoch graph, entries
+
+    // true if launch i of n_launches carries timing events; records it with its entries
+    bool time_launch(int64_t i, int64_t n_launches, int64_t entries) {
+        if (timed == 0 || (timed == 1 && i != n_launches / 2)) return false;
+        timed_idx.push_back(i);
+        timed_len.push_back(entries);
+        return true;
+    }
     // error word written by kernels (validation)
     int32_t *flag = nullptr;
 };

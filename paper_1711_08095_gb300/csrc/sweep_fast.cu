@@ -79,7 +79,8 @@ __host__ __device__ inline int64_t dense_pre_floats(const Dims &d) {
 __host__ __device__ inline int64_t dense_post_floats(const Dims &d) {
     const int64_t PI = (int64_t)d.J1 * d.J2 * d.J3, Q = (int64_t)d.J1 * d.J2;
     const int64_t stage = (int64_t)d.I3 * Q <= kMaccStage ? (int64_t)d.I3 * Q : 0;
-    return 3 * PI + 3 * (int64_t)d.I3 * d.J3 + (int64_t)(d.J1 + d.J2 + d.J3) * (eig_ld(d) + 1) + stage;
+    return 3 * PI + 3 * (int64_t)d.I3 * d.J3 + (int64_t)(d.J1 + d.J2 + d.J3) * (eig_ld(d) + 1) +
+           (int64_t)d.I3 * d.J3 * d.J3 + 2 * (int64_t)d.I3 + stage;
 }
 
 struct FastArgs {
@@ -1183,116 +1184,183 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
 // The same row step with one thread per row for a compile-time rank J <= 16: H (packed lower
 // triangle), its Cholesky factor and both triangular solves stay in registers, with no
 // synchronisation inside a row.
+// floats of shared memory of the thread-per-row step at rank J
+__host__ __device__ inline int64_t rows_thread_floats(int J) {
+    return (int64_t)kRowsPerThreadCta * ((J + 1) & ~1) + kCkStage;
+}
+
 template <int CJ>
 __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, float *__restrict__ g, int32_t RS,
                                  const int32_t *__restrict__ cnt, int32_t I, int32_t I3, float lam,
                                  float inv_lr, float inv_n, const float *__restrict__ Ckg,
                                  float *__restrict__ gram_out, const float *__restrict__ wc, float *sm) {
-    constexpr int J = CJ, JP = (J + 3) & ~3, NL = J * (J + 1) / 2;
+    constexpr int J = CJ, JP = (J + 3) & ~3, NL = J * (J + 1) / 2, NLP = (NL + 3) & ~3, JE = (J + 1) & ~1;
     const int64_t r0 = (int64_t)blk * kRowsPerThreadCta;
     if (r0 >= I) return;
-    float *rows = sm;                          // kRowsPerThreadCta x J (updated rows)
-    float *wts = rows + kRowsPerThreadCta * J; // kRowsPerThreadCta
-    float *sCk = wts + kRowsPerThreadCta;      // I3 x J x J, if it fits
-    const bool stage = I3 * J * J <= kCkStage;
-    if (stage && do_step)
-        for (int e = threadIdx.x; e < I3 * J * J; e += blockDim.x) sCk[e] = Ckg[e];
-    __syncthreads();
-    const float *Ck = stage ? sCk : Ckg;
+    float *rows = sm;                           // kRowsPerThreadCta x JE: updated rows times sqrt(weight)
+    float *sCk = rows + kRowsPerThreadCta * JE; // I3 packed lower triangles (NLP floats each), if they fit
+    const bool stage = I3 * NLP <= kCkStage;
     const int64_t row = r0 + threadIdx.x;
     const bool valid = row < I;
-    float u[J];
-#pragma unroll
-    for (int p = 0; p < J; ++p) u[p] = valid ? U[row * J + p] : 0.f;
+    // the row's inputs, all loads in flight together
+    float u[J], b[J];
+    int nrow = 0;
+    float n = 0.f;  // the row's entries in this wave
+    float *acc = g + row * RS;
+    // the row's entries per platform in this wave: the set-up table, or the sweep's counts
+    const float *wn = wc ? wc + row * I3 : acc + JP;
     if (valid) {
-        float *acc = g + row * RS;
-        // the row's entries per platform in this wave: the set-up table, or the sweep's counts
-        const float *wn = wc ? wc + row * I3 : acc + JP;
+        nrow = cnt[row];
         if (do_step) {
-            float n = 0.f;
+#pragma unroll 4
             for (int k = 0; k < I3; ++k) n += wn[k];
-            if (n > 0.f) {
-                float L[NL];
-                const float nreg = n * lam / (float)max(cnt[row], 1);  // the wave's L2 weight
-                const float diag = kBlocks * nreg + inv_lr;
+        }
 #pragma unroll
-                for (int p = 0, t = 0; p < J; ++p)
+        for (int p = 0; p < J; ++p) u[p] = U[row * J + p];
 #pragma unroll
-                    for (int q = 0; q <= p; ++q, ++t) L[t] = p == q ? diag : 0.f;
-                for (int k = 0; k < I3; ++k) {
-                    const float nk = kBlocks * wn[k];
-                    if (nk > 0.f) {
-                        const float *C = Ck + (int64_t)k * J * J;
+        for (int p = 0; p < J; p += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(acc + p);
+            b[p] = v.x;
+            if (p + 1 < J) b[p + 1] = v.y;
+            if (p + 2 < J) b[p + 2] = v.z;
+            if (p + 3 < J) b[p + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < J; ++p) u[p] = b[p] = 0.f;
+    }
+    if (stage && do_step)  // lower triangles, row p at p (p + 1) / 2
+        for (int e = threadIdx.x; e < I3 * NLP; e += blockDim.x) {
+            const int k = e / NLP, t = e % NLP;
+            int p = 0;
+            while ((p + 1) * (p + 2) / 2 <= t) ++p;
+            const int q = t - p * (p + 1) / 2;
+            sCk[e] = t < NL ? Ckg[(int64_t)k * J * J + p * J + q] : 0.f;
+        }
+    __syncthreads();
+    if (valid) {
+        if (do_step && n > 0.f) {
+            float L[NL];
+            const float nreg = n * lam / (float)max(nrow, 1);  // the wave's L2 weight
+            const float diag = kBlocks * nreg + inv_lr;
+#pragma unroll
+            for (int p = 0, t = 0; p < J; ++p)
+#pragma unroll
+                for (int q = 0; q <= p; ++q, ++t) L[t] = p == q ? diag : 0.f;
+            for (int k = 0; k < I3; ++k) {
+                const float nk = kBlocks * wn[k];
+                if (nk > 0.f) {
+                    if (stage) {
+                        const float4 *C4 = reinterpret_cast<const float4 *>(sCk + k * NLP);
+#pragma unroll
+                        for (int t = 0; t < NLP; t += 4) {
+                            const float4 c4 = C4[t / 4];
+                            L[t] = fmaf(nk, c4.x, L[t]);
+                            if (t + 1 < NL) L[t + 1] = fmaf(nk, c4.y, L[t + 1]);
+                            if (t + 2 < NL) L[t + 2] = fmaf(nk, c4.z, L[t + 2]);
+                            if (t + 3 < NL) L[t + 3] = fmaf(nk, c4.w, L[t + 3]);
+                        }
+                    } else {
+                        const float *C = Ckg + (int64_t)k * J * J;
 #pragma unroll
                         for (int p = 0, t = 0; p < J; ++p)
 #pragma unroll
                             for (int q = 0; q <= p; ++q, ++t) L[t] = fmaf(nk, C[p * J + q], L[t]);
                     }
                 }
-                // Cholesky (packed lower triangle, row p starts at p (p + 1) / 2)
+            }
+            // Cholesky (packed lower triangle, row p starts at p (p + 1) / 2); the inverse
+            // diagonal is kept, so the solves below multiply instead of dividing
+            float dinv[J];
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    float dd = L[j * (j + 1) / 2 + j];
+            for (int j = 0; j < J; ++j) {
+                float dd = L[j * (j + 1) / 2 + j];
 #pragma unroll
-                    for (int k = 0; k < j; ++k) dd -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
-                    dd = sqrtf(fmaxf(dd, 1e-20f));
-                    L[j * (j + 1) / 2 + j] = dd;
-                    const float inv = 1.f / dd;
+                for (int k = 0; k < j; ++k) dd -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+                const float inv = rsqrtf(fmaxf(dd, 1e-20f));
+                dinv[j] = inv;
 #pragma unroll
-                    for (int i = j + 1; i < J; ++i) {
-                        float x = L[i * (i + 1) / 2 + j];
+                for (int i = j + 1; i < J; ++i) {
+                    float x = L[i * (i + 1) / 2 + j];
 #pragma unroll
-                        for (int k = 0; k < j; ++k) x -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
-                        L[i * (i + 1) / 2 + j] = x * inv;
-                    }
+                    for (int k = 0; k < j; ++k) x -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+                    L[i * (i + 1) / 2 + j] = x * inv;
                 }
-                float y[J];
+            }
+            float y[J];
 #pragma unroll
-                for (int i = 0; i < J; ++i) {
-                    // the data term summed by the sweep, plus the wave's L2 term n lambda/|Omega| u
-                    float x = fmaf(nreg, u[i], acc[i]);
+            for (int i = 0; i < J; ++i) {
+                // the data term summed by the sweep, plus the wave's L2 term n lambda/|Omega| u
+                float x = fmaf(nreg, u[i], b[i]);
 #pragma unroll
-                    for (int k = 0; k < i; ++k) x -= L[i * (i + 1) / 2 + k] * y[k];
-                    y[i] = x / L[i * (i + 1) / 2 + i];
-                }
+                for (int k = 0; k < i; ++k) x -= L[i * (i + 1) / 2 + k] * y[k];
+                y[i] = x * dinv[i];
+            }
 #pragma unroll
-                for (int i = J - 1; i >= 0; --i) {
-                    float x = y[i];
+            for (int i = J - 1; i >= 0; --i) {
+                float x = y[i];
 #pragma unroll
-                    for (int k = i + 1; k < J; ++k) x -= L[k * (k + 1) / 2 + i] * y[k];
-                    y[i] = x / L[i * (i + 1) / 2 + i];
-                }
+                for (int k = i + 1; k < J; ++k) x -= L[k * (k + 1) / 2 + i] * y[k];
+                y[i] = x * dinv[i];
+            }
 #pragma unroll
-                for (int p = 0; p < J; ++p) {
-                    u[p] -= y[p];
-                    U[row * J + p] = u[p];
-                }
+            for (int p = 0; p < J; ++p) {
+                u[p] -= y[p];
+                U[row * J + p] = u[p];
             }
         }
         for (int e = 0; e < RS; e += 4) *reinterpret_cast<float4 *>(acc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    {  // the row's share of the moments: weight cnt / n, folded into the row as its square root
+        const float sw = sqrtf((float)nrow * inv_n);
 #pragma unroll
-    for (int p = 0; p < J; ++p) rows[threadIdx.x * J + p] = u[p];
-    wts[threadIdx.x] = valid ? (float)cnt[row] * inv_n : 0.f;
+        for (int p = 0; p < JE; ++p) rows[threadIdx.x * JE + p] = p < J ? sw * u[p] : 0.f;
+    }
     __syncthreads();
-    // moments: each of the J*J outputs is split over R threads (a slice of the rows each),
-    // with four independent partial sums per thread
-    constexpr int R = pow2_floor((J * J >= kRowsPerThreadCta) ? 1 : kRowsPerThreadCta / (J * J));
-    constexpr int SL = kRowsPerThreadCta / R;  // a multiple of 4 (R <= 64)
-    static_assert(SL * R == kRowsPerThreadCta && SL % 4 == 0, "row slices");
-    for (int s = threadIdx.x; s < J * J * R; s += blockDim.x) {
-        const int e = s % (J * J), h = s / (J * J);
-        const int p = e / J, q = e % J;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        const int i0 = h * SL;
-#pragma unroll 2
-        for (int i = i0; i < i0 + SL; i += 4) {
-            a0 = fmaf(wts[i] * rows[i * J + p], rows[i * J + q], a0);
-            a1 = fmaf(wts[i + 1] * rows[(i + 1) * J + p], rows[(i + 1) * J + q], a1);
-            a2 = fmaf(wts[i + 2] * rows[(i + 2) * J + p], rows[(i + 2) * J + q], a2);
-            a3 = fmaf(wts[i + 3] * rows[(i + 3) * J + p], rows[(i + 3) * J + q], a3);
+    // moments sum_i w_i u_i u_i^T: one 2 x 2 block (rows p, p + 1; columns q, q + 1; p <= q) per
+    // group of R consecutive lanes, lane h of the group taking rows h, h + R, ...; the group's
+    // sums meet by shuffles and its first lane adds the block and its mirror image
+    constexpr int NB = JE / 2, NBLK = NB * (NB + 1) / 2;
+    constexpr int R = pow2_floor(NBLK >= kRowsPerThreadCta ? 1 : (kRowsPerThreadCta / NBLK < 32 ? kRowsPerThreadCta / NBLK : 32));
+    static_assert(kRowsPerThreadCta % R == 0 && 32 % R == 0, "row groups");
+    for (int base = 0; base < NBLK * R; base += blockDim.x) {
+        const int t = base + threadIdx.x, bk = t / R, h = t % R;
+        float m00 = 0.f, m01 = 0.f, m10 = 0.f, m11 = 0.f;
+        int bp = 0, bq = 0;
+        if (bk < NBLK) {
+            // block bk -> (bp, bq), bp <= bq, in row-major order of the upper triangle
+            int rem = bk;
+            while (rem >= NB - bp) { rem -= NB - bp; ++bp; }
+            bq = bp + rem;
+#pragma unroll 4
+            for (int i = h; i < kRowsPerThreadCta; i += R) {
+                const float2 x = *reinterpret_cast<const float2 *>(rows + i * JE + 2 * bp);
+                const float2 y = *reinterpret_cast<const float2 *>(rows + i * JE + 2 * bq);
+                m00 = fmaf(x.x, y.x, m00);
+                m01 = fmaf(x.x, y.y, m01);
+                m10 = fmaf(x.y, y.x, m10);
+                m11 = fmaf(x.y, y.y, m11);
+            }
         }
-        atomicAdd(gram_out + e, (a0 + a1) + (a2 + a3));
+#pragma unroll
+        for (int o = R / 2; o; o >>= 1) {
+            m00 += __shfl_xor_sync(0xffffffffu, m00, o);
+            m01 += __shfl_xor_sync(0xffffffffu, m01, o);
+            m10 += __shfl_xor_sync(0xffffffffu, m10, o);
+            m11 += __shfl_xor_sync(0xffffffffu, m11, o);
+        }
+        if (bk < NBLK && h == 0) {
+            const int p = 2 * bp, q = 2 * bq;
+            const float m[4] = {m00, m01, m10, m11};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int pp = p + (c >> 1), qq = q + (c & 1);
+                if (pp < J && qq < J) {
+                    atomicAdd(gram_out + pp * J + qq, m[c]);
+                    if (bp != bq) atomicAdd(gram_out + qq * J + pp, m[c]);
+                }
+            }
+        }
     }
 }
 
@@ -1559,10 +1627,14 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
 //   core gradient D = sum_k M_k kron c_k + n lambda/|Omega| G, solved in the eigenbases:
 //   G <- G - (Va, Vb, Vc) [ (D x1 Va^T x2 Vb^T x3 Vc^T) / (4 la lb lc + diag) ];
 //   then the moments of the previous wave end are cleared for reuse.
+// CJ1, CJ2, CJ3: the core ranks when fixed at compile time (0: read from A.d).
+template <int CJ1, int CJ2, int CJ3>
 __device__ void dense_post(const DenseArgs &A, float *sm) {
     const Dims &d = A.d;
-    const int J1 = d.J1, J2 = d.J2, J3 = d.J3, I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
-    const int ld = eig_ld(d);
+    constexpr bool kFixed = CJ1 > 0 && CJ2 > 0 && CJ3 > 0;
+    const int J1 = kFixed ? CJ1 : d.J1, J2 = kFixed ? CJ2 : d.J2, J3 = kFixed ? CJ3 : d.J3;
+    const int I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2, J23 = J2 * J3;
+    const int ld = kFixed ? (CJ1 > CJ2 ? (CJ1 > CJ3 ? CJ1 : CJ3) : (CJ2 > CJ3 ? CJ2 : CJ3)) + 1 : eig_ld(d);
     float *sG = sm;                  // PI
     float *sX = sG + PI;             // PI (scratch)
     float *sT = sX + PI;             // PI (scratch)
@@ -1573,27 +1645,34 @@ __device__ void dense_post(const DenseArgs &A, float *sm) {
     float *Vb = Va + J1 * ld;        // J2 x ld
     float *Vc = Vb + J2 * ld;        // J3 x ld
     float *la = Vc + J3 * ld;        // J1 + J2 + J3 eigenvalues
-    float *sMacc = la + J1 + J2 + J3;  // the wave's M_k, if they fit
+    float *sInv = la + J1 + J2 + J3; // I3 x J3 x J3 platform-system inverses
+    float *sNk = sInv + I3 * J3 * J3;  // I3: the wave's entries per platform
+    float *sCnt = sNk + I3;          // I3: all entries per platform
+    float *sMacc = sCnt + I3;        // the wave's M_k, if they fit
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool stage_m = I3 * Q <= kMaccStage;
     const float *Mk = stage_m ? sMacc : A.macc;
-    {  // the step's inputs, four loads per thread in flight at a time
+    {  // every input of the step, eight loads per thread in flight at a time
         const int o1 = stage_m ? I3 * Q : 0, o2 = o1 + PI, o3 = o2 + I3 * J3, o4 = o3 + J1 * J1,
-                  o5 = o4 + J2 * J2, o6 = o5 + J3 * J3, N = o6 + J1 + J2 + J3;
-        for (int base = tid; base < N; base += 4 * nt) {
-            float v[4];
+                  o5 = o4 + J2 * J2, o6 = o5 + J3 * J3, o7 = o6 + J1 + J2 + J3, o8 = o7 + I3 * J3 * J3,
+                  o9 = o8 + I3, N = o9 + I3;
+        for (int base = tid; base < N; base += 8 * nt) {
+            float v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int t = base + u * nt;
                 v[u] = t >= N ? 0.f
                        : t < o1 ? A.macc[t]
                        : t < o2 ? A.G[t - o1]
                        : t < o3 ? A.U3[t - o2]
                        : t < o6 ? A.eigv[t - o3]  // Ma, Mb, Cn eigenvectors, contiguous
-                                : A.eigval[t - o6];
+                       : t < o7 ? A.eigval[t - o6]
+                       : t < o8 ? A.ainv[t - o7]
+                       : t < o9 ? A.nk[t - o8]
+                                : (float)A.cnt3[t - o9];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int t = base + u * nt;
                 if (t >= N) continue;
                 if (t < o1) {
@@ -1611,21 +1690,35 @@ __device__ void dense_post(const DenseArgs &A, float *sm) {
                 } else if (t < o6) {
                     const int e = t - o5;
                     Vc[(e / J3) * ld + e % J3] = v[u];
-                } else {
+                } else if (t < o7) {
                     la[t - o6] = fmaxf(v[u], 0.f);
+                } else {
+                    sInv[t - o7] = v[u];  // then sNk, sCnt (contiguous)
                 }
             }
         }
     }
     __syncthreads();
     const float *lb = la + J1, *lc = la + J1 + J2;
-    for (int s = tid; s < I3 * J3; s += nt) {  // platform gradients
-        const int k = s / J3, r = s % J3;
-        float a = 0.f;
-        const float *M = Mk + (int64_t)k * Q;
-        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], M[pq], a);
-        const float reg = A.cnt3[k] > 0 ? A.nk[k] * A.lam / (float)A.cnt3[k] : 0.f;
-        sGk[s] = fmaf(reg, sC[s], a);
+    {  // platform gradients: TP lanes per output, partial sums met by shuffles
+        const int NO = I3 * J3;
+        int TP = 1;
+        while (TP < 32 && 2 * TP * NO <= nt) TP *= 2;
+        for (int base = 0; base < NO * TP; base += nt) {  // the same trip count in every thread
+            const int t = base + tid, o = t / TP, h = t % TP;
+            float a = 0.f;
+            if (o < NO) {
+                const int k = o / J3, r = o % J3;
+                const float *M = Mk + (int64_t)k * Q;
+                for (int pq = h; pq < Q; pq += TP) a = fmaf(sG[pq * J3 + r], M[pq], a);
+            }
+            for (int w = TP / 2; w; w >>= 1) a += __shfl_xor_sync(0xffffffffu, a, w);
+            if (o < NO && h == 0) {
+                const int k = o / J3;
+                const float reg = sCnt[k] > 0.f ? sNk[k] * A.lam / sCnt[k] : 0.f;
+                sGk[o] = fmaf(reg, sC[o], a);
+            }
+        }
     }
     for (int s = tid; s < PI; s += nt) {  // core gradient D
         const int pq = s / J3, r = s % J3;
@@ -1636,53 +1729,60 @@ __device__ void dense_post(const DenseArgs &A, float *sm) {
     __syncthreads();
     for (int s = tid; s < I3 * J3; s += nt) {  // platform steps
         const int k = s / J3, r = s % J3;
-        const float *inv = A.ainv + (int64_t)k * J3 * J3 + r * J3;
+        const float *inv = sInv + (k * J3 + r) * J3;
         float a = 0.f;
+#pragma unroll
         for (int t = 0; t < J3; ++t) a = fmaf(inv[t], sGk[k * J3 + t], a);
         sDel[s] = a;
     }
     // D <- D x1 Va^T x2 Vb^T x3 Vc^T   (index s = (p*J2 + q)*J3 + r)
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int p = s / J23, qr = s % J23;
         float a = 0.f;
-        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[pp * ld + p], sX[(pp * J2 + q) * J3 + r], a);
+#pragma unroll
+        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[pp * ld + p], sX[pp * J23 + qr], a);
         sT[s] = a;
     }
     __syncthreads();
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int p = s / J23, q = (s / J3) % J2, r = s % J3;
         float a = 0.f;
-        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[qq * ld + q], sT[(p * J2 + qq) * J3 + r], a);
+#pragma unroll
+        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[qq * ld + q], sT[p * J23 + qq * J3 + r], a);
         sX[s] = a;
     }
     __syncthreads();
     const float diag = 1.f / A.lr + kBlocks * A.n_wave * A.lam_core;
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int p = s / J23, q = (s / J3) % J2, r = s % J3;
         float a = 0.f;
-        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[rr * ld + r], sX[(p * J2 + q) * J3 + rr], a);
+#pragma unroll
+        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[rr * ld + r], sX[(s - r) + rr], a);
         sT[s] = a / (kBlocks * la[p] * lb[q] * lc[r] + diag);
     }
     __syncthreads();
     // back: D <- D x1 Va x2 Vb x3 Vc
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int p = s / J23, qr = s % J23;
         float a = 0.f;
-        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[p * ld + pp], sT[(pp * J2 + q) * J3 + r], a);
+#pragma unroll
+        for (int pp = 0; pp < J1; ++pp) a = fmaf(Va[p * ld + pp], sT[pp * J23 + qr], a);
         sX[s] = a;
     }
     __syncthreads();
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int p = s / J23, q = (s / J3) % J2, r = s % J3;
         float a = 0.f;
-        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[q * ld + qq], sX[(p * J2 + qq) * J3 + r], a);
+#pragma unroll
+        for (int qq = 0; qq < J2; ++qq) a = fmaf(Vb[q * ld + qq], sX[p * J23 + qq * J3 + r], a);
         sT[s] = a;
     }
     __syncthreads();
     for (int s = tid; s < PI; s += nt) {
-        const int p = s / (J2 * J3), q = (s / J3) % J2, r = s % J3;
+        const int r = s % J3;
         float a = 0.f;
-        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[r * ld + rr], sT[(p * J2 + q) * J3 + rr], a);
+#pragma unroll
+        for (int rr = 0; rr < J3; ++rr) a = fmaf(Vc[r * ld + rr], sT[(s - r) + rr], a);
         A.G[s] = sG[s] - a;
     }
     for (int s = tid; s < I3 * J3; s += nt) A.U3[s] = sC[s] - sDel[s];
@@ -1727,11 +1827,11 @@ __device__ void wave_end_rows(const DenseArgs &A, const RowArgs &R, int blk, int
     }
 }
 
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int CJ3>
 __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, int mode) {
     extern __shared__ __align__(16) float smw[];
     if (blockIdx.x == 0) {
-        if (mode == 0) dense_post(A, smw);
+        if (mode == 0) dense_post<CJ1, CJ2, CJ3>(A, smw);
         return;
     }
     wave_end_rows<CJ1, CJ2>(A, R, blockIdx.x - 1, mode, smw);
@@ -1739,7 +1839,7 @@ __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, i
 
 // The end of one wave for every problem of a batch: per problem one CTA takes the dense step
 // and the next ones its row steps (boff: prefix offsets of the problems' CTAs).
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int CJ3>
 __global__ void __launch_bounds__(256)
     k_batch_wave_end(const DenseArgs *__restrict__ dargs, const RowArgs *__restrict__ rargs,
                      const int32_t *__restrict__ boff, int32_t P) {
@@ -1759,34 +1859,44 @@ __global__ void __launch_bounds__(256)
     const DenseArgs A = dargs[pid];
     const RowArgs R = rargs[pid];
     if (local == 0) {
-        dense_post(A, smw);
+        dense_post<CJ1, CJ2, CJ3>(A, smw);
         return;
     }
     wave_end_rows<CJ1, CJ2>(A, R, local - 1, 0, smw);
 }
 
-// compile-time row ranks of the thread-per-row step
-#define SNECT_DISPATCH_ROWS(J1, J2, FN, ...)                           \
-    (((J1) == 5 && (J2) == 5)     ? FN<5, 5>(__VA_ARGS__)              \
-     : ((J1) == 10 && (J2) == 10) ? FN<10, 10>(__VA_ARGS__)            \
-     : ((J1) == 16 && (J2) == 16) ? FN<16, 16>(__VA_ARGS__)            \
-                                  : FN<0, 0>(__VA_ARGS__))
+// compile-time row ranks of the thread-per-row step, and all three ranks of the dense step
+// where they match a common configuration
+#define SNECT_DISPATCH_ROWS(J1, J2, J3, FN, ...)                                  \
+    (((J1) == 5 && (J2) == 5)     ? ((J3) == 2 ? FN<5, 5, 2>(__VA_ARGS__)          \
+                                               : FN<5, 5, 0>(__VA_ARGS__))         \
+     : ((J1) == 10 && (J2) == 10) ? ((J3) == 5 ? FN<10, 10, 5>(__VA_ARGS__)        \
+                                               : FN<10, 10, 0>(__VA_ARGS__))       \
+     : ((J1) == 16 && (J2) == 16) ? ((J3) == 5 ? FN<16, 16, 5>(__VA_ARGS__)        \
+                                               : FN<16, 16, 0>(__VA_ARGS__))       \
+                                  : FN<0, 0, 0>(__VA_ARGS__))
 
 template <int CJ1, int CJ2>
 int rows_per_cta() { return (CJ1 > 0 && CJ2 > 0) ? kRowsPerThreadCta : kRowsPerCta; }
 
-template <int CJ1, int CJ2>
+// the sweep's shared-memory carveout too, so that the SMs keep one configuration across
+// the kernels of an epoch
+template <int CJ1, int CJ2, int CJ3>
 cudaError_t set_wave_end_attr(Ctx *, size_t smem) {
-    return cudaFuncSetAttribute(k_fast_wave_end<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fast_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fast_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int CJ3>
 cudaError_t launch_wave_end_k(Ctx *c, const DenseArgs &A, RowArgs R, int mode, size_t smem) {
     const int rpc = rows_per_cta<CJ1, CJ2>();
     R.nb1 = ceil_div(c->d.I1, rpc);
     const int nb2 = ceil_div(c->d.I2, rpc);
     const unsigned grid = (unsigned)(1 + R.nb1 + nb2);
-    k_fast_wave_end<CJ1, CJ2><<<grid, 256, smem, c->stream>>>(A, R, mode);
+    k_fast_wave_end<CJ1, CJ2, CJ3><<<grid, 256, smem, c->stream>>>(A, R, mode);
     return cudaGetLastError();
 }
 
@@ -1911,10 +2021,8 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - 1), nt) + 1;
     c->launches++;
     if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
-    if (c->wcnt)
-        k_fast_sweep<CJ1, CJ2, CJ3, false><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
-    else
-        k_fast_sweep<CJ1, CJ2, CJ3, true><<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
+    auto kern = c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
+    kern<<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
     return cudaGetLastError();
 }
 
@@ -1923,7 +2031,7 @@ size_t wave_end_smem(const Ctx *c) {
     const size_t dense = (size_t)dense_post_floats(d);
     const size_t rows = std::max<size_t>(kRowWarps * ((size_t)kMaxRank * kTileStride + 2 * kMaxRank) +
                                              kRowWarps * (size_t)kMaxRank * kMaxRank + kCkStage,
-                                         (size_t)kRowsPerThreadCta * (std::max(d.J1, d.J2) + 1) + kCkStage);
+                                         (size_t)std::max(rows_thread_floats(d.J1), rows_thread_floats(d.J2)));
     return sizeof(float) * std::max(dense, rows);
 }
 
@@ -1976,7 +2084,7 @@ cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
     RowArgs R;
     make_wave_args(c, w, parity, mode, &A, &R);
     c->launches++;
-    return SNECT_DISPATCH_ROWS(c->d.J1, c->d.J2, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
+    return SNECT_DISPATCH_ROWS(c->d.J1, c->d.J2, c->d.J3, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
 }
 
 }  // namespace
@@ -2007,7 +2115,7 @@ int init_fast(Ctx *c) {
         SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
     }
     SNECT_CUDA(c, cudaMemsetAsync(c->flag + 2, 0, 2 * sizeof(int32_t), c->stream));
-    SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, set_wave_end_attr, c, wave_end_smem(c)));
+    SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, d.J3, set_wave_end_attr, c, wave_end_smem(c)));
     // the first wave's moments: those of the initial rows, into the odd buffer (the first
     // wave's pre-work forms its curvatures and eigenbases from them)
     SNECT_CUDA(c, launch_wave_end(c, -1, 1, 1));
@@ -2020,9 +2128,10 @@ int enqueue_fast_epoch(Ctx *c) {
     SNECT_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(int32_t) * c->n_waves, c->stream));
     // n_waves is even, so wave w's parity (w % 2) continues across epochs
     for (int64_t w = 0; w < c->n_waves; ++w) {
-        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[w], c->stream, cudaEventRecordExternal));
+        const bool tm = c->time_launch(w, c->n_waves, c->wave_len[w]);
+        if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[w], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, run_sweep, c, w));
-        SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[w], c->stream, cudaEventRecordExternal));
+        if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[w], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_wave_end(c, w, (int)(w & 1), 0));
     }
     return SNECT_OK;
@@ -2090,13 +2199,16 @@ cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int CJ3>
 cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
     const size_t smem = wave_end_smem(b->ctx[0]);
-    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_batch_wave_end<CJ1, CJ2><<<b->wave_end_blocks, 256, smem, st>>>(b->d_dense + w * b->P, b->d_rows + w * b->P,
+    k_batch_wave_end<CJ1, CJ2, CJ3><<<b->wave_end_blocks, 256, smem, st>>>(b->d_dense + w * b->P, b->d_rows + w * b->P,
                                                                      b->d_boff, b->P);
     return cudaGetLastError();
 }
@@ -2110,7 +2222,7 @@ cudaError_t batch_sweep_attr(Batch *b) {
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int CJ3>
 int batch_rows_per_cta(Batch *) { return rows_per_cta<CJ1, CJ2>(); }
 
 int batch_fail(Batch *b, int code, const std::string &m) {
@@ -2136,7 +2248,7 @@ int batch_build_graph(Batch *b) {
         b->epoch_kernels = 0;
         for (int64_t w = 0; w < b->n_waves && e == cudaSuccess; ++w) {
             e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_sweep_k, b, w, cap);
-            if (e == cudaSuccess) e = SNECT_DISPATCH_ROWS(d.J1, d.J2, batch_wave_end_k, b, w, cap);
+            if (e == cudaSuccess) e = SNECT_DISPATCH_ROWS(d.J1, d.J2, d.J3, batch_wave_end_k, b, w, cap);
             b->epoch_kernels += 2;
         }
         if (e == cudaSuccess)  // every problem's network pass
@@ -2204,7 +2316,7 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     std::vector<DenseArgs> hd((size_t)(W * P));
     std::vector<RowArgs> hr((size_t)(W * P));
     std::vector<int32_t> toff((size_t)(W * (P + 1))), boff((size_t)P + 1);
-    const int rpc = SNECT_DISPATCH_ROWS(b->d.J1, b->d.J2, batch_rows_per_cta, b);
+    const int rpc = SNECT_DISPATCH_ROWS(b->d.J1, b->d.J2, b->d.J3, batch_rows_per_cta, b);
     boff[0] = 0;
     for (int64_t p = 0; p < P; ++p) {
         Ctx *c = b->ctx[p];

@@ -60,6 +60,30 @@ def test_fast_mode_is_stable_for_any_wave(small, gpu_lib):
         assert np.isfinite(l1["total"]) and l1["total"] < l0["total"], (wave, l0, l1)
 
 
+def test_sweep_timing_modes(gpu_lib):
+    """Timing events: none by default, the middle launch (mode 1) or every launch (mode -1);
+    the timed launches account for their entries, all of them over a whole epoch."""
+    import paper_1711_08095_gb300 as snect
+
+    p = S.config2(n_patients=60, n_genes=2000, nnz=40_000, n_edges=3_000)
+    for batch in (0, 1024):
+        c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                        batch=batch, wave=4000 if batch == 0 else 0)
+        c.epoch(1)
+        assert c.sweep_times() == (0.0, 0, 0)
+        c.set_sweep_timing(-1)
+        c.epoch(1)
+        ms, n, e = c.sweep_times()
+        assert n >= 2 and e == len(p.idx) and ms > 0, (batch, ms, n, e)
+        c.set_sweep_timing(1)
+        c.epoch(2)
+        ms1, n1, e1 = c.sweep_times()
+        assert n1 == 1 and 0 < e1 <= -(-len(p.idx) // (n - 1)) and ms1 > 0, (batch, ms1, n1, e1)
+        with pytest.raises(RuntimeError):
+            c.set_sweep_timing(2)
+        c.close()
+
+
 def test_fast_mode_unobserved_rows_stay_and_small_waves_work(gpu_lib):
     p = S.config2(n_patients=60, n_genes=2000, nnz=40_000, n_edges=3_000)
     c = ctx(p, wave=1000)  # many waves, ragged platform segments and tiles
