@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--e2e-jobs", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true",
                     help="a smaller problem of the same shape, 12M entries (for profiling)")
@@ -550,7 +550,8 @@ def main():
         "e2e": {"value": p.nnz * job_epochs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "step": "one training job: snect_init from pinned host buffers, %d epochs, objective and "
-                        "factors read back (median of %d jobs, %.1f ms)" % (job_epochs, len(e2e_times), e2e_s * 1e3)},
+                        "factors read back (median of %d jobs, %.1f ms)" % (job_epochs, len(e2e_times), e2e_s * 1e3),
+                "jobs_ms": [round(x * 1e3, 2) for x in e2e_times]},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
                      "frac": (achieved / pk) if achieved else None,

@@ -101,7 +101,11 @@ struct FastArgs {
     int32_t count_atomics;  // 1: count each row's entries per platform with atomics (no table)
 };
 
-__device__ void dense_pre(const DenseArgs &A, float *sm);
+// The wave-independent half of the dense step; part 0, 1, 2 split it over three CTAs, -1
+// runs all of it in one.
+template <int CJ1 = 0, int CJ2 = 0, int CJ3 = 0>
+__device__ void dense_pre(const DenseArgs &A, float *sm, int part = -1);
+constexpr int kPreCtas = 3;  // CTAs of a fast-sweep launch that take the dense pre-work
 
 // Adds each run of equal patient indices in a warp to its patient row once.  The entries of a
 // tile are sorted by patient within their wave and platform, so a patient's entries sit next
@@ -556,9 +560,10 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
     const int J1P = even_up(J1), J2P = even_up(J2);
     const int PI = J1 * J2 * J3;
     extern __shared__ __align__(16) float sm[];
-    // CTA 0 (dispatched first, so it runs beside the tile CTAs): the wave's dense pre-work
-    if (blockIdx.x == 0) {
-        dense_pre(A.pre, sm);
+    // CTAs 0-2 (dispatched first, so they run beside the tile CTAs): the wave's dense
+    // pre-work, split into its three independent parts
+    if (blockIdx.x < kPreCtas) {
+        dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
         return;
     }
     float *sG = sm;                            // PI
@@ -588,8 +593,8 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
         }
         __syncthreads();
         const int lane = tid & 31;
-        const int64_t W = (int64_t)(gridDim.x - 1) * (kFastThreads / 32);
-        const int64_t w = (int64_t)(blockIdx.x - 1) * (kFastThreads / 32) + (tid >> 5);
+        const int64_t W = (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32);
+        const int64_t w = (int64_t)(blockIdx.x - kPreCtas) * (kFastThreads / 32) + (tid >> 5);
         const int64_t U = (int64_t)A.n_tiles * (kFastTile / 32);
         const int64_t u0 = w * U / W, u1 = (w + 1) * U / W;
         float mreg[MRows<CJ1>::n];
@@ -1215,8 +1220,17 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
 #pragma unroll 4
             for (int k = 0; k < I3; ++k) n += wn[k];
         }
+        if constexpr (J % 2 == 0) {  // the row starts on an 8-byte boundary
 #pragma unroll
-        for (int p = 0; p < J; ++p) u[p] = U[row * J + p];
+            for (int p = 0; p < J; p += 2) {
+                const float2 v = *reinterpret_cast<const float2 *>(U + row * J + p);
+                u[p] = v.x;
+                u[p + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < J; ++p) u[p] = U[row * J + p];
+        }
 #pragma unroll
         for (int p = 0; p < J; p += 4) {
             const float4 v = *reinterpret_cast<const float4 *>(acc + p);
@@ -1304,12 +1318,16 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
                 y[i] = x * dinv[i];
             }
 #pragma unroll
-            for (int p = 0; p < J; ++p) {
-                u[p] -= y[p];
-                U[row * J + p] = u[p];
+            for (int p = 0; p < J; ++p) u[p] -= y[p];
+            if constexpr (J % 2 == 0) {
+#pragma unroll
+                for (int p = 0; p < J; p += 2)
+                    *reinterpret_cast<float2 *>(U + row * J + p) = make_float2(u[p], u[p + 1]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < J; ++p) U[row * J + p] = u[p];
             }
         }
-        for (int e = 0; e < RS; e += 4) *reinterpret_cast<float4 *>(acc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     {  // the row's share of the moments: weight cnt / n, folded into the row as its square root
         const float sw = sqrtf((float)nrow * inv_n);
@@ -1317,6 +1335,11 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
         for (int p = 0; p < JE; ++p) rows[threadIdx.x * JE + p] = p < J ? sw * u[p] : 0.f;
     }
     __syncthreads();
+    {  // every thread has read its accumulators: clear the CTA's rows of them, coalesced
+        const int nr = (int)(I - r0 < kRowsPerThreadCta ? I - r0 : kRowsPerThreadCta);
+        float4 *a4 = reinterpret_cast<float4 *>(g + r0 * RS);  // RS is a multiple of 4
+        for (int t = threadIdx.x; t < nr * RS / 4; t += blockDim.x) a4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     // moments sum_i w_i u_i u_i^T: one 2 x 2 block (rows p, p + 1; columns q, q + 1; p <= q) per
     // group of R consecutive lanes, lane h of the group taking rows h, h + R, ...; the group's
     // sums meet by shuffles and its first lane adds the block and its mirror image
@@ -1466,9 +1489,10 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, int ld, float *
     __syncwarp();
 }
 
-// The wave-independent half of the dense step, taken during the wave's sweep by one extra
-// CTA of the sweep launch: it needs only values fixed before the sweep (G, the platform rows,
-// the moments of the previous wave end, the wave's platform counts).
+// The wave-independent half of the dense step, taken during the wave's sweep by extra CTAs
+// of the sweep launch (three in the FP32 fast sweep, one part each; one CTA elsewhere): it
+// needs only values fixed before the sweep (G, the platform rows, the moments of the
+// previous wave end, the wave's platform counts).  Its three parts are independent.
 //   * Cn = sum_k n_k c_k c_k^T and the eigen-decompositions of Ma, Mb, Cn (Jacobi sweeps from
 //     the previous eigenbasis every kEigEvery-th wave; in between the eigenbasis is kept and
 //     the eigenvalues refreshed as its Rayleigh quotients) -> eigv, eigval;
@@ -1477,10 +1501,14 @@ __device__ void warp_jacobi(float *M, float *V, float *T, int n, int ld, float *
 //     entries in the wave);
 //   * the platform curvatures C1_k = Gc_k Mb Gc_k^T, C2_k = Gc_k^T Ma Gc_k (Gc_k = G x3 c_k)
 //     for the wave's row steps -> curv.
-__device__ void dense_pre(const DenseArgs &A, float *sm) {
+template <int CJ1, int CJ2, int CJ3>
+__device__ void dense_pre(const DenseArgs &A, float *sm, int part) {
     const Dims &d = A.d;
-    const int J1 = d.J1, J2 = d.J2, J3 = d.J3, I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
-    const int ld = eig_ld(d), TS = eig_tile(d);
+    constexpr bool kFixed = CJ1 > 0 && CJ2 > 0 && CJ3 > 0;
+    const int J1 = kFixed ? CJ1 : d.J1, J2 = kFixed ? CJ2 : d.J2, J3 = kFixed ? CJ3 : d.J3;
+    const int I3 = d.I3, PI = J1 * J2 * J3, Q = J1 * J2;
+    const int ld = kFixed ? (CJ1 > CJ2 ? (CJ1 > CJ3 ? CJ1 : CJ3) : (CJ2 > CJ3 ? CJ2 : CJ3)) + 1 : eig_ld(d);
+    const int TS = eig_tile(d);
     float *sG = sm;                  // PI
     float *sX = sG + PI;             // PI (scratch)
     float *sT = sX + PI;             // PI (scratch)
@@ -1492,27 +1520,33 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
     float *sJ = sMb + J2 * J2;       // 3 x (M, V, T) tiles
     float *sAk = sJ + 9 * TS;        // I3 x J3 x J3 platform systems
     const int tid = threadIdx.x, nt = blockDim.x;
-    const bool full_eig = (*A.wave_counter % kEigEvery) == 0;
-    for (int s = tid; s < PI; s += nt) sG[s] = A.G[s];
-    for (int s = tid; s < I3 * J3; s += nt) sC[s] = A.U3[s];
-    for (int s = tid; s < J1 * J1; s += nt) sMa[s] = A.gram_in[s];
-    for (int s = tid; s < J2 * J2; s += nt) sMb[s] = A.gram_in[J1 * J1 + s];
+    // part 0: eigenbases; 1: H and the platform-system inverses; 2: row curvatures; -1: all
+    const bool want_eig = part < 0 || part == 0, want_h = part < 0 || part == 1, want_curv = part < 0 || part == 2;
+    if (want_h || want_curv)
+        for (int s = tid; s < PI; s += nt) sG[s] = A.G[s];
+    if (want_eig || want_curv)
+        for (int s = tid; s < I3 * J3; s += nt) sC[s] = A.U3[s];
+    for (int s = tid; s < J1 * J1 + J2 * J2; s += nt) sMa[s] = A.gram_in[s];  // Ma, Mb (contiguous)
     __syncthreads();
-    for (int s = tid; s < J3 * J3; s += nt) {
-        const int r = s / J3, t = s % J3;
-        float a = 0.f;
-        for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
-        sCn[s] = a;
-    }
-    for (int s = tid; s < PI; s += nt) {  // X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
-        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-        float a = 0.f;
-        for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
-        sX[s] = a;
-    }
+    if (want_eig)
+        for (int s = tid; s < J3 * J3; s += nt) {
+            const int r = s / J3, t = s % J3;
+            float a = 0.f;
+            for (int k = 0; k < I3; ++k) a = fmaf(A.nk[k] * sC[k * J3 + r], sC[k * J3 + t], a);
+            sCn[s] = a;
+        }
+    if (want_h)
+        for (int s = tid; s < PI; s += nt) {  // X[r][p][q'] = sum_p' Ma[p][p'] g(p', q', r)
+            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+            float a = 0.f;
+#pragma unroll
+            for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sG[(pp * J2 + q) * J3 + r], a);
+            sX[s] = a;
+        }
     __syncthreads();
     const int warp = tid >> 5;
-    if (warp < 3) {  // eigen-decompositions of Ma, Mb, Cn, one warp each
+    if (want_eig && warp < 3) {  // eigen-decompositions of Ma, Mb, Cn, one warp each
+        const bool full_eig = (*A.wave_counter % kEigEvery) == 0;
         const int n = warp == 0 ? J1 : (warp == 1 ? J2 : J3);
         const float *src = warp == 0 ? sMa : (warp == 1 ? sMb : sCn);
         float *M = sJ + warp * 3 * TS, *V = M + TS, *T = V + TS;
@@ -1523,62 +1557,118 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         const int eoff = warp == 0 ? 0 : (warp == 1 ? J1 : J1 + J2);
         for (int p = (tid & 31); p < n; p += 32) A.eigval[eoff + p] = M[p * ld + p];
     }
-    for (int s = tid; s < PI; s += nt) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
-        const int r = s / Q, p = (s / J2) % J1, q = s % J2;
-        float a = 0.f;
-        for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
-        sT[s] = a;
-    }
-    __syncthreads();
-    for (int s = tid; s < J3 * J3; s += nt) {  // H[r][t] = sum_pq g(p,q,r) T[t][p][q]
-        const int r = s / J3, t = s % J3;
-        float a = 0.f;
-        for (int pq = 0; pq < Q; ++pq) a = fmaf(sG[pq * J3 + r], sT[t * Q + pq], a);
-        sH[s] = a;
-    }
-    __syncthreads();
-    if (tid < I3) {  // platform row k: the inverse of (4 (n_k H + reg I) + I/lr), by Cholesky
-        const int k = tid;
-        float *Ak = sAk + k * J3 * J3;
-        float *inv = A.ainv + (int64_t)k * J3 * J3;
-        const float nk = A.nk[k];
-        if (nk > 0.f) {
+    if (want_h) {
+        for (int s = tid; s < PI; s += nt) {  // T[r][p][q] = sum_q' X[r][p][q'] Mb[q'][q]
+            const int r = s / Q, p = (s / J2) % J1, q = s % J2;
+            float a = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < J2; ++qq) a = fmaf(sX[(r * J1 + p) * J2 + qq], sMb[qq * J2 + q], a);
+            sT[s] = a;
+        }
+        __syncthreads();
+        // H[r][t] = sum_pq g(p,q,r) T[t][p][q]: TP lanes per output, partial sums met by shuffles
+        const int NO = J3 * J3;
+        int TP = 1;
+        while (TP < 32 && 2 * TP * NO <= nt) TP *= 2;
+        for (int base = 0; base < NO * TP; base += nt) {  // the same trip count in every thread
+            const int t = base + tid, o = t / TP, h = t % TP;
+            float a = 0.f;
+            if (o < NO) {
+                const int r = o / J3, tt = o % J3;
+                for (int pq = h; pq < Q; pq += TP) a = fmaf(sG[pq * J3 + r], sT[tt * Q + pq], a);
+            }
+            for (int w = TP / 2; w; w >>= 1) a += __shfl_xor_sync(0xffffffffu, a, w);
+            if (o < NO && h == 0) sH[o] = a;
+        }
+        __syncthreads();
+        for (int k = tid; k < I3; k += nt) {  // platform row k: the inverse of (4 (n_k H + reg I) + I/lr)
+            float *inv = A.ainv + (int64_t)k * J3 * J3;
+            const float nk = A.nk[k];
+            if (!(nk > 0.f)) {
+                for (int e = 0; e < J3 * J3; ++e) inv[e] = 0.f;
+                continue;
+            }
             const float reg = A.cnt3[k] > 0 ? nk * A.lam / (float)A.cnt3[k] : 0.f;
-            for (int r = 0; r < J3; ++r)
-                for (int t = 0; t < J3; ++t)
-                    Ak[r * J3 + t] =
-                        kBlocks * (nk * sH[r * J3 + t] + (r == t ? reg : 0.f)) + (r == t ? 1.f / A.lr : 0.f);
-            for (int j = 0; j < J3; ++j) {
-                float dd = Ak[j * J3 + j];
-                for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
-                dd = sqrtf(fmaxf(dd, 1e-20f));
-                Ak[j * J3 + j] = dd;
-                for (int i = j + 1; i < J3; ++i) {
-                    float x = Ak[i * J3 + j];
-                    for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
-                    Ak[i * J3 + j] = x / dd;
+            if constexpr (kFixed) {  // Cholesky and both solves in registers
+                constexpr int N = CJ3;
+                float L[N][N], dinv[N];
+#pragma unroll
+                for (int r = 0; r < N; ++r)
+#pragma unroll
+                    for (int t = 0; t <= r; ++t)
+                        L[r][t] = kBlocks * (nk * sH[r * N + t] + (r == t ? reg : 0.f)) + (r == t ? 1.f / A.lr : 0.f);
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    float dd = L[j][j];
+#pragma unroll
+                    for (int q = 0; q < j; ++q) dd -= L[j][q] * L[j][q];
+                    dinv[j] = rsqrtf(fmaxf(dd, 1e-20f));
+#pragma unroll
+                    for (int i = j + 1; i < N; ++i) {
+                        float x = L[i][j];
+#pragma unroll
+                        for (int q = 0; q < j; ++q) x -= L[i][q] * L[j][q];
+                        L[i][j] = x * dinv[j];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < N; ++c) {  // column c of the inverse: L L^T x = e_c
+                    float y[N];
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        float x = i == c ? 1.f : 0.f;
+#pragma unroll
+                        for (int q = 0; q < i; ++q) x -= L[i][q] * y[q];
+                        y[i] = x * dinv[i];
+                    }
+#pragma unroll
+                    for (int i = N - 1; i >= 0; --i) {
+                        float x = y[i];
+#pragma unroll
+                        for (int q = i + 1; q < N; ++q) x -= L[q][i] * y[q];
+                        y[i] = x * dinv[i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < N; ++i) inv[i * N + c] = y[i];
+                }
+            } else {
+                float *Ak = sAk + k * J3 * J3;
+                for (int r = 0; r < J3; ++r)
+                    for (int t = 0; t < J3; ++t)
+                        Ak[r * J3 + t] =
+                            kBlocks * (nk * sH[r * J3 + t] + (r == t ? reg : 0.f)) + (r == t ? 1.f / A.lr : 0.f);
+                for (int j = 0; j < J3; ++j) {
+                    float dd = Ak[j * J3 + j];
+                    for (int q = 0; q < j; ++q) dd -= Ak[j * J3 + q] * Ak[j * J3 + q];
+                    dd = sqrtf(fmaxf(dd, 1e-20f));
+                    Ak[j * J3 + j] = dd;
+                    for (int i = j + 1; i < J3; ++i) {
+                        float x = Ak[i * J3 + j];
+                        for (int q = 0; q < j; ++q) x -= Ak[i * J3 + q] * Ak[j * J3 + q];
+                        Ak[i * J3 + j] = x / dd;
+                    }
+                }
+                for (int c = 0; c < J3; ++c) {  // column c of the inverse: L L^T x = e_c
+                    float y[kMaxRank];
+                    for (int i = 0; i < J3; ++i) {
+                        float x = i == c ? 1.f : 0.f;
+                        for (int q = 0; q < i; ++q) x -= Ak[i * J3 + q] * y[q];
+                        y[i] = x / Ak[i * J3 + i];
+                    }
+                    for (int i = J3 - 1; i >= 0; --i) {
+                        float x = y[i];
+                        for (int q = i + 1; q < J3; ++q) x -= Ak[q * J3 + i] * y[q];
+                        y[i] = x / Ak[i * J3 + i];
+                    }
+                    for (int i = 0; i < J3; ++i) inv[i * J3 + c] = y[i];
                 }
             }
-            for (int c = 0; c < J3; ++c) {  // column c of the inverse: L L^T x = e_c
-                float y[kMaxRank];
-                for (int i = 0; i < J3; ++i) {
-                    float x = i == c ? 1.f : 0.f;
-                    for (int q = 0; q < i; ++q) x -= Ak[i * J3 + q] * y[q];
-                    y[i] = x / Ak[i * J3 + i];
-                }
-                for (int i = J3 - 1; i >= 0; --i) {
-                    float x = y[i];
-                    for (int q = i + 1; q < J3; ++q) x -= Ak[q * J3 + i] * y[q];
-                    y[i] = x / Ak[i * J3 + i];
-                }
-                for (int i = 0; i < J3; ++i) inv[i * J3 + c] = y[i];
-            }
-        } else {
-            for (int e = 0; e < J3 * J3; ++e) inv[e] = 0.f;
         }
     }
+    if (!want_curv) return;
     // platform curvatures for the wave's row steps (moments of gram_in): all platforms at once
     // when their Gc and W fit in the two PI-sized scratch buffers
+    __syncthreads();  // sX, sT free (part -1)
     float *sGc = sX, *sW = sT;
     const int kb = (I3 * Q <= PI) ? I3 : 1;  // platforms per batch
     for (int k0 = 0; k0 < I3; k0 += kb) {
@@ -1586,6 +1676,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         for (int s = tid; s < nkb * Q; s += nt) {  // Gc_k = G x3 c_k
             const int k = k0 + s / Q, pq = s % Q;
             float a = 0.f;
+#pragma unroll
             for (int r = 0; r < J3; ++r) a = fmaf(sG[pq * J3 + r], sC[k * J3 + r], a);
             sGc[s] = a;
         }
@@ -1593,6 +1684,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         for (int s = tid; s < nkb * Q; s += nt) {  // W1 = Gc Mb  (J1 x J2)
             const int b = s / Q, p = (s % Q) / J2, q = s % J2;
             float a = 0.f;
+#pragma unroll
             for (int qq = 0; qq < J2; ++qq) a = fmaf(sGc[b * Q + p * J2 + qq], sMb[qq * J2 + q], a);
             sW[s] = a;
         }
@@ -1600,6 +1692,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         for (int s = tid; s < nkb * J1 * J1; s += nt) {  // C1 = W1 Gc^T
             const int b = s / (J1 * J1), p = (s / J1) % J1, t = s % J1;
             float a = 0.f;
+#pragma unroll
             for (int q = 0; q < J2; ++q) a = fmaf(sW[b * Q + p * J2 + q], sGc[b * Q + t * J2 + q], a);
             A.curv[(int64_t)(k0 + b) * J1 * J1 + p * J1 + t] = a;
         }
@@ -1607,6 +1700,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         for (int s = tid; s < nkb * Q; s += nt) {  // W2 = Ma Gc  (J1 x J2)
             const int b = s / Q, p = (s % Q) / J2, q = s % J2;
             float a = 0.f;
+#pragma unroll
             for (int pp = 0; pp < J1; ++pp) a = fmaf(sMa[p * J1 + pp], sGc[b * Q + pp * J2 + q], a);
             sW[s] = a;
         }
@@ -1615,6 +1709,7 @@ __device__ void dense_pre(const DenseArgs &A, float *sm) {
         for (int s = tid; s < nkb * J2 * J2; s += nt) {  // C2 = Gc^T W2
             const int b = s / (J2 * J2), q = (s / J2) % J2, t = s % J2;
             float a = 0.f;
+#pragma unroll
             for (int p = 0; p < J1; ++p) a = fmaf(sGc[b * Q + p * J2 + q], sW[b * Q + p * J2 + t], a);
             C2[(int64_t)(k0 + b) * J2 * J2 + q * J2 + t] = a;
         }
@@ -2017,8 +2112,10 @@ template <int CJ1, int CJ2, int CJ3>
 cudaError_t run_sweep(Ctx *c, int64_t w) {
     const FastArgs A = make_fast_args(c, w);
     const int64_t nt = A.n_tiles;
-    // CTA 0 takes the wave's dense pre-work, the others the tiles (one resident wave of CTAs)
-    const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - 1), nt) + 1;
+    // CTAs 0-2 take the wave's dense pre-work (CTA 0 alone in the tensor-core form), the
+    // others the tiles (one resident wave of CTAs)
+    const int pre = c->cfg.precision == SNECT_BF16 ? 1 : kPreCtas;
+    const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - pre), nt) + pre;
     c->launches++;
     if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
     auto kern = c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
