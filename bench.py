@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry case of the same
 # structure (bench.py --small), scaled to a launch by its entries.  To be re-measured, or set to
 # None, whenever the sweep kernel changes.
-SWEEP_DRAM_BYTES_PER_ENTRY = 12.895e6 / 675_000
+SWEEP_DRAM_BYTES_PER_ENTRY = 12.864e6 / 675_000
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
