@@ -97,7 +97,7 @@ struct FastArgs {
     float *gA, *gB;
     int32_t rs1, rs2;  // row strides of gA, gB
     int32_t *err;      // set when a tensor-core wait gives up
-    DenseArgs pre;     // the wave's dense pre-work (one extra CTA of the launch)
+    DenseArgs pre;     // the wave's dense pre-work (the first CTAs of the launch)
     int32_t count_atomics;  // 1: count each row's entries per platform with atomics (no table)
 };
 
@@ -1186,14 +1186,15 @@ __device__ void wave_rows(bool first, int blk, int do_step, float *__restrict__ 
     }
 }
 
-// The same row step with one thread per row for a compile-time rank J <= 16: H (packed lower
-// triangle), its Cholesky factor and both triangular solves stay in registers, with no
-// synchronisation inside a row.
-// floats of shared memory of the thread-per-row step at rank J
+// floats of shared memory of the thread-per-row step at rank J: the stepped rows (stride J
+// rounded up to even) and the staged platform curvatures
 __host__ __device__ inline int64_t rows_thread_floats(int J) {
     return (int64_t)kRowsPerThreadCta * ((J + 1) & ~1) + kCkStage;
 }
 
+// The same row step with one thread per row for a compile-time rank J <= 16: H (packed lower
+// triangle), its Cholesky factor and both triangular solves stay in registers, with no
+// synchronisation inside a row.
 template <int CJ>
 __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, float *__restrict__ g, int32_t RS,
                                  const int32_t *__restrict__ cnt, int32_t I, int32_t I3, float lam,
