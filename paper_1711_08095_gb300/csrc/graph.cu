@@ -6,12 +6,15 @@
 // when the pass starts:
 //   u_k <- (1 - a_j) u_k + a_j s_j,   a_j = lr * lambda_g * y_kj
 // Columns of a row evolve independently.
-//   k_edge_pass        rows of degree <= kHeavyDegree: one thread per (row, column) walks the
-//                      row's CSR list (reads of s for consecutive columns are coalesced);
-//   k_edge_pass_heavy  hub rows, one CTA each: the walk is a composition of affine maps
+//   light rows (degree <= kHeavyDegree): one thread per (row, column) walks the row's CSR
+//                      list (reads of s for consecutive columns are coalesced);
+//   hub rows           one CTA each: the walk is a composition of affine maps
 //                      u -> (1 - a) u + a s, so each thread folds a contiguous chunk of the
 //                      list into (P, S) with P = prod (1 - a), S the chunk's walk from 0, and
 //                      the chunks are then applied to u in list order.
+// The two touch disjoint rows and read only the snapshot, so one launch (k_edge_pass_all)
+// runs both: the hub CTAs first (their walks are the longest), the light rows' CTAs beside
+// them.  The batched form launches them separately over all problems.
 #include "common.cuh"
 
 namespace snect {
@@ -32,12 +35,6 @@ __device__ __forceinline__ void light_walk(const int32_t *__restrict__ ptr, cons
         u = u - st * (u - snap[(int64_t)col[s] * J2 + q]);
     }
     U2[t] = u;
-}
-
-__global__ void k_edge_pass(const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                            const float *__restrict__ cw, const float *__restrict__ snap,
-                            float *__restrict__ U2, int32_t I2, int32_t J2, float step) {
-    light_walk(ptr, col, cw, snap, U2, I2, J2, step, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 constexpr int kHeavyThreads = 512;
@@ -72,12 +69,17 @@ __device__ __forceinline__ void heavy_walk(int32_t k, const int32_t *__restrict_
 }
 
 __global__ void __launch_bounds__(kHeavyThreads)
-    k_edge_pass_heavy(const int32_t *__restrict__ rows, const int32_t *__restrict__ ptr,
-                      const int32_t *__restrict__ col, const float *__restrict__ cw,
-                      const float *__restrict__ snap, float *__restrict__ U2, int32_t J2, float step) {
+    k_edge_pass_all(const int32_t *__restrict__ rows, int32_t n_heavy, const int32_t *__restrict__ ptr,
+                    const int32_t *__restrict__ col, const float *__restrict__ cw, const float *__restrict__ snap,
+                    float *__restrict__ U2, int32_t I2, int32_t J2, float step) {
     __shared__ float sP[kHeavyThreads];
     __shared__ float sS[kHeavyThreads];
-    heavy_walk(rows[blockIdx.x], ptr, col, cw, snap, U2, J2, step, sP, sS);
+    if ((int)blockIdx.x < n_heavy) {
+        heavy_walk(rows[blockIdx.x], ptr, col, cw, snap, U2, J2, step, sP, sS);
+        return;
+    }
+    light_walk(ptr, col, cw, snap, U2, I2, J2, step,
+               (int64_t)(blockIdx.x - n_heavy) * kHeavyThreads + threadIdx.x);
 }
 
 // batched: blockIdx.y selects the problem
@@ -112,14 +114,10 @@ cudaError_t launch_edge_pass(Ctx *c) {
                                     c->stream);
     if (e != cudaSuccess) return e;
     const float step = c->cfg.lr * c->cfg.lambda_g;
-    k_edge_pass<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->csr_ptr, c->csr_col, c->csr_w, c->snap,
-                                                         c->U[1], c->d.I2, c->d.J2, step);
+    const int32_t nh = (int32_t)c->n_heavy;
+    k_edge_pass_all<<<(unsigned)(ceil_div(n, kHeavyThreads) + nh), kHeavyThreads, 0, c->stream>>>(
+        c->heavy_rows, nh, c->csr_ptr, c->csr_col, c->csr_w, c->snap, c->U[1], c->d.I2, c->d.J2, step);
     c->launches++;
-    if (c->n_heavy) {
-        k_edge_pass_heavy<<<(unsigned)c->n_heavy, kHeavyThreads, 0, c->stream>>>(
-            c->heavy_rows, c->csr_ptr, c->csr_col, c->csr_w, c->snap, c->U[1], c->d.J2, step);
-        c->launches++;
-    }
     return cudaGetLastError();
 }
 
