@@ -46,3 +46,31 @@ def test_oracle_is_not_imported_by_the_library_package():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src += open(os.path.join(dirpath, f)).read()
     assert "import oracle" not in src and "from oracle" not in src and "snect_oracle" not in src
+
+
+def test_null_handles_are_rejected_before_any_device_work():
+    """Every entry point taking a context checks it first: a null handle returns SNECT_EINVAL
+    (no CUDA call is made, so this runs without a GPU)."""
+    import ctypes
+
+    lib = snect.load(build_if_missing=True)
+    EINVAL = -1
+    d = ctypes.c_double()
+    n = ctypes.c_int64()
+    assert lib.snect_epoch(None, 1) == EINVAL
+    assert lib.snect_batches(None, 0, 1) == EINVAL
+    assert lib.snect_edge_pass(None) == EINVAL
+    assert lib.snect_loss(None, None, None, 0, None) == EINVAL
+    assert lib.snect_get_factors(None, None, None, None, None) == EINVAL
+    assert lib.snect_set_factors(None, None, None, None, None) == EINVAL
+    assert lib.snect_qr_post(None, None) == EINVAL
+    assert lib.snect_foldin(None, None, None, 1, None) == EINVAL
+    assert lib.snect_topk(None, None, 1, None, None) == EINVAL
+    assert lib.snect_set_sweep_timing(None, 1) == EINVAL
+    assert lib.snect_sweep_times(None, ctypes.byref(d), ctypes.byref(n), None) == EINVAL
+    assert lib.snect_launch_count(None) == 0
+    lib.snect_destroy(None)
+    out = ctypes.c_void_p()
+    assert lib.snect_init(ctypes.byref(out), None, None, None, 0, None, None, 0, None, None, None, None,
+                          None) == EINVAL
+    assert b"null" in lib.snect_last_error(None)
