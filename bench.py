@@ -47,8 +47,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per training entry of k_fast_sweep, FP32 core 10x10x5, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry case of the same
 # structure (bench.py --small), scaled to a launch by its entries.  To be re-measured, or set to
-# None, whenever the sweep kernel changes.
-SWEEP_DRAM_BYTES_PER_ENTRY = 12.864e6 / 675_000
+# None, whenever the sweep kernel changes.  None: the kernel has changed since the last capture
+# (12.864 MB per 675,000-entry launch, before the run vectors moved to shared memory).
+SWEEP_DRAM_BYTES_PER_ENTRY = None
 FALLBACK_BF16_TFLOPS = 1900.0
 
 

@@ -401,6 +401,9 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
     const int lane = threadIdx.x & 31;
     const int q = lane >> 1;      // this lane's component of the spread vectors
     const int par = lane & 1;     // parity of the M_k rows this lane accumulates
+    // per warp: w2 (floats 0-15) and s (16-31) of the current run, shared by the lanes
+    __shared__ __align__(16) float sWv[kFastThreads / 32][32];
+    float *wv = sWv[threadIdx.x >> 5];
     float b[J2];
     float x = 0.f;
     int ej = 0;
@@ -444,15 +447,25 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
 #pragma unroll
             for (int p = 0; p < J1; ++p) a[p] = __ldg(ua + p);
         }
-        // w2 = Gc^T a: component q in lanes 2q, 2q + 1, then gathered by every lane
+        // w2 = Gc^T a: component q in lanes 2q, 2q + 1, then read by every lane from shared
+        // memory (broadcast float4 loads)
         float wq = 0.f;
         if (q < J2) {
 #pragma unroll
             for (int p = 0; p < J1; ++p) wq = fmaf(sGc[p * J2 + q], a[p], wq);
         }
-        float w2[J2];
+        __syncwarp();  // every lane is done with the previous run's w2 and s
+        if (!par && q < J2) wv[q] = wq;
+        __syncwarp();
+        float w2[JB];
 #pragma unroll
-        for (int qq = 0; qq < J2; ++qq) w2[qq] = __shfl_sync(FULL, wq, 2 * qq);
+        for (int t4 = 0; t4 < JB / 4; ++t4) {
+            const float4 v = reinterpret_cast<const float4 *>(wv)[t4];
+            w2[4 * t4] = v.x;
+            w2[4 * t4 + 1] = v.y;
+            w2[4 * t4 + 2] = v.z;
+            w2[4 * t4 + 3] = v.w;
+        }
         // the lane's entry, if it is in this run: residual and gene-row gradient
         float r = 0.f;
         if (mine) {
@@ -483,13 +496,23 @@ __device__ __forceinline__ void warp_runs(const FastArgs &A, const Rec &e, bool 
                 mreg[t] = fmaf(ap, s_q, mreg[t]);
             }
         }
-        // patient gradient Gc s: (Gc s)[p] = sum_q Gc[p][q] s[q], summed over the
-        // even lanes (one per component q)
-        float tv[16];
-#pragma unroll
-        for (int p = 0; p < 16; ++p) tv[p] = (p < J1 && q < J2 && !par) ? sGc[p * J2 + (q < J2 ? q : 0)] * s_q : 0.f;
-        const float gcs = reduce_scatter16(tv);  // lane l: (Gc s)[l / 2]
+        // patient gradient Gc s: s goes to shared memory, and lane 2p forms
+        // (Gc s)[p] = sum_q Gc[p][q] s[q] from row p of Gc
+        if (!par && q < J2) wv[16 + q] = s_q;
+        __syncwarp();
         if (!par && q < J1) {
+            float sv[JB];
+#pragma unroll
+            for (int t4 = 0; t4 < JB / 4; ++t4) {
+                const float4 v = reinterpret_cast<const float4 *>(wv + 16)[t4];
+                sv[4 * t4] = v.x;
+                sv[4 * t4 + 1] = v.y;
+                sv[4 * t4 + 2] = v.z;
+                sv[4 * t4 + 3] = v.w;
+            }
+            float gcs = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < J2; ++qq) gcs = fmaf(sGc[q * J2 + qq], sv[qq], gcs);
             float *ga = A.gA + (int64_t)ih * A.rs1;
             atomicAdd(ga + q, gcs);
             if (CNT && lane == 0 && A.count_atomics) atomicAdd(ga + JA + k, (float)__popc(run));
