@@ -12,7 +12,8 @@
 // (Ma = E[a a^T], Mb = E[b b^T]):
 //   * patient row i:  H = sum_k n_ik Gc_k Mb Gc_k^T + n_i lambda/|Omega^{1,i}| I   (J1 x J1)
 //   * gene row j:     H = sum_k n_jk Gc_k^T Ma Gc_k + n_j lambda/|Omega^{2,j}| I   (J2 x J2)
-//     (n_ik: the row's entries of platform k in the wave; one warp per row, Cholesky)
+//     (n_ik: the row's entries of platform k in the wave; Cholesky, one thread per row for
+//     compile-time ranks up to 16, else one warp per row)
 //   * platform row k: H = n_k G_(3) (Ma kron Mb) G_(3)^T + n_k lambda/|Omega^{3,k}| I
 //   * core:           H = Cn kron Mb kron Ma + n lambda/|Omega| I, Cn = sum_k n_k c_k c_k^T,
 //     solved in the eigenbases of Ma, Mb, Cn (one-warp Jacobi, warm-started per wave).
