@@ -74,3 +74,16 @@ def test_null_handles_are_rejected_before_any_device_work():
     assert lib.snect_init(ctypes.byref(out), None, None, None, 0, None, None, 0, None, None, None, None,
                           None) == EINVAL
     assert b"null" in lib.snect_last_error(None)
+
+
+def test_without_a_gpu_the_product_path_fails_loudly():
+    """No CPU fallback: where no CUDA device can be used, building a context raises the
+    library's error instead of computing anything on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import snect_synth as S
+
+    p = S.config2(n_patients=20, n_genes=50, nnz=500, n_edges=30)
+    with pytest.raises(snect.SnectError):
+        snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr, batch=0)
