@@ -47,3 +47,25 @@ def test_single_process_aggregate_is_local():
     import bench
 
     assert bench.aggregate(10.0, 500) == (10.0, 500, 50000.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host: one JSON line with the
+    arm's metric and unit, impl "reference", its cpu_baseline and an e2e block without
+    transfers (about 15 s on one core)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "nnz-updates/s per epoch" and d["unit"] == "nnz-updates/s"
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
