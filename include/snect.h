@@ -190,12 +190,15 @@ void snect_batch_destroy(snect_batch *batch);
  *   stream     a cudaStream_t, or NULL for the default stream; the call synchronises it.
  * Its only working memory is a fixed device array inside the library (about 1 MiB, reserved
  * on every GPU that loads the library until the process exits), which bounds the query at
- * n <= 1,048,576 cells; larger queries return SNECT_EINVAL.  The first call on each device
- * looks up that array's address with the device current; make that first call before any
- * stream capture.  Calls share the array, so two calls whose work overlaps on the GPU (from
- * different streams or threads) race; serialise them.  Errors: SNECT_EINVAL for bad sizes,
- * an out-of-range cell, a non-finite value or a system that is not positive definite;
- * messages through snect_last_error(NULL). */
+ * n <= 1,048,576 cells; larger queries return SNECT_EINVAL before any work is queued.  The
+ * first call on each device does a one-time set-up with that device current (it looks up the
+ * array's address and raises one kernel's shared-memory limit so that every core up to
+ * J1*J2*J3 = 5,120 fits); make that first call before any stream capture begins.  Each call
+ * ends by copying two status words to the host and synchronising the stream.  Calls share
+ * the array, so two calls whose work overlaps on the GPU (from different streams or threads)
+ * race; serialise them.  Errors: SNECT_EINVAL for bad sizes, an out-of-range cell, a
+ * non-finite value or a system that is not positive definite; on those two device-side
+ * errors u_out holds J1 zeros.  Messages through snect_last_error(NULL). */
 int snect_foldin_static(const float *G, const float *U2, const float *U3, int32_t I2, int32_t I3,
                         int32_t J1, int32_t J2, int32_t J3, const int32_t *jk, const float *val,
                         int64_t n, float lambda, float *u_out, void *stream);
@@ -214,6 +217,28 @@ int snect_set_sweep_timing(snect_ctx *ctx, int32_t mode);
  * *n_entries (may be NULL) = training entries those launches processed.  All zero when no
  * epoch has run with timing on.  Synchronises. */
 int snect_sweep_times(snect_ctx *ctx, double *ms_total, int64_t *n_launches, int64_t *n_entries);
+
+/* Diagnostic of the fast sweep: what one wave's entry sweep accumulates before its end step.
+ * Runs the sweep kernel of wave w alone, at the current parameters, in the launch
+ * configuration an epoch uses, and copies out its accumulators: the summed data-term part of
+ * the gradient equation (Sec. 2.3.2, as Alg. 1 lines 5-8 evaluate it per entry), all terms at
+ * the wave-start parameters:
+ *   gA  any, I1*J1 floats (or NULL): per patient row i, sum over the wave's entries of i of
+ *       r (G x2 b_j x3 c_k), r = x~ - x
+ *   gB  any, I2*J2 floats (or NULL): per gene row j, sum of r (G x1 a_i x3 c_k)
+ *   M   any, I3*J1*J2 floats (or NULL): per platform k, M_k[p][q] = sum over the wave's entries
+ *       of platform k of r a_p b_q; the core's data-term gradient is sum_k M_k o c_k and
+ *       platform row k's is G_(3) vec(M_k)
+ *   nA  any, I1*I3 floats (or NULL): the wave's entries per (patient, platform); nB likewise
+ *       I2*I3 per (gene, platform)
+ *   first, count  (host, may be NULL): the wave's entries are positions [first, first+count)
+ *       of the visit order given at snect_init
+ * The factors and core are not changed, and the accumulators are cleared again afterwards;
+ * the fast mode's curvature state (platform systems, eigenbases) is refreshed as the wave's
+ * own sweep refreshes it.  Fast mode only.  Synchronises.  Errors: SNECT_EINVAL (mode, wave
+ * index), SNECT_ETIMEDOUT (a tensor-core wait of the BF16 sweep gave up), SNECT_ECUDA. */
+int snect_wave_grads(snect_ctx *ctx, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB,
+                     int64_t *first, int64_t *count);
 
 /* Number of kernel launches the context has issued so far (for launch accounting). */
 int64_t snect_launch_count(const snect_ctx *ctx);

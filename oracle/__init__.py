@@ -144,6 +144,24 @@ def batch_step(I, params: Params, lam, lr, idx, val, start, length, cnt=None, n_
                           ctypes.c_int64(n_omega))
 
 
+def data_grad_sums(I, params: Params, idx, val, start, length):
+    """The data-term part of the gradient equation (Sec. 2.3.2) summed over entries
+    [start, start+length) of the visit order, all at the same parameters: dict of gA (I1 x J1),
+    gB (I2 x J2), gC (I3 x J3), gG (J1 x J2 x J3), and the range's entries per (patient,
+    platform) nA (I1 x I3) and per (gene, platform) nB (I2 x I3)."""
+    lib = _load()
+    I, Ip = _i32(I)
+    J, Jp = _i32(params.J)
+    idx, ip = _i32(idx)
+    val, vp = _f64(val)
+    out = dict(gA=np.empty((I[0], J[0])), gB=np.empty((I[1], J[1])), gC=np.empty((I[2], J[2])),
+               gG=np.empty(tuple(J)), nA=np.empty((I[0], I[2])), nB=np.empty((I[1], I[2])))
+    lib.oracle_data_grad_sums(Ip, Jp, params.G.ctypes.data_as(_f64p), *(u.ctypes.data_as(_f64p) for u in params.U),
+                              ip, vp, ctypes.c_int64(start), ctypes.c_int64(length),
+                              *(out[k].ctypes.data_as(_f64p) for k in ("gA", "gB", "gC", "gG", "nA", "nB")))
+    return out
+
+
 def edge_pass(I2, params: Params, lam_g, lr, edges, w):
     """Network-term pass over the gene factor (Alg. 1 line 10, row-owned reading)."""
     lib = _load()

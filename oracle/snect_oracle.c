@@ -208,6 +208,46 @@ void oracle_batch_step(const int32_t *I, const int32_t *J, double lambda, double
     free(gG);
 }
 
+/* The data-term part of the gradient equation (Sec. 2.3.2) summed over the entries
+ * [start, start+len) of the visit order, every term at the same parameters (as Alg. 1 lines
+ * 5-8 evaluate one entry, without the L2 terms): with r = x~ - x per entry,
+ *   gA[i] = sum_{e: i_e = i} r (G x2 b x3 c)     I1 x J1
+ *   gB[j] = sum_{e: j_e = j} r (G x1 a x3 c)     I2 x J2
+ *   gC[k] = sum_{e: k_e = k} r (G x1 a x2 b)     I3 x J3
+ *   gG    = sum_e r a o b o c                    J1 x J2 x J3
+ * i.e. the gradient of 1/2 sum_e (x_e - x~_e)^2 over the range.  nA (I1 x I3) and nB
+ * (I2 x I3) count the range's entries per (patient, platform) and (gene, platform).  Every
+ * output is overwritten; sums run in entry order. */
+void oracle_data_grad_sums(const int32_t *I, const int32_t *J, const double *G, const double *U1,
+                           const double *U2, const double *U3, const int32_t *idx, const double *val,
+                           int64_t start, int64_t len, double *gA, double *gB, double *gC, double *gG,
+                           double *nA, double *nB) {
+    const double *U[3] = {U1, U2, U3};
+    double *out[3] = {gA, gB, gC};
+    int64_t PI = (int64_t)J[0] * J[1] * J[2];
+    for (int md = 0; md < 3; ++md)
+        for (int64_t s = 0; s < (int64_t)I[md] * J[md]; ++s) out[md][s] = 0.0;
+    for (int64_t s = 0; s < PI; ++s) gG[s] = 0.0;
+    for (int64_t s = 0; s < (int64_t)I[0] * I[2]; ++s) nA[s] = 0.0;
+    for (int64_t s = 0; s < (int64_t)I[1] * I[2]; ++s) nB[s] = 0.0;
+    double *eG = (double *)malloc(sizeof(double) * PI);
+    double ga[64], gb[64], gc[64];
+    for (int64_t e = start; e < start + len; ++e) {
+        const int32_t *t = idx + 3 * e;
+        entry_grads(J, G, U[0] + (int64_t)t[0] * J[0], U[1] + (int64_t)t[1] * J[1],
+                    U[2] + (int64_t)t[2] * J[2], val[e], 0.0, 0.0, 0.0, 0.0, ga, gb, gc, eG);
+        const double *g[3] = {ga, gb, gc};
+        for (int md = 0; md < 3; ++md) {
+            double *dst = out[md] + (int64_t)t[md] * J[md];
+            for (int q = 0; q < J[md]; ++q) dst[q] += g[md][q];
+        }
+        for (int64_t s = 0; s < PI; ++s) gG[s] += eG[s];
+        nA[(int64_t)t[0] * I[2] + t[2]] += 1.0;
+        nB[(int64_t)t[1] * I[2] + t[2]] += 1.0;
+    }
+    free(eG);
+}
+
 /* Network term pass (Alg. 1 line 10, reading R4).  The oracle builds its own sorted
  * adjacency from the undirected edge list. */
 void oracle_edge_pass(int32_t I2, int32_t J2, double lambda_g, double lr, double *U2,

@@ -49,6 +49,7 @@ EXPORTS = (
     "snect_serve_stop",
     "snect_set_sweep_timing",
     "snect_sweep_times",
+    "snect_wave_grads",
     "snect_launch_count",
     "snect_last_error",
     "snect_destroy",
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = False):
         "snect_set_sweep_timing": (ctypes.c_int, [P, ctypes.c_int32]),
         "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64)]),
+        "snect_wave_grads": (ctypes.c_int, [P, i64, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
         "snect_last_error": (ctypes.c_char_p, [P]),
         "snect_destroy": (None, [P]),
@@ -282,6 +285,21 @@ class Snect:
         e = ctypes.c_int64()
         self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(e)))
         return ms.value, n.value, e.value
+
+    def wave_grads(self, w: int):
+        """One wave's entry sweep alone at the current parameters (snect_wave_grads): dict of
+        gA (I1 x J1), gB (I2 x J2), M (I3 x J1 x J2), nA (I1 x I3), nB (I2 x I3) and the wave's
+        entry range (first, count) in the visit order."""
+        I, J = self.I, self.J
+        out = dict(gA=np.empty((I[0], J[0]), np.float32), gB=np.empty((I[1], J[1]), np.float32),
+                   M=np.empty((I[2], J[0], J[1]), np.float32), nA=np.empty((I[0], I[2]), np.float32),
+                   nB=np.empty((I[1], I[2]), np.float32))
+        first, count = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.snect_wave_grads(self._h, int(w), *(out[k].ctypes.data for k in
+                                                                  ("gA", "gB", "M", "nA", "nB")),
+                                               ctypes.byref(first), ctypes.byref(count)))
+        out["first"], out["count"] = first.value, count.value
+        return out
 
     def serve(self, n_slots: int = 8, mem_budget_bytes: int = 1 << 30, max_cells: int = 75_000):
         """Starts a continuous-batching fold-in + top-k server on this context's factors."""

@@ -539,6 +539,19 @@ int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches, int64
     return SNECT_OK;
 }
 
+int snect_wave_grads(snect_ctx *h, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB,
+                     int64_t *first, int64_t *count) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (c->cfg.batch > 0) return fail(c, SNECT_EINVAL, "snect_wave_grads needs fast mode");
+    if (w < 0 || w >= c->n_waves) return fail(c, SNECT_EINVAL, "wave index outside [0, n_waves)");
+    const int rc = fast_wave_grads(c, w, gA, gB, M, nA, nB);
+    if (rc) return rc;
+    if (first) *first = w * c->wave;
+    if (count) *count = c->wave_len[w];
+    return SNECT_OK;
+}
+
 int64_t snect_launch_count(const snect_ctx *h) {
     const Ctx *c = reinterpret_cast<const Ctx *>(h);
     return c ? c->launches.load() : 0;

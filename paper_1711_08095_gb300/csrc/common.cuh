@@ -173,6 +173,8 @@ int prep_det_groups(Ctx *c);
 int prep_fast_tiles(Ctx *c);       // prep.cu: groups each wave's entries by platform, tiles
 int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of the fast sweep
 int enqueue_fast_epoch(Ctx *c);
+// the entry sweep of one wave alone, its accumulators copied out (snect_wave_grads)
+int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB);
 void free_fast(Ctx *c);
 constexpr int kFastTile = 256;     // entries per tile (one per thread of the wave kernel)
 constexpr int64_t kMinWave = 4096;      // default wave: nnz/16 clamped to [kMinWave, kMaxWave]

@@ -9,11 +9,14 @@
 // reserved on every GPU that loads the library until the process exits.
 //
 // Host code cannot use the array's name as a device address (in host code it names a
-// host-side stand-in), so the first call on each device looks the address up with
-// cudaGetSymbolAddress, with that device current, and caches it; that first call should come
-// before any stream capture.  Every call shares the array and leaves its contents behind:
-// the status words are cleared at the start of each call and every partial is overwritten
-// before it is read.  Two calls whose work overlaps on the GPU race on the array.
+// host-side stand-in), so the first call on each device does a one-time set-up with that
+// device current: it looks the address up with cudaGetSymbolAddress and caches it, and it
+// raises the partial-sum kernel's dynamic shared-memory limit so that every core the entry
+// point accepts (J1*J2*J3 <= 5,120) fits beside the kernel's static tiles.  That first call
+// should come before any stream capture.  Every call shares the array and leaves its
+// contents behind: the status words are cleared at the start of each call and every partial
+// is overwritten before it is read.  Two calls whose work overlaps on the GPU race on the
+// array.
 //
 // The arithmetic is that of snect_foldin: w_jk = G x2 u2_j x3 u3_k (computed here per cell,
 // in the same order as snect_foldin's table), a fixed-order FP32 Gram per CTA, the partials
@@ -41,7 +44,7 @@ constexpr int64_t kSScratchFloats = kSMaxParts * kSPartStride + kSStatusWords;  
 static __device__ __align__(256) float g_foldin_scratch[kSScratchFloats];
 
 std::mutex g_addr_mu;
-float *g_addr[256] = {};  // per device: device address of g_foldin_scratch
+float *g_addr[256] = {};  // per device: device address of g_foldin_scratch (null: not set up)
 
 __global__ void k_static_check(const int32_t *__restrict__ jk, const float *__restrict__ val, int64_t n,
                                int32_t I2, int32_t I3, int32_t *status) {
@@ -124,6 +127,10 @@ __global__ void __launch_bounds__(kSThreads)
     __shared__ double M[kMaxRank * kMaxRank];
     __shared__ double rhs[kMaxRank];
     const int nG = J1 * J1;
+    if (status[0]) {  // a bad cell was flagged: the output row is zero, not a partial solution
+        if (threadIdx.x < J1) u_out[threadIdx.x] = 0.f;
+        return;
+    }
     for (int s = threadIdx.x; s < nG + J1; s += blockDim.x) {
         float a = 0.f;
         for (int t = 0; t < n_part; ++t) a += part[(int64_t)t * (nG + J1) + s];
@@ -176,6 +183,13 @@ int scratch_address(float **out) {
         if (e != cudaSuccess || !p)
             return fail(nullptr, SNECT_ECUDA,
                         std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        // the core (up to kMaxCore floats) is the kernel's dynamic shared memory, beside about
+        // 33 KB of static tiles: above the 48 KB default once J1*J2*J3 > 3,840
+        e = cudaFuncSetAttribute(k_static_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * kMaxCore));
+        if (e != cudaSuccess)
+            return fail(nullptr, SNECT_ECUDA,
+                        std::string("cudaFuncSetAttribute(k_static_partial): ") + cudaGetErrorString(e));
         g_addr[dev] = static_cast<float *>(p);
     }
     *out = g_addr[dev];

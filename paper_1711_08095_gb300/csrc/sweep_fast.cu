@@ -2259,6 +2259,52 @@ int enqueue_fast_epoch(Ctx *c) {
     return SNECT_OK;
 }
 
+int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB) {
+    const Dims &d = c->d;
+    if (w < 0 || w >= c->n_waves) return fail(c, SNECT_EINVAL, "wave index outside [0, n_waves)");
+    const size_t rs1 = (size_t)row_stride(d.J1, d.I3), rs2 = (size_t)row_stride(d.J2, d.I3);
+    const size_t na = (size_t)d.I1 * rs1, nb = (size_t)d.I2 * rs2, nm = (size_t)d.I3 * d.J1 * d.J2;
+    auto clear = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(c->gacc[0], 0, sizeof(float) * na, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->gacc[1], 0, sizeof(float) * nb, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, sizeof(float) * nm, c->stream);
+        return e;
+    };
+    SNECT_CUDA(c, clear());
+    SNECT_CUDA(c, cudaMemsetAsync(c->tile_ctr + w, 0, sizeof(int32_t), c->stream));
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag + 3, 0, sizeof(int32_t), c->stream));
+    SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, run_sweep, c, w));
+    const int JA = (d.J1 + 3) & ~3, JB = (d.J2 + 3) & ~3;
+    const cudaMemcpyKind kd = cudaMemcpyDefault;
+    if (gA)
+        SNECT_CUDA(c, cudaMemcpy2DAsync(gA, sizeof(float) * d.J1, c->gacc[0], sizeof(float) * rs1,
+                                        sizeof(float) * d.J1, d.I1, kd, c->stream));
+    if (gB)
+        SNECT_CUDA(c, cudaMemcpy2DAsync(gB, sizeof(float) * d.J2, c->gacc[1], sizeof(float) * rs2,
+                                        sizeof(float) * d.J2, d.I2, kd, c->stream));
+    if (M) SNECT_CUDA(c, cudaMemcpyAsync(M, c->macc, sizeof(float) * nm, kd, c->stream));
+    if (c->wcnt) {  // the set-up table of the wave's entries per (row, platform)
+        const float *t = c->wcnt + (size_t)w * ((size_t)d.I1 + d.I2) * d.I3;
+        if (nA) SNECT_CUDA(c, cudaMemcpyAsync(nA, t, sizeof(float) * d.I1 * d.I3, kd, c->stream));
+        if (nB)
+            SNECT_CUDA(c, cudaMemcpyAsync(nB, t + (size_t)d.I1 * d.I3, sizeof(float) * (size_t)d.I2 * d.I3, kd,
+                                          c->stream));
+    } else {  // counted by the sweep's atomics, after each row's gradient
+        if (nA)
+            SNECT_CUDA(c, cudaMemcpy2DAsync(nA, sizeof(float) * d.I3, c->gacc[0] + JA, sizeof(float) * rs1,
+                                            sizeof(float) * d.I3, d.I1, kd, c->stream));
+        if (nB)
+            SNECT_CUDA(c, cudaMemcpy2DAsync(nB, sizeof(float) * d.I3, c->gacc[1] + JB, sizeof(float) * rs2,
+                                            sizeof(float) * d.I3, d.I2, kd, c->stream));
+    }
+    int32_t tc_err = 0;
+    SNECT_CUDA(c, cudaMemcpyAsync(&tc_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, clear());
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a tensor-core completion wait timed out in the sweep");
+    return SNECT_OK;
+}
+
 void free_fast(Ctx *c) {
     auto f = [](auto *&p) {
         if (p) cudaFree(p);

@@ -1,0 +1,110 @@
+"""The fast sweep checked element by element: what one wave's sweep accumulates.
+
+Inside a fast-mode wave every entry's gradient is evaluated at the wave-start parameters
+and summed (the gradient equation of Sec. 2.3.2, data term; each row's L2 term is added once
+at the wave end).  So what the sweep kernel accumulates before the wave's end step is a
+plain, order-free quantity: per patient row, per gene row and per platform the summed
+data-term gradients, and per platform M_k = sum r a b^T, from which the core's data-term
+gradient is sum_k M_k o c_k and platform row k's is G_(3) vec(M_k).  The FP64 oracle sums
+the same per-entry gradients (oracle.data_grad_sums, pinned by finite differences), so every
+value is compared: |gpu - oracle| <= tol (|oracle| + rms), tol 1e-5 for the FP32 sweeps.  The
+counts of each row's entries per platform in the wave (the row steps' weights) are integers
+and must match exactly.
+
+Every compiled path of the sweep is driven: the statically partitioned per-run sweep
+(10x10x5, 16x16x5), its tile-claiming variant (16x16x5 with 20 platforms, every platform's
+Gc beyond the shared-memory budget), the variant that counts with atomics (64 platforms,
+1,024-entry waves), the per-entry sweep (32x32x5, and runtime ranks 3x7x4), and the BF16
+tensor-core sweep (tolerance 3e-2: its operands are rounded to BF16).  Each at the initial
+parameters and again after two epochs, on the first, a middle and the last (ragged) wave.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import snect_synth as S
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL_BF16 = 3e-2
+
+
+def close(got, want, tol):
+    got = np.asarray(got, np.float64)
+    rms = float(np.sqrt(np.mean(want * want))) if want.size else 0.0
+    err = np.abs(got - want) / (np.abs(want) + rms + 1e-30)
+    return float(err.max()) if err.size else 0.0
+
+
+def check_waves(p, tol, precision=0, wave=0, epochs_between=2):
+    import paper_1711_08095_gb300 as snect
+
+    c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                    batch=0, wave=wave, precision=precision)
+    report = []
+    for stage in range(2):
+        if stage:
+            c.epoch(epochs_between)
+        G, U = c.get_factors()
+        P = oracle.Params(G, U)
+        first = c.wave_grads(0)
+        n_waves = -(-p.nnz // first["count"]) if first["count"] else 0
+        n_waves += n_waves & 1
+        for w in sorted({0, n_waves // 2, n_waves - 1}):
+            got = c.wave_grads(w)
+            want = oracle.data_grad_sums(p.I, P, p.idx, p.val, got["first"], got["count"])
+            assert got["count"] > 0 and got["first"] + got["count"] <= p.nnz
+            M = got["M"].astype(np.float64)
+            gG = np.einsum("kpq,kr->pqr", M, U[2].astype(np.float64))
+            gC = np.einsum("pqr,kpq->kr", G.astype(np.float64), M)
+            errs = {"gA": close(got["gA"], want["gA"], tol), "gB": close(got["gB"], want["gB"], tol),
+                    "gG": close(gG, want["gG"], tol), "gC": close(gC, want["gC"], tol)}
+            report.append((stage, w, errs))
+            for key, e in errs.items():
+                assert e <= tol, (p.J, stage, w, key, e)
+            assert np.array_equal(got["nA"], want["nA"].astype(np.float32)), (stage, w, "nA")
+            assert np.array_equal(got["nB"], want["nB"].astype(np.float32)), (stage, w, "nB")
+    # the diagnostic leaves the factors alone
+    G2, U2 = c.get_factors()
+    assert np.array_equal(G2, G) and all(np.array_equal(a, b) for a, b in zip(U2, U))
+    c.close()
+    print("wave-gradient parity", p.J, p.I, ["%d/%d %s" % (s, w, {k: "%.1e" % v for k, v in e.items()})
+                                              for s, w, e in report])
+
+
+def test_static_partition_sweep_10x10x5(gpu_lib):
+    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000)
+    check_waves(p, TOL32)
+
+
+def test_static_partition_sweep_16x16x5(gpu_lib):
+    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=(16, 16, 5))
+    check_waves(p, TOL32)
+
+
+def test_tile_claiming_sweep_many_platforms(gpu_lib):
+    p = S.config2(n_patients=120, n_genes=3000, n_platforms=20, nnz=200_000, n_edges=5_000, J_true=(5, 5, 2),
+                  J_fit=(16, 16, 5))
+    check_waves(p, TOL32)
+
+
+def test_count_atomics_sweep_small_waves(gpu_lib):
+    """With 1,024-entry waves on 64 platforms the per-wave count table would outgrow the
+    entries, so the sweep counts each row's entries per platform with atomics."""
+    p = S.config2(n_patients=120, n_genes=3000, n_platforms=64, nnz=100_000, n_edges=5_000, J_true=(5, 5, 2),
+                  J_fit=(5, 5, 2))
+    check_waves(p, TOL32, wave=1024)
+
+
+@pytest.mark.parametrize("J", [(32, 32, 5), (3, 7, 4)])
+def test_per_entry_sweep(J, gpu_lib):
+    p = S.config2(n_patients=100, n_genes=3000, nnz=100_000, n_edges=5_000, J_fit=J)
+    check_waves(p, TOL32)
+
+
+def test_bf16_tensor_core_sweep(gpu_lib):
+    import paper_1711_08095_gb300 as snect
+
+    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=(16, 16, 5))
+    check_waves(p, TOL_BF16, precision=snect.BF16)

@@ -193,6 +193,42 @@ def test_batch_step_sums_entry_gradients_at_batch_start(tiny):
         assert np.allclose(x - b, total[a], rtol=1e-12, atol=1e-15), a
 
 
+def test_data_grad_sums_are_the_gradient_of_the_range_data_term(tiny):
+    """The summed data-term gradients of a range of entries (the quantity a fast-mode wave
+    accumulates) are the gradient of 1/2 sum_range (x - x~)^2 w.r.t. every row and the core:
+    central differences of the objective, with the platform rows' and the core's sums
+    included; the per-(row, platform) entry counts equal a brute-force count."""
+    P0 = oracle.Params(tiny.G0, tiny.U0)
+    lo, n = 3, 11
+    idx, val = tiny.idx[lo:lo + n], tiny.val[lo:lo + n].astype(np.float64)
+    got = oracle.data_grad_sums(tiny.I, P0, tiny.idx, tiny.val, lo, n)
+
+    def f(arrs):
+        r = val - xhat_kron(arrs[0], arrs[1:], idx)
+        return 0.5 * float(r @ r)
+
+    grads = fd_grad(f, [P0.G.copy()] + [u.copy() for u in P0.U])
+    for key, g in zip(("gG", "gA", "gB", "gC"), grads):
+        assert rel_err(got[key], g) < 1e-6, key
+    nA = np.zeros((tiny.I[0], tiny.I[2]))
+    nB = np.zeros((tiny.I[1], tiny.I[2]))
+    for i, j, k in idx:
+        nA[i, k] += 1
+        nB[j, k] += 1
+    assert np.array_equal(got["nA"], nA) and np.array_equal(got["nB"], nB)
+
+
+def test_data_grad_sums_match_a_batch_step_without_l2(tiny):
+    """With lambda = 0 one mini-batch step moves each touched row by -lr times its summed
+    data-term gradient (reading R2), which ties the two oracle routes together."""
+    P0 = oracle.Params(tiny.G0, tiny.U0)
+    P1 = P0.copy()
+    oracle.batch_step(tiny.I, P1, 0.0, tiny.lr, tiny.idx, tiny.val, 2, 9)
+    got = oracle.data_grad_sums(tiny.I, P0, tiny.idx, tiny.val, 2, 9)
+    for key, b, a in zip(("gG", "gA", "gB", "gC"), [P0.G] + P0.U, [P1.G] + P1.U):
+        assert np.allclose((b - a) / tiny.lr, got[key], rtol=1e-10, atol=1e-13), key
+
+
 # ---------------------------------------------------------------------------------------
 # network pass (Alg. 1 line 10)
 def test_edge_pass_on_a_matching_is_a_gradient_step_on_the_graph_term():
