@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-jobs", type=int, default=5)
+    ap.add_argument("--breakdown-epochs", type=int, default=5,
+                    help="epochs with CUDA events around every kernel after the timed region")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the lock-free (paper-faithful) ablation")
     ap.add_argument("--small", action="store_true",
                     help="a smaller problem of the same shape, 12M entries (for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
@@ -208,6 +211,31 @@ def cpu_baseline(p, budget_s=15.0):
     return out
 
 
+def kernel_breakdown(ctx, nnz, epochs):
+    """Per-kernel device time of the epoch, live: `epochs` more epochs with CUDA events around
+    every kernel launch (timing mode 2), read back after each epoch; ms per epoch and per
+    launch of the entry sweeps, the wave ends and the network pass.  Not part of `value`."""
+    ctx.set_sweep_timing(2)
+    ctx.epoch(1)  # captures the graph with the event nodes
+    tot = {"sweep": [0.0, 0], "wave_end": [0.0, 0], "network_pass": [0.0, 0]}
+    for _ in range(epochs):
+        ctx.epoch(1)
+        for k, (ms, n) in ctx.kernel_times().items():
+            tot[k][0] += ms
+            tot[k][1] += n
+    ctx.set_sweep_timing(0)
+    out = {"epochs": epochs}
+    for k, (ms, n) in tot.items():
+        out[k] = {"ms_per_epoch": ms / max(epochs, 1), "launches_per_epoch": n / max(epochs, 1),
+                  "ms_per_launch": ms / n if n else None}
+    out["sweep_ms_total"], out["sweep_launches"] = tot["sweep"][0], tot["sweep"][1]
+    out["sweep_launches_per_epoch"] = tot["sweep"][1] / max(epochs, 1)
+    out["note"] = ("kernel durations between events recorded on the stream right before and after each launch; "
+                   "the event nodes themselves add a few microseconds between kernels, so these epochs are "
+                   "not timed for `value`")
+    return out
+
+
 def serving(args, snect):
     """Serving form: the paper-scale planted model at core 16 x 16 x 5 frozen on the device; a
     Poisson stream of new-patient queries (5,000-75,000 observed cells, log-uniform) folded in
@@ -301,27 +329,151 @@ def precision_form(p, snect, epochs=10):
     return out
 
 
+def max_principal_angle(X, Y):
+    """Largest principal angle (degrees) between the column spaces of X and Y (None when
+    either holds a non-finite value)."""
+    if not (np.isfinite(X).all() and np.isfinite(Y).all()):
+        return None
+    qx, _ = np.linalg.qr(np.asarray(X, np.float64))
+    qy, _ = np.linalg.qr(np.asarray(Y, np.float64))
+    sv = np.clip(np.linalg.svd(qx.T @ qy, compute_uv=False), -1.0, 1.0)
+    return float(np.degrees(np.arccos(sv.min())))
+
+
+def wave_grad_error(c, p, P0):
+    """Max over the elements of one wave's accumulated data-term gradients (patient rows, gene
+    rows, platform rows, core) of |gpu - oracle| / (|oracle| + rms), at the parameters P0."""
+    import oracle
+
+    got = c.wave_grads(0)
+    want = oracle.data_grad_sums(p.I, P0, p.idx, p.val, got["first"], got["count"])
+    M = got["M"].astype(np.float64)
+    derived = {"gA": got["gA"], "gB": got["gB"], "gG": np.einsum("kpq,kr->pqr", M, P0.U[2]),
+               "gC": np.einsum("pqr,kpq->kr", P0.G, M)}
+    out = {}
+    for k, v in derived.items():
+        w = want[k]
+        rms = float(np.sqrt(np.mean(w * w)))
+        out[k] = float((np.abs(np.asarray(v, np.float64) - w) / (np.abs(w) + rms + 1e-30)).max())
+    return out
+
+
 def precision_config1(snect):
     """The precision form's own workload: the parity tensor (200 x 300 x 4) refit at core
-    16x16x5 and 32x32x5, FP32 and BF16 fast mode from the same start for 20 epochs; the
-    objective and test RMSE of each, beside the FP64 oracle's sequential run where it stays
-    finite (at these over-parameterised ranks it can leave the finite range at lr 0.01)."""
+    16x16x5 and 32x32x5, FP32 and BF16 fast mode from the same start for 20 epochs.  Error
+    against the FP64 oracle, per result:
+      * the contraction: one wave's accumulated data-term gradients (patient rows, gene rows,
+        platform rows, core) at the initial parameters, against the oracle's FP64 sums of the
+        same per-entry gradients (element-wise max of |gpu - oracle| / (|oracle| + rms));
+      * the fit: objective, test RMSE and the largest principal angle between each of U1's and
+        U2's column spaces and the oracle's, after 20 epochs, against the oracle's deterministic
+        fixed-order mini-batch run (batches of 1,024, the pinned reading R2).  The oracle's
+        sequential per-entry run at lr 0.01 is reported beside it; at these over-parameterised
+        ranks it can leave the finite range."""
+    import oracle
     import snect_synth as S
 
     out = {}
     for J in ((16, 16, 5), (32, 32, 5)):
         p = S.config1(J_fit=J)
-        row = {}
+        P0 = oracle.Params(p.G0, p.U0)
+        Pm = P0.copy()
+        for _ in range(p.epochs):
+            oracle.epoch(p.I, Pm, p.lam, p.lam_g, p.lr, 1024, p.idx, p.val, p.edges, p.w)
+        lm = oracle.loss(p.I, Pm, p.lam, p.lam_g, p.idx, p.val, p.edges, p.w)["total"]
+        rm = oracle.rmse(Pm, p.test_idx, p.test_val)
+        fin = lambda v: v if np.isfinite(v) else "non-finite"
+        Ps = P0.copy()
+        for _ in range(p.epochs):
+            oracle.sgd_epoch(p.I, Ps, p.lam, p.lam_g, p.lr, p.idx, p.val, p.edges, p.w)
+        rs = oracle.rmse(Ps, p.test_idx, p.test_val)
+        row = {"oracle_minibatch": {"rmse_test": fin(rm), "objective": fin(lm)},
+               "oracle_sequential": {"rmse_test": rs if np.isfinite(rs) else "non-finite"}}
         for name, prec in (("fp32", snect.FP32), ("bf16", snect.BF16)):
             c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
                             batch=0, precision=prec)
+            werr = wave_grad_error(c, p, P0)
             c.epoch(p.epochs)
             l = c.loss(p.test_idx, p.test_val)
+            G, U = c.get_factors()
             c.close()
-            row[name] = {"rmse_test": l["rmse_test"], "objective": l["total"]}
+            row[name] = {"rmse_test": l["rmse_test"], "objective": l["total"],
+                         "wave_gradient_error_vs_oracle": werr,
+                         "rmse_test_relative_to_oracle_minibatch": fin(l["rmse_test"] / rm - 1.0),
+                         "objective_relative_to_oracle_minibatch": fin(l["total"] / lm - 1.0),
+                         "max_principal_angle_deg_vs_oracle_minibatch": {
+                             "U1": max_principal_angle(U[0], Pm.U[0]), "U2": max_principal_angle(U[1], Pm.U[1])}}
         row["bf16_rmse_relative_to_fp32"] = row["bf16"]["rmse_test"] / row["fp32"]["rmse_test"] - 1.0
         out["%dx%dx%d" % J] = row
     return out
+
+
+def lockfree_ablation(snect):
+    """The lock-free form of Alg. 1 as the paper states it (Sec. 2.3.3: entries and network
+    edges interleaved in random order, rows updated without locks, the core stepped by one
+    worker with step lr * P) at several worker counts P, against the oracle's run of the same
+    order with one worker and beside the wave-synchronous fast mode, all from the same start:
+    test RMSE after the epochs (NaN: the run left the finite range)."""
+    import oracle
+    import snect_synth as S
+    import torch
+
+    out = {}
+    for name, p, E, Ps in (("parity 200x300x4, core 5x5x2", S.config1(), 20, (1, 8, 64, 512, 4096)),
+                           ("paper structure 150x15000x5, 200k entries, core 10x10x5",
+                            S.config2(n_patients=150, nnz=200_000, n_edges=10_000), 10, (8, 64, 512, 4096))):
+        order = S.interleaved_order(p.nnz, p.edges.shape[0])
+        P0 = oracle.Params(p.G0, p.U0)
+        for _ in range(E):
+            oracle.hogwild_epoch(p.I, P0, p.lam, p.lam_g, p.lr, p.idx, p.val, p.edges, p.w, order)
+        row = {"epochs": E, "oracle_one_worker_rmse_test": oracle.rmse(P0, p.test_idx, p.test_val)}
+        for P in Ps:
+            c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                            batch=1024)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.hogwild_epoch(order, P=P, n=E)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            r = c.loss(p.test_idx, p.test_val)["rmse_test"]
+            c.close()
+            row["P=%d" % P] = {"rmse_test": r if np.isfinite(r) else "non-finite", "seconds": dt,
+                               "core_step": p.lr * P}
+        f = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr, batch=0)
+        f.epoch(E)
+        row["fast_mode_rmse_test"] = f.loss(p.test_idx, p.test_val)["rmse_test"]
+        f.close()
+        out[name] = row
+    return out
+
+
+def analyses(snect, served_u):
+    """Downstream analyses on the paper-scale planted serving model (core 16x16x5): the
+    personalised subtype matrix and its norms (Sec. 3.3) for a batch of served profiles in one
+    call, and k-means stratification of the 4,500 patient rows into 13 clusters (Sec. 3.1.1)
+    from 13 seeded random rows; wall time of each call through the C ABI."""
+    import snect_synth as S
+
+    m = S.serving_model()
+    I = tuple(u.shape[0] for u in m.U)
+    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
+    c = snect.Snect(I, m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32), np.zeros(0, np.float32),
+                    m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
+    u = np.ascontiguousarray(served_u if served_u is not None else m.U[0], np.float32)
+    c.subtype(u[:16])  # warm-up
+    t0 = time.perf_counter()
+    c.subtype(u)
+    ts = time.perf_counter() - t0
+    rng = np.random.default_rng(13)
+    init = m.U[0][rng.choice(I[0], 13, replace=False)].astype(np.float64)
+    c.kmeans(init, 5)
+    t0 = time.perf_counter()
+    a, _, upd, inertia = c.kmeans(init, 100)
+    tk = time.perf_counter() - t0
+    c.close()
+    return {"subtype": {"profiles": int(u.shape[0]), "ms": ts * 1e3},
+            "kmeans": {"rows": I[0], "k": 13, "centroid_updates": upd, "ms": tk * 1e3,
+                       "cluster_sizes": np.bincount(a, minlength=13).tolist()}}
 
 
 def parity_config(snect):
@@ -506,8 +658,9 @@ def main():
     ms, _, value = aggregate(ev0.elapsed_time(ev1), p.nnz * args.steps, dist, dev)
     if dist:
         dist.barrier()
-    sweep_ms, sweep_n, sweep_entries = ctx.sweep_times()  # the timed sweep of the last timed epoch
+    mid_ms, mid_n, mid_entries = ctx.sweep_times()  # the timed sweep of the last timed epoch
     loss = ctx.loss(t(p.test_idx), t(p.test_val))
+    breakdown = kernel_breakdown(ctx, p.nnz, args.breakdown_epochs)
     ctx.close()
     del ctx
     torch.cuda.synchronize()
@@ -535,11 +688,15 @@ def main():
 
     pk, pk_kind = peaks()
     # roofline of the sweep kernel: algorithmic bytes per entry = 16 (entry record) +
-    # 4*(J1+J2+J3) gathered rows + 4*(J1+J2+J3) row write-back, per launch = one wave
+    # 4*(J1+J2+J3) gathered rows + 4*(J1+J2+J3) row write-back, per launch = one wave.  The
+    # launch duration is the average over every sweep launch of the breakdown epochs (CUDA
+    # events around each launch); the middle launch of the timed region is the cross-check.
     J = p.J
     bytes_per_nnz = 16 + 8 * sum(J)
-    per_launch = sweep_entries / max(sweep_n, 1)  # entries of one timed launch (one wave)
-    achieved = (bytes_per_nnz * per_launch) / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
+    sw_ms, sw_n = breakdown["sweep_ms_total"], breakdown["sweep_launches"]
+    per_launch = p.nnz / max(breakdown["sweep_launches_per_epoch"], 1)  # entries of one launch (one wave)
+    achieved = (bytes_per_nnz * per_launch) / (sw_ms / sw_n / 1e3) / 1e9 if sw_n else None
+    achieved_mid = ((bytes_per_nnz * mid_entries / mid_n) / (mid_ms / mid_n / 1e3) / 1e9) if mid_n else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -561,9 +718,13 @@ def main():
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 12M-entry case scaled by entries)",
                      "kernel": "%s (one launch per wave)" % ("k_fast_sweep_tc" if bf16 else "k_fast_sweep"),
                      "bytes_per_unit": bytes_per_nnz, "units_per_launch": per_launch,
-                     "peak_kind": pk_kind,
-                     "timing": "CUDA events on the library's stream around the middle sweep launch of every "
-                               "epoch; the last timed epoch's: %d launch, %.4f ms" % (sweep_n, sweep_ms)},
+                     "peak_kind": pk_kind, "avg_launch_ms": (sw_ms / sw_n) if sw_n else None,
+                     "timing": "CUDA events on the library's stream around every sweep launch of %d epochs "
+                               "run right after the timed region (%d launches; the timed region itself carries "
+                               "events only around the middle launch of each epoch, whose last duration gives "
+                               "achieved_middle_launch)" % (args.breakdown_epochs, sw_n),
+                     "achieved_middle_launch": achieved_mid},
+        "kernel_breakdown": breakdown,
         "clocks": clk.summary(),
         "quality": quality(loss, job_loss, job_epochs, args.warmup + args.steps, args.small or bf16),
     }
@@ -578,6 +739,10 @@ def main():
         line["batched_form"] = batched_form(args, snect)
     if rank == 0 and args.serve_queries > 0:
         line["serving"] = serving(args, snect)
+    if rank == 0 and not args.no_ablation:
+        line["lockfree_ablation"] = lockfree_ablation(snect)
+    if rank == 0:
+        line["analyses"] = analyses(snect, None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

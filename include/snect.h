@@ -203,13 +203,59 @@ int snect_foldin_static(const float *G, const float *U2, const float *U3, int32_
                         int32_t J1, int32_t J2, int32_t J3, const int32_t *jk, const float *val,
                         int64_t n, float lambda, float *u_out, void *stream);
 
+/* Personalised subtype analysis (Sec. 3.3) of n patient profiles u (any, n*J1 floats, e.g.
+ * rows of U1 or fold-in results): per profile the subtype matrix S = G x1 u (J2 x J3),
+ * S[q][r] = sum_p g_pqr u_p; row_norm[q] = ||S[q][:]|| (the weight of gene-mode subtype q);
+ * platform_norm[k] = the norm of column k of S x3 U3, (S x3 U3)[q][k] = sum_r S[q][r] U3[k][r]
+ * (the weight of platform k).  S: any, n*J2*J3 floats; row_norm: any, n*J2; platform_norm: any,
+ * n*I3; each may be NULL.  FP32, fixed summation order.  All profiles in one launch.
+ * Synchronises.  Errors: SNECT_EINVAL, SNECT_ECUDA. */
+int snect_subtype(snect_ctx *ctx, const float *u, int64_t n, float *S, float *row_norm, float *platform_norm);
+
+/* Stratification of the patients (Sec. 3.1.1): k-means with Euclidean distance on the rows of
+ * U1, by Lloyd's iterations from the initial centroids init (any, k*J1 doubles).  A pass assigns
+ * each row to its nearest centroid (squared distance, ties to the lower index); a pass that
+ * changes no assignment ends the run; otherwise each centroid with rows moves to their mean
+ * (one without rows stays).  At most max_iter passes.  The assignment is decided in FP64 with a
+ * fixed operation order (per centroid, coordinates in order, no fused multiply-add) and each
+ * centroid is its rows' sum in ascending row order divided by their count, so the result is
+ * the one a sequential FP64 program with that order computes.
+ *   assign     any, I1 int32: the last pass's clusters (or NULL)
+ *   centroids  any, k*J1 doubles: the final centroids (or NULL)
+ *   n_updates  host: centroid updates made (or NULL); inertia  host: sum over the rows of the
+ *              squared distance to their assigned final centroid (or NULL)
+ * 1 <= k <= min(I1, 128), max_iter >= 1.  Synchronises.  Errors: SNECT_EINVAL, SNECT_ECUDA. */
+int snect_kmeans(snect_ctx *ctx, int32_t k, const double *init, int32_t max_iter, int32_t *assign,
+                 double *centroids, int32_t *n_updates, double *inertia);
+
+/* The lock-free form of Alg. 1 as the paper states it (Sec. 2.3.3), for comparison with the
+ * fast mode: P workers walk one interleaved order of entries and network edges (order: any,
+ * n_items int32; a value t < nnz is entry t of the visit order, t >= nnz is edge t - nnz);
+ * worker w takes items w, w + P, w + 2P, ...  An entry updates its three rows by the per-entry
+ * gradients of Sec. 2.3.2, read and applied without locks (atomic adds); only worker 0 steps
+ * the core, with step lr * P (Alg. 1 line 8).  An edge moves both gene rows towards each other
+ * (line 10).  With P = 1 this is Alg. 1 with one worker.  Runs n_epochs passes over the order
+ * (no separate network pass).  Needs a deterministic-mode context (batch > 0), which keeps the
+ * entries in the visit order.  Asynchronous after the order is checked.  Errors: SNECT_EINVAL
+ * (mode, P < 1, an item out of range), SNECT_ECUDA. */
+int snect_hogwild_epoch(snect_ctx *ctx, const int32_t *order, int64_t n_items, int32_t P, int32_t n_epochs);
+
 /* Which entry-sweep launches of an epoch carry CUDA timing events (fast mode: one sweep
  * launch per wave; deterministic mode: the gradient kernel of each batch).  mode 0 (the
- * default): none; 1: one launch per epoch, the middle one; -1: every launch.  Each timed
- * launch adds two event nodes to the epoch's CUDA graph, which cost the epoch several
- * microseconds each, so timing is off unless asked for.  A change takes effect at the next
- * snect_epoch (the epoch graph is captured again).  Errors: SNECT_EINVAL for another mode. */
+ * default): none; 1: one launch per epoch, the middle one; -1: every launch; 2: every launch
+ * of every kernel of the epoch (the sweeps, the wave ends or deterministic apply kernels, the
+ * network pass; read with snect_kernel_times).  Each timed launch adds two event nodes to
+ * the epoch's CUDA graph, which cost the epoch several microseconds each, so timing is off
+ * unless asked for.  A change takes effect at the next snect_epoch (the epoch graph is
+ * captured again).  Errors: SNECT_EINVAL for another mode. */
 int snect_set_sweep_timing(snect_ctx *ctx, int32_t mode);
+
+/* Per-kernel device time of the most recent epoch under timing mode 2: ms[0] / n[0] the
+ * entry-sweep launches, ms[1] / n[1] the wave-end steps (fast mode) or the apply kernels
+ * (deterministic mode), ms[2] / n[2] the network pass; each the summed milliseconds between
+ * CUDA events recorded on the context's stream immediately before and after each launch.
+ * ms and n: host, 3 each.  All zero unless an epoch ran with mode 2.  Synchronises. */
+int snect_kernel_times(snect_ctx *ctx, double *ms, int64_t *n);
 
 /* Device time of the timed entry-sweep launches (snect_set_sweep_timing) of the most recent
  * epoch, measured with CUDA events recorded on the context's stream immediately before and

@@ -52,6 +52,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_foldin.restype = ctypes.c_int
             lib.oracle_qr_post.restype = ctypes.c_int
+            lib.oracle_kmeans.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -240,3 +241,52 @@ def qr_post(I, params: Params):
     J, Jp = _i32(params.J)
     return int(lib.oracle_qr_post(Ip, Jp, params.G.ctypes.data_as(_f64p),
                                   *(u.ctypes.data_as(_f64p) for u in params.U)))
+
+
+def hogwild_epoch(I, params: Params, lam, lam_g, lr, idx, val, edges, w, order):
+    """Alg. 1 lines 3-13 with one worker in a given interleaved order of entries and edges
+    (order[t] < nnz: entry order[t]; otherwise edge order[t] - nnz), reading R13."""
+    lib = _load()
+    I, Ip = _i32(I)
+    J, Jp = _i32(params.J)
+    idx, ip = _i32(idx)
+    val, vp = _f64(val)
+    edges, ep = _i32(edges.reshape(-1, 2) if len(edges) else np.zeros((0, 2), np.int32))
+    w, wp = _f64(w)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    lib.oracle_hogwild_epoch(Ip, Jp, ctypes.c_double(lam), ctypes.c_double(lam_g), ctypes.c_double(lr),
+                             params.G.ctypes.data_as(_f64p), *(u.ctypes.data_as(_f64p) for u in params.U), ip, vp,
+                             ctypes.c_int64(idx.shape[0]), ep, wp, ctypes.c_int64(edges.shape[0]),
+                             order.ctypes.data_as(_i64p), ctypes.c_int64(order.shape[0]))
+
+
+def subtype(G, U3, u):
+    """Personalised subtype matrix S = G x1 u (J2 x J3), its row norms (J2) and the column
+    norms of S x3 U3 (I3) (Sec. 3.3)."""
+    lib = _load()
+    G, Gp = _f64(G)
+    U3, cp = _f64(U3)
+    u, up = _f64(u)
+    J, Jp = _i32(G.shape)
+    S = np.zeros((G.shape[1], G.shape[2]))
+    rn = np.zeros(G.shape[1])
+    pn = np.zeros(U3.shape[0])
+    lib.oracle_subtype(Jp, ctypes.c_int32(U3.shape[0]), Gp, cp, up, S.ctypes.data_as(_f64p),
+                       rn.ctypes.data_as(_f64p), pn.ctypes.data_as(_f64p))
+    return S, rn, pn
+
+
+def kmeans(X, init, max_iter=100):
+    """Lloyd's k-means of the rows of X from the initial centroids (Sec. 3.1.1, reading R14):
+    (assignment int32, centroids float64, centroid updates made, inertia)."""
+    lib = _load()
+    X, xp = _f64(X)
+    cent = np.array(init, dtype=np.float64, order="C")
+    n, d = X.shape
+    k = cent.shape[0]
+    assign = np.zeros(n, dtype=np.int32)
+    inertia = ctypes.c_double()
+    it = lib.oracle_kmeans(xp, ctypes.c_int64(n), ctypes.c_int32(d), ctypes.c_int32(k),
+                           cent.ctypes.data_as(_f64p), ctypes.c_int32(max_iter),
+                           assign.ctypes.data_as(_i32p), ctypes.byref(inertia))
+    return assign, cent, int(it), inertia.value

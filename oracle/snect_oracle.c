@@ -29,6 +29,15 @@
  *       that the per-entry L2 terms of Sec. 2.3.2 add up to for one row.
  *   R7  Top-k: cosine similarity, descending, ties to the lower row index, a zero-norm row
  *       (or query) scores 0.
+ *   R13 The lock-free form of Alg. 1 (Sec. 2.3.3) with one worker: entries and network edges
+ *       are visited in one given interleaved order; an entry updates its three rows and the
+ *       core at once from the values it read (core step eta * P with P = 1); an edge updates
+ *       both endpoints from the values read before either changes.
+ *   R14 k-means (Sec. 3.1.1): Lloyd's iterations with squared Euclidean distances from given
+ *       initial centroids; ties go to the lower centroid index; a centroid with no rows keeps
+ *       its place; stop when an assignment pass changes nothing.  Distances are summed over
+ *       the coordinates in order, centroids as sums over the rows in ascending order divided
+ *       by the count, all in FP64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -517,4 +526,139 @@ int oracle_qr_post(const int32_t *I, const int32_t *J, double *G, double *U1, do
     }
     free(Gn);
     return skipped;
+}
+
+/* Alg. 1 lines 3-13 with one worker (P = 1) in a given interleaved order (reading R13):
+ * order[t] < n picks entry order[t] of idx/val, order[t] >= n picks edge order[t] - n.
+ * Entry: the per-entry gradients of Sec. 2.3.2 at the current values, then
+ * u_in <- u_in - lr g_n for the three rows and G <- G - lr * P * gG with P = 1.
+ * Edge (k1, k2, y): u_k1 <- u_k1 - lr lambda_g y (u_k1 - u_k2) and
+ * u_k2 <- u_k2 - lr lambda_g y (u_k2 - u_k1), both from the values before the edge.
+ * The counts |Omega^{n,i}| come from all n entries. */
+void oracle_hogwild_epoch(const int32_t *I, const int32_t *J, double lambda, double lambda_g,
+                          double lr, double *G, double *U1, double *U2, double *U3,
+                          const int32_t *idx, const double *val, int64_t n, const int32_t *edges,
+                          const double *w, int64_t m, const int64_t *order, int64_t n_items) {
+    int64_t *cnt[3];
+    for (int md = 0; md < 3; ++md) cnt[md] = (int64_t *)malloc(sizeof(int64_t) * ((size_t)I[md] + 1));
+    oracle_counts(I, idx, n, cnt[0], cnt[1], cnt[2]);
+    int64_t PI = (int64_t)J[0] * J[1] * J[2];
+    double *gG = (double *)malloc(sizeof(double) * PI);
+    double ga[64], gb[64], gc[64], d[64];
+    for (int64_t t = 0; t < n_items; ++t) {
+        int64_t it = order[t];
+        if (it < n) {
+            const int32_t *e = idx + 3 * it;
+            double *a = U1 + (int64_t)e[0] * J[0];
+            double *b = U2 + (int64_t)e[1] * J[1];
+            double *c = U3 + (int64_t)e[2] * J[2];
+            entry_grads(J, G, a, b, c, val[it], lambda / (double)cnt[0][e[0]],
+                        lambda / (double)cnt[1][e[1]], lambda / (double)cnt[2][e[2]],
+                        lambda / (double)n, ga, gb, gc, gG);
+            for (int q = 0; q < J[0]; ++q) a[q] -= lr * ga[q];
+            for (int q = 0; q < J[1]; ++q) b[q] -= lr * gb[q];
+            for (int q = 0; q < J[2]; ++q) c[q] -= lr * gc[q];
+            for (int64_t s = 0; s < PI; ++s) G[s] -= lr * gG[s];
+        } else {
+            int64_t ed = it - n;
+            double *u = U2 + (int64_t)edges[2 * ed] * J[1];
+            double *v = U2 + (int64_t)edges[2 * ed + 1] * J[1];
+            double st = lr * lambda_g * w[ed];
+            for (int q = 0; q < J[1]; ++q) d[q] = u[q] - v[q];
+            for (int q = 0; q < J[1]; ++q) {
+                u[q] -= st * d[q];
+                v[q] += st * d[q];
+            }
+        }
+    }
+    free(gG);
+    for (int md = 0; md < 3; ++md) free(cnt[md]);
+}
+
+/* Personalised subtype matrix of one patient profile u (Sec. 3.3): S = G x1 u (J2 x J3),
+ * S[q][r] = sum_p g_pqr u_p.  row_norm[q] = ||S[q][:]|| is the weight of gene-mode subtype q
+ * for the patient; platform_norm[k] = || (S x3 U3)[:][k] ||, (S x3 U3)[q][k] =
+ * sum_r S[q][r] U3[k][r], is the weight of platform k (I3 platforms). */
+void oracle_subtype(const int32_t *J, int32_t I3, const double *G, const double *U3, const double *u,
+                    double *S, double *row_norm, double *platform_norm) {
+    for (int q = 0; q < J[1]; ++q)
+        for (int r = 0; r < J[2]; ++r) {
+            double acc = 0.0;
+            for (int p = 0; p < J[0]; ++p) acc += G[GIDX(p, q, r, J[1], J[2])] * u[p];
+            S[q * J[2] + r] = acc;
+        }
+    for (int q = 0; q < J[1]; ++q) {
+        double acc = 0.0;
+        for (int r = 0; r < J[2]; ++r) acc += S[q * J[2] + r] * S[q * J[2] + r];
+        row_norm[q] = sqrt(acc);
+    }
+    for (int k = 0; k < I3; ++k) {
+        double acc = 0.0;
+        for (int q = 0; q < J[1]; ++q) {
+            double t = 0.0;
+            for (int r = 0; r < J[2]; ++r) t += S[q * J[2] + r] * U3[(int64_t)k * J[2] + r];
+            acc += t * t;
+        }
+        platform_norm[k] = sqrt(acc);
+    }
+}
+
+/* k-means of the n rows of X (n x d) into k clusters (Sec. 3.1.1 on the patient profiles,
+ * reading R14), from the initial centroids cent (k x d, overwritten with the final ones).
+ * Each pass assigns every row to its nearest centroid; if no assignment changed, it stops;
+ * otherwise every centroid with rows moves to their mean.  At most max_iter passes.  assign
+ * (n) gets the last pass's clusters, *inertia the summed squared distance of every row to its
+ * assigned centroid among the final ones.  Returns the number of centroid updates made. */
+int oracle_kmeans(const double *X, int64_t n, int32_t d, int32_t k, double *cent, int32_t max_iter,
+                  int32_t *assign, double *inertia) {
+    double *sum = (double *)malloc(sizeof(double) * (size_t)k * d);
+    int64_t *cntk = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int updates = 0;
+    for (int64_t i = 0; i < n; ++i) assign[i] = -1;
+    for (int it = 0; it < max_iter; ++it) {
+        int64_t changed = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int best = 0;
+            double bd = 0.0;
+            for (int c = 0; c < k; ++c) {
+                double dist = 0.0;
+                for (int p = 0; p < d; ++p) {
+                    double t = X[i * d + p] - cent[(int64_t)c * d + p];
+                    dist = dist + t * t;
+                }
+                if (c == 0 || dist < bd) {
+                    bd = dist;
+                    best = c;
+                }
+            }
+            if (assign[i] != best) ++changed;
+            assign[i] = best;
+        }
+        if (changed == 0) break;
+        for (int c = 0; c < k; ++c) {
+            cntk[c] = 0;
+            for (int p = 0; p < d; ++p) sum[(int64_t)c * d + p] = 0.0;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            cntk[assign[i]] += 1;
+            for (int p = 0; p < d; ++p) sum[(int64_t)assign[i] * d + p] += X[i * d + p];
+        }
+        for (int c = 0; c < k; ++c)
+            if (cntk[c] > 0)
+                for (int p = 0; p < d; ++p) cent[(int64_t)c * d + p] = sum[(int64_t)c * d + p] / (double)cntk[c];
+        ++updates;
+    }
+    double tot = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double dist = 0.0;
+        for (int p = 0; p < d; ++p) {
+            double t = X[i * d + p] - cent[(int64_t)assign[i] * d + p];
+            dist = dist + t * t;
+        }
+        tot += dist;
+    }
+    *inertia = tot;
+    free(sum);
+    free(cntk);
+    return updates;
 }

@@ -49,6 +49,10 @@ EXPORTS = (
     "snect_serve_stop",
     "snect_set_sweep_timing",
     "snect_sweep_times",
+    "snect_subtype",
+    "snect_kmeans",
+    "snect_hogwild_epoch",
+    "snect_kernel_times",
     "snect_wave_grads",
     "snect_launch_count",
     "snect_last_error",
@@ -137,6 +141,10 @@ def load(build_if_missing: bool = False):
         "snect_set_sweep_timing": (ctypes.c_int, [P, ctypes.c_int32]),
         "snect_sweep_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64)]),
+        "snect_subtype": (ctypes.c_int, [P, P, i64, P, P, P]),
+        "snect_kmeans": (ctypes.c_int, [P, i32, P, i32, P, P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]),
+        "snect_hogwild_epoch": (ctypes.c_int, [P, P, i64, i32, i32]),
+        "snect_kernel_times": (ctypes.c_int, [P, P, P]),
         "snect_wave_grads": (ctypes.c_int, [P, i64, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]),
         "snect_launch_count": (ctypes.c_int64, [P]),
@@ -275,7 +283,8 @@ class Snect:
         return idx, sc
 
     def set_sweep_timing(self, mode: int):
-        """Sweep launches timed per epoch: 0 none (default), 1 the middle one, -1 all."""
+        """Sweep launches timed per epoch: 0 none (default), 1 the middle one, -1 all, 2 every
+        kernel of the epoch (see kernel_times)."""
         self._check(self._lib.snect_set_sweep_timing(self._h, int(mode)))
 
     def sweep_times(self):
@@ -285,6 +294,48 @@ class Snect:
         e = ctypes.c_int64()
         self._check(self._lib.snect_sweep_times(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(e)))
         return ms.value, n.value, e.value
+
+    def subtype(self, u):
+        """Personalised subtype analysis (Sec. 3.3) of profiles u ((n, J1) or (J1,)): (S (n, J2,
+        J3), row norms (n, J2), platform norms (n, I3))."""
+        keep = []
+        u2 = u if hasattr(u, "data_ptr") else np.ascontiguousarray(u, np.float32)
+        n = int(u2.shape[0]) if len(u2.shape) == 2 else 1
+        J, I = self.J, self.I
+        S = np.empty((n, J[1], J[2]), np.float32)
+        rn = np.empty((n, J[1]), np.float32)
+        pn = np.empty((n, I[2]), np.float32)
+        self._check(self._lib.snect_subtype(self._h, _ptr(u2, keep, np.float32), n, S.ctypes.data, rn.ctypes.data,
+                                            pn.ctypes.data))
+        return S, rn, pn
+
+    def kmeans(self, init, max_iter: int = 100):
+        """k-means of the rows of U1 (Sec. 3.1.1) from initial centroids init (k x J1):
+        (assignment int32, centroids float64, centroid updates, inertia)."""
+        init = np.ascontiguousarray(init, np.float64)
+        k = int(init.shape[0])
+        assign = np.empty(self.I[0], np.int32)
+        cent = np.empty((k, self.J[0]), np.float64)
+        upd = ctypes.c_int32()
+        inertia = ctypes.c_double()
+        self._check(self._lib.snect_kmeans(self._h, k, init.ctypes.data, int(max_iter), assign.ctypes.data,
+                                           cent.ctypes.data, ctypes.byref(upd), ctypes.byref(inertia)))
+        return assign, cent, upd.value, inertia.value
+
+    def hogwild_epoch(self, order, P: int, n: int = 1):
+        """n epochs of the lock-free form of Alg. 1 with P workers over one interleaved order of
+        entries and edges (snect_hogwild_epoch)."""
+        keep = []
+        n_items = int(order.shape[0])
+        self._check(self._lib.snect_hogwild_epoch(self._h, _ptr(order, keep, np.int32), n_items, int(P), int(n)))
+
+    def kernel_times(self):
+        """Under timing mode 2: {class: (summed ms, launches)} of the most recent epoch for the
+        entry sweeps, the wave ends (or deterministic apply kernels) and the network pass."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        self._check(self._lib.snect_kernel_times(self._h, ms, n))
+        return {k: (ms[t], n[t]) for t, k in enumerate(("sweep", "wave_end", "network_pass"))}
 
     def wave_grads(self, w: int):
         """One wave's entry sweep alone at the current parameters (snect_wave_grads): dict of

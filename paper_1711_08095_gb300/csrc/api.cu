@@ -55,8 +55,12 @@ void free_all(Ctx *c) {
     c->epoch_exec = nullptr;
     for (auto e : c->ev_begin) cudaEventDestroy(e);
     for (auto e : c->ev_end) cudaEventDestroy(e);
+    for (auto e : c->aux_begin) cudaEventDestroy(e);
+    for (auto e : c->aux_end) cudaEventDestroy(e);
     c->ev_begin.clear();
     c->ev_end.clear();
+    c->aux_begin.clear();
+    c->aux_end.clear();
     free_fast(c);
     dfree(c->rec);
     for (int m = 0; m < 3; ++m) {
@@ -118,7 +122,10 @@ int enqueue_det_epoch(Ctx *c) {
         if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[b], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, launch_det_grad(c, first, len));
         if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[b], c->stream, cudaEventRecordExternal));
+        int rc = aux_event(c, 1, false);
+        if (rc) return rc;
         SNECT_CUDA(c, launch_det_apply(c, first, len));
+        if ((rc = aux_event(c, 1, true))) return rc;
     }
     return SNECT_OK;
 }
@@ -126,8 +133,9 @@ int enqueue_det_epoch(Ctx *c) {
 int enqueue_epoch(Ctx *c) {
     int rc = c->cfg.batch > 0 ? enqueue_det_epoch(c) : enqueue_fast_epoch(c);
     if (rc) return rc;
+    if ((rc = aux_event(c, 2, false))) return rc;
     SNECT_CUDA(c, launch_edge_pass(c));
-    return SNECT_OK;
+    return aux_event(c, 2, true);
 }
 
 // one epoch captured once into a CUDA graph (on a private stream: capture is not allowed on
@@ -139,6 +147,7 @@ int build_epoch_graph(Ctx *c) {
     const int64_t before = c->launches;
     c->timed_idx.clear();
     c->timed_len.clear();
+    c->aux_cls.clear();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int rc = SNECT_OK;
@@ -200,6 +209,26 @@ int timing_events(Ctx *c, int64_t n) {
         c->ev_begin.push_back(a);
         SNECT_CUDA(c, cudaEventCreate(&b));
         c->ev_end.push_back(b);
+    }
+    return SNECT_OK;
+}
+
+int aux_event(Ctx *c, int32_t cls, bool end) {
+    if (c->timed != 2) return SNECT_OK;
+    if (!end) {
+        const size_t i = c->aux_cls.size();
+        if (i >= c->aux_begin.size()) {  // made on demand, before the graph that records them
+            cudaEvent_t a = nullptr, b = nullptr;
+            SNECT_CUDA(c, cudaEventCreate(&a));
+            SNECT_CUDA(c, cudaEventCreate(&b));
+            c->aux_begin.push_back(a);
+            c->aux_end.push_back(b);
+        }
+        c->aux_cls.push_back(cls);
+        SNECT_CUDA(c, cudaEventRecordWithFlags(c->aux_begin[i], c->stream, cudaEventRecordExternal));
+    } else {
+        SNECT_CUDA(c, cudaEventRecordWithFlags(c->aux_end[c->aux_cls.size() - 1], c->stream,
+                                               cudaEventRecordExternal));
     }
     return SNECT_OK;
 }
@@ -507,7 +536,7 @@ int snect_topk(snect_ctx *h, const float *u, int32_t k, int32_t *idx_out, float 
 int snect_set_sweep_timing(snect_ctx *h, int32_t mode) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c) return SNECT_EINVAL;
-    if (mode < -1 || mode > 1) return fail(c, SNECT_EINVAL, "sweep timing mode must be -1, 0 or 1");
+    if (mode < -1 || mode > 2) return fail(c, SNECT_EINVAL, "sweep timing mode must be -1, 0, 1 or 2");
     if (mode == c->timed) return SNECT_OK;
     c->timed = mode;
     if (c->epoch_exec) {  // the next epoch captures a graph with the new event nodes
@@ -517,6 +546,7 @@ int snect_set_sweep_timing(snect_ctx *h, int32_t mode) {
     }
     c->timed_idx.clear();
     c->timed_len.clear();
+    c->aux_cls.clear();
     return SNECT_OK;
 }
 
@@ -539,6 +569,39 @@ int snect_sweep_times(snect_ctx *h, double *ms_total, int64_t *n_launches, int64
     return SNECT_OK;
 }
 
+int snect_subtype(snect_ctx *h, const float *u, int64_t n, float *S, float *row_norm, float *platform_norm) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (n < 0) return fail(c, SNECT_EINVAL, "n must be >= 0");
+    if (n == 0) return SNECT_OK;
+    if (!u) return fail(c, SNECT_EINVAL, "null profile pointer");
+    return run_subtype(c, u, n, S, row_norm, platform_norm);
+}
+
+int snect_kmeans(snect_ctx *h, int32_t k, const double *init, int32_t max_iter, int32_t *assign,
+                 double *centroids, int32_t *n_updates, double *inertia) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (k < 1 || k > kmeans_max_clusters() || k > c->d.I1)
+        return fail(c, SNECT_EINVAL, "k must be in [1, min(I1, 128)]");
+    if (max_iter < 1) return fail(c, SNECT_EINVAL, "max_iter must be >= 1");
+    if (!init) return fail(c, SNECT_EINVAL, "null initial centroids");
+    return run_kmeans(c, k, init, max_iter, assign, centroids, n_updates, inertia);
+}
+
+int snect_hogwild_epoch(snect_ctx *h, const int32_t *order, int64_t n_items, int32_t P, int32_t n_epochs) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c) return SNECT_EINVAL;
+    if (c->cfg.batch <= 0)
+        return fail(c, SNECT_EINVAL, "snect_hogwild_epoch needs a deterministic-mode context (batch > 0), "
+                                     "which keeps the entries in the visit order");
+    if (P < 1) return fail(c, SNECT_EINVAL, "P must be >= 1");
+    if (n_items < 0 || n_items > INT32_MAX || n_epochs < 0) return fail(c, SNECT_EINVAL, "bad n_items or n_epochs");
+    if (n_items == 0 || n_epochs == 0) return SNECT_OK;
+    if (!order) return fail(c, SNECT_EINVAL, "null order");
+    return run_hogwild(c, order, n_items, P, n_epochs);
+}
+
 int snect_wave_grads(snect_ctx *h, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB,
                      int64_t *first, int64_t *count) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
@@ -549,6 +612,30 @@ int snect_wave_grads(snect_ctx *h, int64_t w, float *gA, float *gB, float *M, fl
     if (rc) return rc;
     if (first) *first = w * c->wave;
     if (count) *count = c->wave_len[w];
+    return SNECT_OK;
+}
+
+int snect_kernel_times(snect_ctx *h, double *ms, int64_t *n) {
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c || !ms || !n) return SNECT_EINVAL;
+    for (int t = 0; t < 3; ++t) {
+        ms[t] = 0.0;
+        n[t] = 0;
+    }
+    if (!c->epoch_exec || c->timed != 2) return SNECT_OK;
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t t = 0; t < c->timed_idx.size(); ++t) {
+        float x = 0.f;
+        SNECT_CUDA(c, cudaEventElapsedTime(&x, c->ev_begin[c->timed_idx[t]], c->ev_end[c->timed_idx[t]]));
+        ms[0] += x;
+        ++n[0];
+    }
+    for (size_t t = 0; t < c->aux_cls.size(); ++t) {
+        float x = 0.f;
+        SNECT_CUDA(c, cudaEventElapsedTime(&x, c->aux_begin[t], c->aux_end[t]));
+        ms[c->aux_cls[t]] += x;
+        ++n[c->aux_cls[t]];
+    }
     return SNECT_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -111,12 +112,17 @@ struct Ctx {
     std::vector<int64_t> timed_idx, timed_len;  // event pairs recorded by the epoch graph, entries
 
     // true if launch i of n_launches carries timing events; records it with its entries
+    // (timed == 2 times every sweep launch, like -1, and the other kernels as well)
     bool time_launch(int64_t i, int64_t n_launches, int64_t entries) {
         if (timed == 0 || (timed == 1 && i != n_launches / 2)) return false;
         timed_idx.push_back(i);
         timed_len.push_back(entries);
         return true;
     }
+    // timed == 2: event pairs around the other kernels of the epoch (wave ends or the
+    // deterministic apply kernels: class 1; the network pass: class 2), in recording order
+    std::vector<cudaEvent_t> aux_begin, aux_end;
+    std::vector<int32_t> aux_cls;
     // error word written by kernels (validation)
     int32_t *flag = nullptr;
 };
@@ -176,6 +182,12 @@ int enqueue_fast_epoch(Ctx *c);
 // the entry sweep of one wave alone, its accumulators copied out (snect_wave_grads)
 int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB);
 void free_fast(Ctx *c);
+// downstream analyses (analysis.cu) and the lock-free form of Alg. 1 (hogwild.cu)
+int run_subtype(Ctx *c, const float *u, int64_t n, float *S, float *row_norm, float *plat_norm);
+int run_kmeans(Ctx *c, int32_t k, const double *init, int32_t max_iter, int32_t *assign, double *centroids,
+               int32_t *n_updates, double *inertia);
+int kmeans_max_clusters();
+int run_hogwild(Ctx *c, const int32_t *order, int64_t n_items, int32_t P, int32_t n_epochs);
 constexpr int kFastTile = 256;     // entries per tile (one per thread of the wave kernel)
 constexpr int64_t kMinWave = 4096;      // default wave: nnz/16 clamped to [kMinWave, kMaxWave]
 constexpr int64_t kMaxWave = 1 << 21;
@@ -183,6 +195,9 @@ int det_scratch_floats(const Ctx *c, int64_t *gbuf_floats, int64_t *part_floats)
 cudaError_t det_init_attrs(Ctx *c);
 cudaError_t loss_init_attrs(Ctx *c);
 int timing_events(Ctx *c, int64_t n);  // makes n begin/end event pairs
+// timed == 2: records the begin (end = false) or end event of the next kernel of class cls
+// around which the epoch graph carries timing events; no-op otherwise
+int aux_event(Ctx *c, int32_t cls, bool end);
 int pack_records(Ctx *c, const int32_t *d_idx, const float *d_val, int64_t n, Rec *out,
                  bool check_ranges, int32_t n_modes);
 

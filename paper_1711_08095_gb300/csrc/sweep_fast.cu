@@ -2254,7 +2254,10 @@ int enqueue_fast_epoch(Ctx *c) {
         if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_begin[w], c->stream, cudaEventRecordExternal));
         SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, run_sweep, c, w));
         if (tm) SNECT_CUDA(c, cudaEventRecordWithFlags(c->ev_end[w], c->stream, cudaEventRecordExternal));
+        int rc = aux_event(c, 1, false);
+        if (rc) return rc;
         SNECT_CUDA(c, launch_wave_end(c, w, (int)(w & 1), 0));
+        if ((rc = aux_event(c, 1, true))) return rc;
     }
     return SNECT_OK;
 }

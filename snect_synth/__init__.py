@@ -41,6 +41,8 @@ __all__ = [
     "serving_model",
     "serving_query",
     "poisson_arrivals",
+    "interleaved_order",
+    "clustered_profiles",
 ]
 
 
@@ -318,3 +320,27 @@ def poisson_arrivals(n, rate, seed=5):
     """Arrival times (seconds) of a Poisson stream: cumulative exponential gaps."""
     rng = np.random.default_rng([seed, 7])
     return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def interleaved_order(nnz, m, seed=6):
+    """A random interleaving of nnz entries and m network edges (Alg. 1 picks both in random
+    order): a permutation of 0 .. nnz + m - 1, where t < nnz is entry t of the visit order and
+    t >= nnz is edge t - nnz.  int32."""
+    rng = np.random.default_rng([seed, nnz, m])
+    return rng.permutation(nnz + m).astype(np.int32)
+
+
+def clustered_profiles(n, d, k, spread=0.05, seed=7):
+    """Patient profiles with planted clusters (the stratification of Sec. 3.1.1 runs k-means
+    on the rows of U1): k centres iid N(0, 1/d) per coordinate, each row a centre plus
+    N(0, spread^2 / d) noise, cluster sizes uneven (Dirichlet weights).  Returns (X (n, d)
+    float32, labels (n,) int32, init (k, d) float64: one seeded random member of each cluster,
+    the initial centroids)."""
+    rng = np.random.default_rng([seed, n, d, k])
+    centres = rng.standard_normal((k, d)) / math.sqrt(d)
+    wts = rng.dirichlet(np.full(k, 2.0))
+    labels = rng.choice(k, size=n, p=wts).astype(np.int32)
+    labels[:k] = np.arange(k, dtype=np.int32)  # every cluster has a member
+    X = (centres[labels] + spread / math.sqrt(d) * rng.standard_normal((n, d))).astype(np.float32)
+    init = np.stack([X[rng.choice(np.flatnonzero(labels == c))] for c in range(k)]).astype(np.float64)
+    return X, labels, init

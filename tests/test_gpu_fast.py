@@ -61,8 +61,9 @@ def test_fast_mode_is_stable_for_any_wave(small, gpu_lib):
 
 
 def test_sweep_timing_modes(gpu_lib):
-    """Timing events: none by default, the middle launch (mode 1) or every launch (mode -1);
-    the timed launches account for their entries, all of them over a whole epoch."""
+    """Timing events: none by default, the middle launch (mode 1), every launch (mode -1) or
+    every kernel by class (mode 2); the timed launches account for their entries, all of them
+    over a whole epoch."""
     import paper_1711_08095_gb300 as snect
 
     p = S.config2(n_patients=60, n_genes=2000, nnz=40_000, n_edges=3_000)
@@ -79,8 +80,16 @@ def test_sweep_timing_modes(gpu_lib):
         c.epoch(2)
         ms1, n1, e1 = c.sweep_times()
         assert n1 == 1 and 0 < e1 <= -(-len(p.idx) // (n - 1)) and ms1 > 0, (batch, ms1, n1, e1)
+        # mode 2: every kernel of the epoch, by class
+        c.set_sweep_timing(2)
+        c.epoch(1)
+        kt = c.kernel_times()
+        ms2, n2, e2 = c.sweep_times()
+        assert kt["sweep"] == (ms2, n2) and n2 == n and e2 == len(p.idx), (batch, kt, n2)
+        assert kt["wave_end"][1] == n and kt["wave_end"][0] > 0, (batch, kt)
+        assert kt["network_pass"][1] == 1 and kt["network_pass"][0] > 0, (batch, kt)
         with pytest.raises(RuntimeError):
-            c.set_sweep_timing(2)
+            c.set_sweep_timing(3)
         c.close()
 
 

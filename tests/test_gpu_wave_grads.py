@@ -15,7 +15,7 @@ Every compiled path of the sweep is driven: the statically partitioned per-run s
 (10x10x5, 16x16x5), its tile-claiming variant (16x16x5 with 20 platforms, every platform's
 Gc beyond the shared-memory budget), the variant that counts with atomics (64 platforms,
 1,024-entry waves), the per-entry sweep (32x32x5, and runtime ranks 3x7x4), and the BF16
-tensor-core sweep (tolerance 3e-2: its operands are rounded to BF16).  Each at the initial
+tensor-core sweep (tolerance 16 units of BF16 roundoff: its operands are rounded to BF16).  Each at the initial
 parameters and again after two epochs, on the first, a middle and the last (ragged) wave.
 """
 import numpy as np
@@ -27,7 +27,11 @@ import snect_synth as S
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
-TOL_BF16 = 3e-2
+# BF16 keeps 8 significant bits: unit roundoff u = 2^-8.  The tensor-core sweep rounds a, b
+# and Gc = G x3 c to BF16 before its K = J-term products (v = Gc b, w2 = Gc^T a), so each
+# product carries up to 2u of relative error and a sum of J terms of mixed sign up to
+# 2u sum|terms|, a few times |sum| at J = 16; the bound is 16u.
+TOL_BF16 = 16 * 2.0 ** -8
 
 
 def close(got, want, tol):
@@ -61,8 +65,7 @@ def check_waves(p, tol, precision=0, wave=0, epochs_between=2):
             errs = {"gA": close(got["gA"], want["gA"], tol), "gB": close(got["gB"], want["gB"], tol),
                     "gG": close(gG, want["gG"], tol), "gC": close(gC, want["gC"], tol)}
             report.append((stage, w, errs))
-            for key, e in errs.items():
-                assert e <= tol, (p.J, stage, w, key, e)
+            assert max(errs.values()) <= tol, (p.J, stage, w, errs, report)
             assert np.array_equal(got["nA"], want["nA"].astype(np.float32)), (stage, w, "nA")
             assert np.array_equal(got["nB"], want["nB"].astype(np.float32)), (stage, w, "nB")
     # the diagnostic leaves the factors alone

@@ -414,3 +414,112 @@ def test_topk_matches_sorted_cosine():
     assert list(idx) == order
     assert np.allclose(s, sc[order], rtol=1e-12)
     assert list(idx[:2]) == [3, 11]
+
+
+# ---------------------------------------------------------------------------------------
+# the lock-free form of Alg. 1 with one worker (Sec. 2.3.3, reading R13)
+def test_hogwild_entries_only_is_the_sequential_epoch(tiny):
+    P0 = oracle.Params(tiny.G0, tiny.U0)
+    P1, P2 = P0.copy(), P0.copy()
+    none = np.zeros((0, 2), np.int32)
+    oracle.sgd_epoch(tiny.I, P1, tiny.lam, tiny.lam_g, tiny.lr, tiny.idx, tiny.val, none, np.zeros(0))
+    oracle.hogwild_epoch(tiny.I, P2, tiny.lam, tiny.lam_g, tiny.lr, tiny.idx, tiny.val, none, np.zeros(0),
+                         np.arange(tiny.nnz))
+    for a, b in zip([P1.G] + P1.U, [P2.G] + P2.U):
+        assert np.array_equal(a, b)
+
+
+def test_hogwild_edges_on_a_matching_are_the_network_pass():
+    """Disjoint edges: each edge item is the row-owned pass's update of both endpoints."""
+    I2, J2 = 6, 3
+    rng = np.random.default_rng(5)
+    U2 = rng.standard_normal((I2, J2))
+    edges = np.array([[0, 3], [4, 1], [2, 5]], np.int32)
+    w = np.array([0.7, 1.0, 0.5])
+    lam_g, lr = 0.4, 0.3
+    A = oracle.Params(np.ones((1, J2, 1)), [np.zeros((1, 1)), U2.copy(), np.zeros((1, 1))])
+    B = oracle.Params(np.ones((1, J2, 1)), [np.zeros((1, 1)), U2.copy(), np.zeros((1, 1))])
+    oracle.edge_pass(I2, A, lam_g, lr, edges, w)
+    no = np.zeros((0, 3), np.int32)
+    oracle.hogwild_epoch((1, I2, 1), B, 0.0, lam_g, lr, no, np.zeros(0), edges, w, np.array([1, 0, 2]))
+    assert np.allclose(A.U[1], B.U[1], rtol=1e-14, atol=1e-15)
+
+
+def test_hogwild_interleaving_matters(tiny):
+    """An edge visited between entries changes what later entries see."""
+    P0 = oracle.Params(tiny.G0, tiny.U0)
+    n, m = tiny.nnz, tiny.edges.shape[0]
+    a, b = P0.copy(), P0.copy()
+    first = np.concatenate([np.arange(n), n + np.arange(m)])
+    mixed = np.concatenate([n + np.arange(m), np.arange(n)])
+    oracle.hogwild_epoch(tiny.I, a, tiny.lam, 5.0, tiny.lr, tiny.idx, tiny.val, tiny.edges, tiny.w, first)
+    oracle.hogwild_epoch(tiny.I, b, tiny.lam, 5.0, tiny.lr, tiny.idx, tiny.val, tiny.edges, tiny.w, mixed)
+    assert not np.allclose(a.U[0], b.U[0])
+
+
+# ---------------------------------------------------------------------------------------
+# personalised subtype matrix (Sec. 3.3)
+def test_subtype_unit_profile_is_a_core_slice():
+    rng = np.random.default_rng(8)
+    G = rng.standard_normal((4, 3, 2))
+    U3 = rng.standard_normal((5, 2))
+    for p in range(4):
+        S, rn, pn = oracle.subtype(G, U3, np.eye(4)[p])
+        assert np.array_equal(S, G[p])
+        assert np.allclose(rn, np.sqrt((G[p] ** 2).sum(1)), rtol=1e-14)
+
+
+def test_subtype_reproduces_the_patient_slice_and_its_norms():
+    """b_j^T S c_k is the patient's predicted cell (Eq. 2 by the matricization identity); with
+    orthonormal U2 and U3 the row norms of S and the platform norms are those of U2^T X_i U3
+    and of the columns of the patient's predicted gene x platform slice X_i."""
+    rng = np.random.default_rng(9)
+    J = (4, 3, 2)
+    I = (5, 7, 4)
+    G = rng.standard_normal(J)
+    U = [rng.standard_normal((I[n], J[n])) for n in range(3)]
+    U[1] = np.linalg.qr(U[1])[0]
+    U[2] = np.linalg.qr(U[2])[0]
+    i = 2
+    S, rn, pn = oracle.subtype(G, U[2], U[0][i])
+    jj, kk = np.meshgrid(np.arange(I[1]), np.arange(I[2]), indexing="ij")
+    idx = np.stack([np.full(jj.size, i), jj.ravel(), kk.ravel()], 1)
+    Xi = xhat_kron(G, U, idx).reshape(I[1], I[2])
+    assert np.allclose(U[1] @ S @ U[2].T, Xi, rtol=1e-12, atol=1e-12)
+    assert np.allclose(pn, np.linalg.norm(Xi, axis=0), rtol=1e-12)
+    assert np.allclose(rn, np.linalg.norm(U[1].T @ Xi @ U[2], axis=1), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# k-means stratification of the patient profiles (Sec. 3.1.1, reading R14)
+def test_kmeans_recovers_planted_clusters_at_a_fixed_point():
+    X, labels, init = S.clustered_profiles(600, 10, 13, spread=0.05, seed=3)
+    a, cent, it, inertia = oracle.kmeans(X, init, 100)
+    assert np.array_equal(a, labels) and it < 100
+    Xd = X.astype(np.float64)
+    D = ((Xd[:, None, :] - cent[None, :, :]) ** 2).sum(-1)
+    assert np.array_equal(np.argmin(D, 1), a)  # each row at its nearest centroid
+    for c in range(13):
+        assert np.allclose(cent[c], Xd[a == c].mean(0), rtol=1e-12, atol=1e-15)  # centroid = mean
+    assert abs(inertia - D[np.arange(600), a].sum()) <= 1e-12 * inertia
+
+
+def test_kmeans_matches_scipy_lloyd():
+    from scipy.cluster.vq import kmeans2
+
+    X, _, init = S.clustered_profiles(500, 8, 5, spread=0.6, seed=4)
+    a, cent, it, _ = oracle.kmeans(X, init, 200)
+    c2, l2 = kmeans2(X.astype(np.float64), init.copy(), iter=it + 1, minit="matrix")
+    assert np.array_equal(a, l2)
+    assert np.allclose(cent, c2, rtol=1e-10, atol=1e-12)
+
+
+def test_kmeans_one_cluster_and_monotone_inertia():
+    X, _, init = S.clustered_profiles(300, 6, 4, spread=0.8, seed=5)
+    a, cent, it, _ = oracle.kmeans(X, X[:1].astype(np.float64), 10)
+    assert it == 1 and not a.any() and np.allclose(cent[0], X.astype(np.float64).mean(0), rtol=1e-12)
+    prev = np.inf
+    for m in range(1, 8):
+        inertia = oracle.kmeans(X, init, m)[3]
+        assert inertia <= prev * (1 + 1e-12)
+        prev = inertia
