@@ -66,10 +66,13 @@ def parse():
     ap.add_argument("--no-ablation", action="store_true", help="skip the lock-free (paper-faithful) ablation")
     ap.add_argument("--small", action="store_true",
                     help="a smaller problem of the same shape, 12M entries (for profiling)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
-                    help="bf16: time the BF16 tensor-core sweep at core 16x16x5 instead (for profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16_tc"],
+                    help="bf16 / bf16_tc: time the BF16-gather or the BF16 tensor-core sweep at core 16x16x5 "
+                         "instead (for profiling)")
     ap.add_argument("--serve-queries", type=int, default=20000, help="fold-in + top-k queries (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, queries/s")
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[5000.0, 10000.0, 20000.0, 40000.0],
+                    help="higher offered rates (queries/s) for the capacity sweep")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 vs BF16 refit at 16x16x5")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="entries of the batched form's cohorts times this (0: skip the batched form)")
@@ -211,6 +214,39 @@ def cpu_baseline(p, budget_s=15.0):
     return out
 
 
+def sweep_kernel_ab(p, snect, epochs=10):
+    """The two complete sweep kernels on the headline workload, from the same start: the
+    lane-group kernel (the default) against the warp-per-unit kernel (SNECT_SWEEP_KERNEL=warp);
+    ms per epoch (CUDA events around `epochs` epochs after one warm-up epoch) and test RMSE."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    out = {}
+    for name in ("lanes", "warp"):
+        if name == "warp":
+            os.environ["SNECT_SWEEP_KERNEL"] = "warp"
+        try:
+            c = snect.Snect(p.I, p.J, t(p.idx), t(p.val), t(p.edges), t(p.w), t(p.G0), [t(u) for u in p.U0],
+                            lam=p.lam, lam_g=p.lam_g, lr=p.lr, batch=0)
+        finally:
+            os.environ.pop("SNECT_SWEEP_KERNEL", None)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.epoch(1)
+        torch.cuda.synchronize()
+        e0.record(st)
+        c.epoch(epochs)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / epochs
+        out[name] = {"ms_per_epoch": ms, "nnz_updates_per_s": p.nnz / (ms / 1e3),
+                     "rmse_test_after_%d_epochs" % (epochs + 1): c.loss(t(p.test_idx), t(p.test_val))["rmse_test"]}
+        c.close()
+    out["lanes_vs_warp"] = out["warp"]["ms_per_epoch"] / out["lanes"]["ms_per_epoch"]
+    return out
+
+
 def kernel_breakdown(ctx, nnz, epochs):
     """Per-kernel device time of the epoch, live: `epochs` more epochs with CUDA events around
     every kernel launch (timing mode 2), read back after each epoch; ms per epoch and per
@@ -236,25 +272,10 @@ def kernel_breakdown(ctx, nnz, epochs):
     return out
 
 
-def serving(args, snect):
-    """Serving form: the paper-scale planted model at core 16 x 16 x 5 frozen on the device; a
-    Poisson stream of new-patient queries (5,000-75,000 observed cells, log-uniform) folded in
-    and searched (cosine top-10 over 4,500 patients) by the continuous-batching server.
-    Latency = submit to completion (host clock)."""
-    import snect_synth as S
-
-    m = S.serving_model()
-    I = tuple(u.shape[0] for u in m.U)
-    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
-    ctx = snect.Snect(I, m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32),
-                      np.zeros(0, np.float32), m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
-    pool_n = 256
-    pool = [S.serving_query(m, q=q) for q in range(pool_n)]  # distinct queries, resubmitted in turn
-    arrivals = S.poisson_arrivals(args.serve_queries, args.serve_rate)
-    srv = ctx.serve(n_slots=16, mem_budget_bytes=512 << 20, max_cells=75_000)
-    # warm-up: every query of the pool once (every kernel and size path loaded and touched)
-    for jk, x, _ in pool:
-        srv.poll(srv.submit(jk, x, 10), 10)
+def serve_stream(srv, pool, arrivals, k=10):
+    """Submits pool[q % len(pool)] at each arrival time (seconds from now) from a producer
+    thread and collects every result; returns (latencies ms, seconds from the first arrival
+    to the last result)."""
     tickets = [None] * len(arrivals)
     t0 = time.perf_counter()
 
@@ -263,8 +284,8 @@ def serving(args, snect):
             d = t0 + ta - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            jk, x, _ = pool[qi % pool_n]
-            tickets[qi] = srv.submit(jk, x, 10)
+            jk, x, _ = pool[qi % len(pool)]
+            tickets[qi] = srv.submit(jk, x, k)
 
     th = threading.Thread(target=producer)
     th.start()
@@ -272,23 +293,56 @@ def serving(args, snect):
     for qi in range(len(arrivals)):
         while tickets[qi] is None:
             time.sleep(0.0002)
-        _, _, _, l = srv.poll(tickets[qi], 10)
-        lat.append(l)
+        lat.append(srv.poll(tickets[qi], k)[3])
     t_end = time.perf_counter()
     th.join()
+    return np.array(lat), t_end - t0
+
+
+def serving(args, snect):
+    """Serving form: the paper-scale planted model at core 16 x 16 x 5 frozen on the device; a
+    Poisson stream of new-patient queries (5,000-75,000 observed cells, log-uniform) folded in
+    and searched (cosine top-10 over 4,500 patients) by the continuous-batching server.
+    Latency = submit to completion (host clock).  After the configured stream (2,000 queries/s),
+    shorter streams at higher offered rates find the capacity: achieved queries/s and p50/p99
+    at each rate."""
+    import snect_synth as S
+
+    sys.setswitchinterval(1e-4)  # the producer and collector threads hand the GIL over promptly
+    m = S.serving_model()
+    I = tuple(u.shape[0] for u in m.U)
+    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
+    ctx = snect.Snect(I, m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32),
+                      np.zeros(0, np.float32), m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
+    pool_n = 256
+    pool = [S.serving_query(m, q=q) for q in range(pool_n)]  # distinct queries, resubmitted in turn
+    srv = ctx.serve(n_slots=16, mem_budget_bytes=512 << 20, max_cells=75_000)
+    # warm-up: every query of the pool once (every kernel and size path loaded and touched)
+    for jk, x, _ in pool:
+        srv.poll(srv.submit(jk, x, 10), 10)
+    lat, dt = serve_stream(srv, pool, S.poisson_arrivals(args.serve_queries, args.serve_rate))
     st = srv.stats()
+    cells = np.array([len(pool[qi % pool_n][1]) for qi in range(len(lat))])
+    out = {"queries": int(len(lat)), "offered_qps": args.serve_rate,
+           "achieved_qps": len(lat) / dt, "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+           "mean_cells": float(cells.mean()), "slots": 16, "max_concurrent": st["max_concurrent"],
+           "mem_budget_bytes": 512 << 20,
+           "workload": "4500x15000x5 planted model, core 16x16x5, frozen; Poisson arrivals; queries of "
+                       "5,000-75,000 cells (log-uniform), %d distinct queries resubmitted in turn; "
+                       "closed-form ridge fold-in + cosine top-10; latency from submit to result" % pool_n,
+           "paper_context_ms_per_query": 550.0}
+    sweep = []
+    for rate in args.serve_sweep:
+        n = int(min(4 * rate, 20000))
+        lat, dt = serve_stream(srv, pool, S.poisson_arrivals(n, rate, seed=int(rate)))
+        sweep.append({"offered_qps": rate, "queries": n, "achieved_qps": n / dt,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))})
+    out["offered_rate_sweep"] = sweep
+    out["max_concurrent_over_sweep"] = srv.stats()["max_concurrent"]
     srv.stop()
     ctx.close()
-    lat = np.array(lat)
-    cells = np.array([len(pool[qi % pool_n][1]) for qi in range(len(arrivals))])
-    return {"queries": int(len(arrivals)), "offered_qps": args.serve_rate,
-            "achieved_qps": len(arrivals) / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-            "mean_cells": float(cells.mean()), "slots": 16, "max_concurrent": st["max_concurrent"],
-            "workload": "4500x15000x5 planted model, core 16x16x5, frozen; Poisson arrivals; queries of "
-                        "5,000-75,000 cells (log-uniform), %d distinct queries resubmitted in turn; "
-                        "closed-form ridge fold-in + cosine top-10; latency from submit to result" % pool_n,
-            "paper_context_ms_per_query": 550.0}
+    return out
 
 
 def precision_form(p, snect, epochs=10):
@@ -302,7 +356,7 @@ def precision_form(p, snect, epochs=10):
     dev = torch.device("cuda", torch.cuda.current_device())
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     out = {}
-    for name, prec in (("fp32", snect.FP32), ("bf16", snect.BF16)):
+    for name, prec in (("fp32", snect.FP32), ("bf16", snect.BF16), ("bf16_tc", snect.BF16_TC)):
         c = snect.Snect(p.I, (16, 16, 5), t(p.idx), t(p.val), t(p.edges), t(p.w), t(G0), [t(u) for u in U0],
                         lam=p.lam, lam_g=p.lam_g, lr=p.lr, batch=0, precision=prec)
         c.set_sweep_timing(1)
@@ -321,11 +375,13 @@ def precision_form(p, snect, epochs=10):
                      "sweep_kernel_ms_per_launch": sw_ms / max(sw_n, 1),
                      "rmse_test_after_%d_epochs" % epochs: l["rmse_test"]}
         c.close()
-    out["bf16_vs_fp32_throughput"] = out["bf16"]["nnz_updates_per_s"] / out["fp32"]["nnz_updates_per_s"]
     key = "rmse_test_after_%d_epochs" % epochs
-    out["bf16_rmse_relative_to_fp32"] = out["bf16"][key] / out["fp32"][key] - 1.0
-    out["workload"] = ("paper-scale tensor (27M train entries) refit at core 16x16x5, same start for both; "
-                       "%d epochs" % epochs)
+    for name in ("bf16", "bf16_tc"):
+        out["%s_vs_fp32_throughput" % name] = out[name]["nnz_updates_per_s"] / out["fp32"]["nnz_updates_per_s"]
+        out["%s_rmse_relative_to_fp32" % name] = out[name][key] / out["fp32"][key] - 1.0
+    out["workload"] = ("paper-scale tensor (27M train entries) refit at core 16x16x5, same start for all; "
+                       "%d epochs; bf16: gene rows gathered from their BF16 copy (lane-group sweep), bf16_tc: "
+                       "dense per-entry contractions on tcgen05" % epochs)
     return out
 
 
@@ -628,8 +684,8 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     snect.load(build_if_missing=True)
-    bf16 = args.precision == "bf16"
-    prec = snect.BF16 if bf16 else snect.FP32
+    bf16 = args.precision != "fp32"
+    prec = {"fp32": snect.FP32, "bf16": snect.BF16, "bf16_tc": snect.BF16_TC}[args.precision]
     p = make_problem(args.small, (16, 16, 5) if bf16 else (10, 10, 5))
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
@@ -716,7 +772,8 @@ def main():
                      "traffic": (SWEEP_DRAM_BYTES_PER_ENTRY * per_launch
                                  if (SWEEP_DRAM_BYTES_PER_ENTRY and not bf16 and tuple(p.J) == (10, 10, 5)) else None),
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 12M-entry case scaled by entries)",
-                     "kernel": "%s (one launch per wave)" % ("k_fast_sweep_tc" if bf16 else "k_fast_sweep"),
+                     "kernel": "%s (one launch per wave)" % {"fp32": "k_fast_sweep_lg", "bf16": "k_fast_sweep_lg (BF16 gathers)",
+                                                             "bf16_tc": "k_fast_sweep_tc"}[args.precision],
                      "bytes_per_unit": bytes_per_nnz, "units_per_launch": per_launch,
                      "peak_kind": pk_kind, "avg_launch_ms": (sw_ms / sw_n) if sw_n else None,
                      "timing": "CUDA events on the library's stream around every sweep launch of %d epochs "
@@ -730,6 +787,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0 and not args.no_ablation:
+        line["sweep_kernel_ab"] = sweep_kernel_ab(p, snect)
     if rank == 0 and not args.no_precision:
         line["precision_form"] = precision_form(p, snect)
         line["precision_form"]["config1_refit"] = precision_config1(snect)

@@ -41,6 +41,7 @@ extern "C" {
 
 #define SNECT_FP32 0
 #define SNECT_BF16 1
+#define SNECT_BF16_TC 2
 
 typedef struct snect_ctx snect_ctx;
 
@@ -56,9 +57,12 @@ typedef struct {
                           entries (<= 4096); 0: fast mode (lock-free sweep) */
     int32_t wave;      /* fast mode: entries between two updates of the core and the
                           platform factor (0 = library default) */
-    int32_t precision; /* SNECT_FP32, or SNECT_BF16: fast mode with J1, J2 in {16, 32}; the
-                          sweep's contractions run on the tensor cores with BF16 operands and
-                          FP32 accumulation, every factor stays FP32 */
+    int32_t precision; /* SNECT_FP32; SNECT_BF16: fast mode with J1, J2 in {16, 32}, the sweep
+                          gathers rows in BF16 (at 16 x 16 x 5 from a BF16 copy of the gene
+                          factor kept beside the FP32 one, arithmetic FP32; at the other ranks
+                          through the tensor-core form below); SNECT_BF16_TC: the same ranks,
+                          the dense per-entry contractions on the tensor cores with BF16
+                          operands and FP32 accumulation.  Every factor stays FP32. */
     uint64_t seed;     /* reserved; the caller supplies the visit order and the init */
 } snect_config;
 
@@ -128,16 +132,17 @@ int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n,
 int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, float *score_out);
 
 /* Continuous-batching service of fold-in + top-k queries (Eq. 9 and Sec. 3.2.1 on a stream
- * of new patients).  snect_serve_start builds the (gene, platform) table of the frozen factors
- * and n_slots slots (one CUDA stream, pinned staging and device buffers for max_cells cells
- * each).  A scheduler thread admits queued requests oldest first whenever a slot is free and
- * the device bytes of the requests in flight plus the next one stay within mem_budget_bytes
- * (a request of n cells counts 12 n + 4 ceil(n / 4096) (J1^2 + J1) bytes: its cells and its
- * Gram partials);
- * admitted requests run concurrently on their slots' streams.  A request's result does not
- * depend on what else is running.  While a server runs, the context must not be trained or
- * have its factors set.  Errors: SNECT_EINVAL (sizes, budget below one largest request),
- * SNECT_ENOMEM. */
+ * of new patients).  snect_serve_start builds the (gene, platform) table of the frozen factors,
+ * one device arena of exactly mem_budget_bytes, and n_slots slots (a CUDA stream, pinned host
+ * staging for max_cells cells, and small fixed device buffers: the fold-in row, I1 scores and
+ * flags, the top-k).  A scheduler thread admits queued requests oldest first whenever a slot
+ * is free and the request's device memory -- its cells and its Gram partials, 256-byte aligned:
+ * about 12 n + 4 ceil(n / 4096) (J1^2 + J1) bytes for n cells -- can be carved out of the arena;
+ * so the requests in flight never hold more device memory than the budget.  Admitted requests
+ * run concurrently on their slots' streams; a host callback on each slot's stream hands the
+ * finished request back to the scheduler.  A request's result does not depend on what else is
+ * running.  While a server runs, the context must not be trained or have its factors set.
+ * Errors: SNECT_EINVAL (sizes, budget below one largest request), SNECT_ENOMEM. */
 typedef struct snect_server snect_server;
 int snect_serve_start(snect_ctx *ctx, int32_t n_slots, int64_t mem_budget_bytes, int32_t max_cells,
                       snect_server **out);

@@ -19,10 +19,11 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Config", "LossTerms", "Snect", "SnectError", "load", "lib_path", "EXPORTS", "FP32", "BF16"]
+__all__ = ["Config", "LossTerms", "Snect", "SnectError", "load", "lib_path", "EXPORTS", "FP32", "BF16", "BF16_TC"]
 
 FP32 = 0
 BF16 = 1
+BF16_TC = 2
 
 # every symbol include/snect.h declares
 EXPORTS = (

@@ -106,11 +106,11 @@ int check_config(const snect_config *cfg, std::string *why) {
     if (!isfinite(cfg->lr) || cfg->lr <= 0.f) return *why = "lr must be finite and > 0", SNECT_EINVAL;
     if (cfg->batch < 0 || cfg->batch > kMaxBatch) return *why = "batch must be in [0, 4096]", SNECT_EINVAL;
     if (cfg->wave < 0) return *why = "wave must be >= 0", SNECT_EINVAL;
-    if (cfg->precision != SNECT_FP32 && cfg->precision != SNECT_BF16)
-        return *why = "precision must be SNECT_FP32 or SNECT_BF16", SNECT_EINVAL;
-    if (cfg->precision == SNECT_BF16 &&
+    if (cfg->precision != SNECT_FP32 && cfg->precision != SNECT_BF16 && cfg->precision != SNECT_BF16_TC)
+        return *why = "precision must be SNECT_FP32, SNECT_BF16 or SNECT_BF16_TC", SNECT_EINVAL;
+    if (cfg->precision != SNECT_FP32 &&
         (cfg->batch != 0 || (cfg->J[0] != 16 && cfg->J[0] != 32) || (cfg->J[1] != 16 && cfg->J[1] != 32)))
-        return *why = "SNECT_BF16 needs fast mode (batch = 0) and J1, J2 in {16, 32}", SNECT_EINVAL;
+        return *why = "SNECT_BF16 and SNECT_BF16_TC need fast mode (batch = 0) and J1, J2 in {16, 32}", SNECT_EINVAL;
     return SNECT_OK;
 }
 
@@ -135,7 +135,9 @@ int enqueue_epoch(Ctx *c) {
     if (rc) return rc;
     if ((rc = aux_event(c, 2, false))) return rc;
     SNECT_CUDA(c, launch_edge_pass(c));
-    return aux_event(c, 2, true);
+    if ((rc = aux_event(c, 2, true))) return rc;
+    SNECT_CUDA(c, refresh_bf16_rows(c));  // the pass moved gene rows
+    return SNECT_OK;
 }
 
 // one epoch captured once into a CUDA graph (on a private stream: capture is not allowed on
@@ -401,6 +403,7 @@ int snect_edge_pass(snect_ctx *h) {
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c) return SNECT_EINVAL;
     SNECT_CUDA(c, launch_edge_pass(c));
+    SNECT_CUDA(c, refresh_bf16_rows(c));
     c->param_version++;
     return SNECT_OK;
 }
@@ -440,7 +443,7 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     if (d_val) cudaFreeAsync(d_val, c->stream);
     if (trec) cudaFreeAsync(trec, c->stream);
     if (rc) return rc;
-    if (c->cfg.precision == SNECT_BF16) {  // a tensor-core wait that gave up
+    if (c->sweep_kind < 0) {  // a tensor-core wait that gave up
         int32_t tc_err = 0;
         SNECT_CUDA(c, cudaMemcpy(&tc_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
         if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a tensor-core completion wait timed out in the sweep");
@@ -477,6 +480,7 @@ int snect_qr_post(snect_ctx *h, int32_t *skipped_modes) {
     int skipped = 0;
     const int rc = qr_post(c, &skipped);
     if (skipped_modes) *skipped_modes = skipped;
+    if (rc == SNECT_OK) SNECT_CUDA(c, refresh_bf16_rows(c));
     return rc;
 }
 
@@ -492,6 +496,7 @@ int snect_set_factors(snect_ctx *h, const float *G, const float *U1, const float
                                       c->stream));
     if (U3)
         SNECT_CUDA(c, cudaMemcpyAsync(c->U[2], U3, sizeof(float) * d.I3 * d.J3, cudaMemcpyDefault, c->stream));
+    if (U2) SNECT_CUDA(c, refresh_bf16_rows(c));
     SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->param_version++;
     return SNECT_OK;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libsnect.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,6 +85,11 @@ struct Ctx {
     // before genes in each wave (null: the sweep counts with atomics instead)
     float *wcnt = nullptr;
     float *curv = nullptr;          // platform curvatures of the row steps (two buffers)
+    // which sweep kernel runs (1 lane-group FP32, 2 lane-group with BF16 gene rows, 0 the
+    // warp-per-unit or per-entry kernel, -1 the tensor-core kernel) and, for 2, the BF16
+    // copy of the gene factor it gathers from (kept current by every writer of U2)
+    int32_t sweep_kind = 0;
+    __nv_bfloat16 *U2h = nullptr;
     // fold-in / top-k
     float *wtable = nullptr;        // I2*I3*J1: w_jk = G x2 u2_j x3 u3_k
     int64_t param_version = 0;      // bumped whenever G or a factor may have changed
@@ -179,6 +185,7 @@ int prep_det_groups(Ctx *c);
 int prep_fast_tiles(Ctx *c);       // prep.cu: groups each wave's entries by platform, tiles
 int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of the fast sweep
 int enqueue_fast_epoch(Ctx *c);
+cudaError_t refresh_bf16_rows(Ctx *c);  // U2 -> its BF16 copy, when the context keeps one
 // the entry sweep of one wave alone, its accumulators copied out (snect_wave_grads)
 int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB);
 void free_fast(Ctx *c);

@@ -2,13 +2,16 @@
 //
 // Requests (a new patient's observed (gene, platform, value) cells) are submitted from any
 // host thread and copied into a host queue.  One scheduler thread admits queued requests,
-// oldest first, whenever a slot is free and the bytes of the requests already on the GPU plus
-// this one stay within the device-memory budget; requests that arrive while others are
-// running are admitted as soon as slots and memory free up.  Each slot owns a CUDA stream,
-// pinned staging buffers and device buffers sized for the largest query, so admitted requests
+// oldest first, whenever a slot is free and the request's device memory -- its cells and its
+// fold-in partial sums -- can be carved out of the server's arena, one device allocation of
+// exactly the memory budget made at start; requests that arrive while others are running are
+// admitted as soon as slots and arena space free up.  So the budget bounds the device memory
+// the requests in flight really use.  Each slot owns a CUDA stream, pinned staging buffers
+// and small fixed buffers (the fold-in row, the scores, the top-k), so admitted requests
 // overlap on the device.  Per request the slot stream runs: copy in -> cell check -> fold-in
 // partials (fixed CTA partition) -> FP64 Cholesky solve -> cosine scores -> top-k -> copy out,
-// then records an event; the scheduler polls the events and publishes finished results.
+// then a host callback on that stream marks the slot finished and wakes the scheduler, which
+// publishes the result, returns the arena space and admits the next requests (no polling).
 // The kernels and their partition depend only on the request, so a request's result is the
 // same alone and in any mix.
 #include <atomic>
@@ -16,6 +19,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -27,6 +31,7 @@
 namespace snect {
 
 int ensure_wtable_for_serving(Ctx *c);  // api.cu
+struct Server;
 
 namespace {
 
@@ -50,6 +55,8 @@ struct Result {
 };
 
 struct Slot {
+    Server *srv = nullptr;
+    int index = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     int32_t *h_jk = nullptr;  // pinned
@@ -58,13 +65,14 @@ struct Slot {
     int32_t *h_idx = nullptr;
     float *h_score = nullptr;
     int32_t *h_flag = nullptr;
-    int2 *d_jk = nullptr;
-    float *d_val = nullptr, *d_part = nullptr, *d_u = nullptr, *d_score = nullptr, *d_top_s = nullptr;
+    int2 *d_jk = nullptr;  // carved from the arena per request
+    float *d_val = nullptr, *d_part = nullptr;
+    float *d_u = nullptr, *d_score = nullptr, *d_top_s = nullptr;
     int32_t *d_status = nullptr, *d_top_i = nullptr, *d_flag = nullptr;
     uint8_t *d_taken = nullptr;
     bool busy = false;
     Request req;
-    int64_t bytes = 0;
+    int64_t bytes = 0, arena_off = -1;
     Clock::time_point t_admit;
 };
 
@@ -75,6 +83,10 @@ struct Server {
     int32_t max_cells = 0;
     int64_t budget = 0;
     int64_t in_flight_bytes = 0;
+    char *arena = nullptr;                 // the budget: one device allocation
+    std::map<int64_t, int64_t> free_blocks;  // arena offset -> bytes, coalesced
+    std::vector<int> finished;             // slots whose stream work has completed
+    bool kick = false;                     // a request was submitted since the scheduler last looked
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv_submit, cv_done;
@@ -89,9 +101,43 @@ struct Server {
 
 namespace {
 
+constexpr int64_t kArenaAlign = 256;
+
+int64_t align_up(int64_t x) { return (x + kArenaAlign - 1) / kArenaAlign * kArenaAlign; }
+
+// arena bytes of a request of n cells: its (gene, platform) pairs, values and the fold-in's
+// per-CTA partial sums, each 256-byte aligned
 int64_t request_bytes(const Ctx *c, int64_t n) {
-    return n * (int64_t)(sizeof(int2) + sizeof(float)) +
-           foldin_parts(n) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1) * (int64_t)sizeof(float);
+    return align_up(n * (int64_t)sizeof(int2)) + align_up(n * (int64_t)sizeof(float)) +
+           align_up(foldin_parts(n) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1) * (int64_t)sizeof(float));
+}
+
+// first fit in the arena (scheduler thread, under the server lock); -1 if no block is large enough
+int64_t arena_alloc(Server *S, int64_t bytes) {
+    for (auto it = S->free_blocks.begin(); it != S->free_blocks.end(); ++it) {
+        if (it->second < bytes) continue;
+        const int64_t off = it->first, rest = it->second - bytes;
+        S->free_blocks.erase(it);
+        if (rest > 0) S->free_blocks[off + bytes] = rest;
+        return off;
+    }
+    return -1;
+}
+
+void arena_free(Server *S, int64_t off, int64_t bytes) {
+    auto it = S->free_blocks.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != S->free_blocks.end() && it->first + it->second == nx->first) {  // merge with the next
+        it->second += nx->second;
+        S->free_blocks.erase(nx);
+    }
+    if (it != S->free_blocks.begin()) {  // and with the previous
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            S->free_blocks.erase(it);
+        }
+    }
 }
 
 void free_slot(Slot &s) {
@@ -102,9 +148,6 @@ void free_slot(Slot &s) {
     cudaFreeHost(s.h_idx);
     cudaFreeHost(s.h_score);
     cudaFreeHost(s.h_flag);
-    cudaFree(s.d_jk);
-    cudaFree(s.d_val);
-    cudaFree(s.d_part);
     cudaFree(s.d_u);
     cudaFree(s.d_score);
     cudaFree(s.d_top_s);
@@ -117,8 +160,9 @@ void free_slot(Slot &s) {
     s = Slot();
 }
 
+// the slot's stream, events, pinned staging for max_cells cells and its small fixed device
+// buffers; the request's cells and partials come from the arena at admission
 cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
-    const int64_t parts = foldin_parts(max_cells) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1);
     cudaError_t e;
 #define TRY(x)                         \
     if ((e = (x)) != cudaSuccess) return e;
@@ -130,9 +174,6 @@ cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
     TRY(cudaMallocHost((void **)&s.h_idx, sizeof(int32_t) * 64));
     TRY(cudaMallocHost((void **)&s.h_score, sizeof(float) * 64));
     TRY(cudaMallocHost((void **)&s.h_flag, sizeof(int32_t) * 2));
-    TRY(cudaMalloc((void **)&s.d_jk, sizeof(int2) * max_cells));
-    TRY(cudaMalloc((void **)&s.d_val, sizeof(float) * max_cells));
-    TRY(cudaMalloc((void **)&s.d_part, sizeof(float) * parts));
     TRY(cudaMalloc((void **)&s.d_u, sizeof(float) * kMaxRank));
     TRY(cudaMalloc((void **)&s.d_score, sizeof(float) * c->d.I1));
     TRY(cudaMalloc((void **)&s.d_top_s, sizeof(float) * 64));
@@ -144,10 +185,27 @@ cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
     return cudaSuccess;
 }
 
-// launches one request on its slot (scheduler thread)
+// runs on the CUDA driver's callback thread once a slot's stream work is done: no CUDA
+// calls here, only the hand-over to the scheduler
+void CUDART_CB on_slot_done(void *p) {
+    Slot *s = static_cast<Slot *>(p);
+    Server *S = s->srv;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->finished.push_back(s->index);
+    }
+    S->cv_submit.notify_all();
+}
+
+// launches one request on its slot (scheduler thread); its device buffers start at arena_off
 cudaError_t launch_request(Ctx *c, Slot &s) {
     const Request &r = s.req;
     const int64_t n = (int64_t)r.val.size();
+    char *base = s.srv->arena + s.arena_off;
+    s.d_jk = reinterpret_cast<int2 *>(base);
+    s.d_val = reinterpret_cast<float *>(base + align_up(n * (int64_t)sizeof(int2)));
+    s.d_part = reinterpret_cast<float *>(base + align_up(n * (int64_t)sizeof(int2)) +
+                                         align_up(n * (int64_t)sizeof(float)));
     std::memcpy(s.h_jk, r.jk.data(), sizeof(int32_t) * 2 * n);
     std::memcpy(s.h_val, r.val.data(), sizeof(float) * n);
     cudaError_t e;
@@ -164,7 +222,8 @@ cudaError_t launch_request(Ctx *c, Slot &s) {
     if ((e = cudaMemcpyAsync(s.h_flag, s.d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream))) return e;
     if ((e = cudaMemcpyAsync(s.h_flag + 1, s.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream)))
         return e;
-    return cudaEventRecord(s.done, s.stream);
+    if ((e = cudaEventRecord(s.done, s.stream))) return e;
+    return cudaLaunchHostFunc(s.stream, on_slot_done, &s);
 }
 
 void scheduler(Server *S) {
@@ -172,11 +231,36 @@ void scheduler(Server *S) {
     cudaSetDevice(c->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
-        // admit: oldest first, while a slot is free and the budget allows
-        bool progressed = false;
+        // retire the slots whose stream work has completed (handed over by on_slot_done)
+        std::vector<int> fin;
+        fin.swap(S->finished);
+        for (int i : fin) {
+            Slot &s = S->slots[i];
+            Result res;
+            const auto now = Clock::now();
+            res.latency_ms = std::chrono::duration<double, std::milli>(now - s.req.t_submit).count();
+            res.queue_ms = std::chrono::duration<double, std::milli>(s.t_admit - s.req.t_submit).count();
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q != cudaSuccess) {
+                res.status = SNECT_ECUDA;
+                S->err = std::string("serving: ") + cudaGetErrorString(q);
+            } else if (s.h_flag[0] || s.h_flag[1]) {
+                res.status = SNECT_EINVAL;
+            } else {
+                res.u.assign(s.h_u, s.h_u + c->d.J1);
+                res.idx.assign(s.h_idx, s.h_idx + s.req.k);
+                res.score.assign(s.h_score, s.h_score + s.req.k);
+            }
+            S->done[s.req.ticket] = std::move(res);
+            s.busy = false;
+            arena_free(S, s.arena_off, s.bytes);
+            s.arena_off = -1;
+            S->in_flight_bytes -= s.bytes;
+            S->completed++;
+        }
+        if (!fin.empty()) S->cv_done.notify_all();
+        // admit: oldest first, while a slot is free and the arena has room
         while (!S->queue.empty()) {
-            const int64_t need = request_bytes(c, (int64_t)S->queue.front().val.size());
-            if (S->in_flight_bytes > 0 && S->in_flight_bytes + need > S->budget) break;
             int free_slot_i = -1;
             for (size_t i = 0; i < S->slots.size(); ++i)
                 if (!S->slots[i].busy) {
@@ -184,11 +268,15 @@ void scheduler(Server *S) {
                     break;
                 }
             if (free_slot_i < 0) break;
+            const int64_t need = request_bytes(c, (int64_t)S->queue.front().val.size());
+            const int64_t off = arena_alloc(S, need);
+            if (off < 0) break;  // wait for requests in flight to return their memory
             Slot &s = S->slots[free_slot_i];
             s.req = std::move(S->queue.front());
             S->queue.pop_front();
             s.busy = true;
             s.bytes = need;
+            s.arena_off = off;
             s.t_admit = Clock::now();
             S->in_flight_bytes += need;
             S->admitted++;
@@ -198,57 +286,25 @@ void scheduler(Server *S) {
             lk.unlock();
             cudaError_t e = launch_request(c, s);
             lk.lock();
-            if (e != cudaSuccess) {
+            if (e != cudaSuccess) {  // nothing of it will complete: retire it here
                 Result res;
                 res.status = SNECT_ECUDA;
                 S->done[s.req.ticket] = std::move(res);
                 S->err = std::string("serving launch: ") + cudaGetErrorString(e);
+                cudaStreamSynchronize(s.stream);
                 s.busy = false;
+                arena_free(S, s.arena_off, s.bytes);
+                s.arena_off = -1;
                 S->in_flight_bytes -= s.bytes;
                 S->cv_done.notify_all();
             }
-            progressed = true;
-        }
-        // retire finished requests
-        for (auto &s : S->slots) {
-            if (!s.busy) continue;
-            const cudaError_t q = cudaEventQuery(s.done);
-            if (q == cudaErrorNotReady) continue;
-            Result res;
-            const auto now = Clock::now();
-            res.latency_ms = std::chrono::duration<double, std::milli>(now - s.req.t_submit).count();
-            res.queue_ms = std::chrono::duration<double, std::milli>(s.t_admit - s.req.t_submit).count();
-            if (q != cudaSuccess) {
-                res.status = SNECT_ECUDA;
-                S->err = std::string("serving: ") + cudaGetErrorString(q);
-            } else if (s.h_flag[0]) {
-                res.status = SNECT_EINVAL;
-            } else if (s.h_flag[1]) {
-                res.status = SNECT_EINVAL;
-            } else {
-                res.u.assign(s.h_u, s.h_u + c->d.J1);
-                res.idx.assign(s.h_idx, s.h_idx + s.req.k);
-                res.score.assign(s.h_score, s.h_score + s.req.k);
-            }
-            S->done[s.req.ticket] = std::move(res);
-            s.busy = false;
-            S->in_flight_bytes -= s.bytes;
-            S->completed++;
-            progressed = true;
-            S->cv_done.notify_all();
         }
         bool any_busy = false;
         for (auto &s : S->slots) any_busy |= s.busy;
         if (S->stop.load() && S->queue.empty() && !any_busy) break;
-        if (!progressed) {
-            if (any_busy) {  // poll the GPU again shortly
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
-                lk.lock();
-            } else {
-                S->cv_submit.wait_for(lk, std::chrono::milliseconds(5));
-            }
-        }
+        // sleep until a completion, a new submission (it may be admissible) or stop
+        S->cv_submit.wait(lk, [&] { return !S->finished.empty() || S->kick || S->stop.load(); });
+        S->kick = false;
     }
 }
 
@@ -276,11 +332,22 @@ int snect_serve_start(snect_ctx *h, int32_t n_slots, int64_t mem_budget_bytes, i
     S->c = c;
     S->max_cells = max_cells;
     S->budget = mem_budget_bytes;
+    cudaError_t ea = cudaMalloc((void **)&S->arena, (size_t)mem_budget_bytes);
+    if (ea != cudaSuccess) {
+        delete S;
+        cudaGetLastError();
+        return fail(c, SNECT_ENOMEM, std::string("serving arena: ") + cudaGetErrorString(ea));
+    }
+    S->free_blocks[0] = mem_budget_bytes;
     S->slots.resize(n_slots);
-    for (auto &s : S->slots) {
+    for (int i = 0; i < n_slots; ++i) {
+        Slot &s = S->slots[i];
         cudaError_t e = alloc_slot(c, s, max_cells);
+        s.srv = S;
+        s.index = i;
         if (e != cudaSuccess) {
             for (auto &x : S->slots) free_slot(x);
+            cudaFree(S->arena);
             delete S;
             cudaGetLastError();
             return fail(c, SNECT_ENOMEM, std::string("serving slot: ") + cudaGetErrorString(e));
@@ -308,8 +375,9 @@ int snect_serve_submit(snect_server *h, const int32_t *jk, const float *val, int
         r.ticket = S->next_ticket++;
         *ticket = r.ticket;
         S->queue.push_back(std::move(r));
+        S->kick = true;
     }
-    S->cv_submit.notify_one();
+    S->cv_submit.notify_all();
     return SNECT_OK;
 }
 
@@ -348,10 +416,14 @@ int snect_serve_stats(snect_server *h, int64_t *admitted, int64_t *completed, in
 int snect_serve_stop(snect_server *h) {
     Server *S = reinterpret_cast<Server *>(h);
     if (!S) return SNECT_EINVAL;
-    S->stop.store(true);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop.store(true);
+    }
     S->cv_submit.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto &s : S->slots) free_slot(s);
+    cudaFree(S->arena);
     delete S;
     return SNECT_OK;
 }

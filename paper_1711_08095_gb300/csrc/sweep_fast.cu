@@ -32,6 +32,9 @@
 //   dc_k[r] = sum_pq g_pqr M_k[p,q] + n_k lambda/|Omega^{3,k}| c_k[r].
 // M_k is accumulated per CTA in registers over staged tiles (one thread per 2 x 2 block and
 // entry slice) and merged into global memory once per platform change.
+#include <stdlib.h>
+#include <string.h>
+
 #include "contract.cuh"
 #include "tc.cuh"
 
@@ -100,6 +103,8 @@ struct FastArgs {
     int32_t *err;      // set when a tensor-core wait gives up
     DenseArgs pre;     // the wave's dense pre-work (the first CTAs of the launch)
     int32_t count_atomics;  // 1: count each row's entries per platform with atomics (no table)
+    int64_t e_first, e_count;  // the wave's entries: positions [e_first, e_first + e_count) of rec
+    const __nv_bfloat16 *U2h;  // BF16 copy of the gene factor (the BF16-gather sweep)
 };
 
 // The wave-independent half of the dense step; part 0, 1, 2 split it over three CTAs, -1
@@ -712,6 +717,249 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Lane-group sweep (compile-time J1, J2 <= 16, every platform's Gc in shared memory, per-wave
+// row counts from the set-up table).
+//
+// The same per-patient-run factoring as warp_runs (w2 = Gc^T a_i once per run, per entry
+// x~ = w2 . b, r = x~ - x, g(b) += r w2, s += r b; per run g(a_i) += Gc s, M_k += a_i s^T), but
+// one entry is handled by a group of L = J2 / VEC lanes, each holding VEC consecutive
+// components of b, w2 and s: a warp takes E = 32 / L entries per step.  A gene row is then
+// gathered as L contiguous vector loads (whole 32-byte sectors) instead of one lane walking it,
+// its gradient leaves as L contiguous vector reductions, x~ is an L-lane shuffle sum, and s
+// stays in each lane's registers until the run closes, when one reduction over the E entry
+// slots completes it.  Each warp walks one contiguous range of the wave's entries (sorted by
+// platform, then patient), so no tile claim and no CTA barrier sit in the loop; a run cut by a
+// range boundary is closed by both warps, each adding its part (every sum is linear).
+//
+// GB = 1 gathers the gene rows from a BF16 copy of U2 (VEC = 4 BF16 = 8 bytes per lane); all
+// arithmetic, the gradients and the factors stay FP32.
+
+template <int CJ2, int GB>
+struct LaneGroup {
+    static constexpr int VEC = (GB || CJ2 % 4 == 0) ? 4 : (CJ2 % 2 == 0 ? 2 : 1);
+    static constexpr int L = CJ2 / VEC;  // lanes per entry
+    static constexpr int E = 32 / L;     // entries per step
+};
+
+// sum of x over the L lanes of this lane's group (lanes g L .. g L + L - 1); every lane of the
+// group gets the same value.  All 32 lanes call this.
+template <int L>
+__device__ __forceinline__ float group_sum(float x) {
+    constexpr unsigned FULL = 0xffffffffu;
+    if constexpr ((L & (L - 1)) == 0) {
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(FULL, x, o);
+        return x;
+    } else {
+        const int base = ((threadIdx.x & 31) / L) * L;
+        float t = 0.f;
+#pragma unroll
+        for (int mm = 0; mm < L; ++mm) t += __shfl_sync(FULL, x, base + mm);
+        return t;
+    }
+}
+
+// sum of x over the E entry slots (lanes m, m + L, m + 2L, ...) of this lane's component
+// group m; every lane of the component group gets the same value.  All 32 lanes call this.
+template <int L, int E>
+__device__ __forceinline__ float slot_sum(float x) {
+    constexpr unsigned FULL = 0xffffffffu;
+    if constexpr (L * E == 32 && (L & (L - 1)) == 0) {
+#pragma unroll
+        for (int o = L; o < 32; o <<= 1) x += __shfl_xor_sync(FULL, x, o);
+        return x;
+    } else {
+        const int m = (threadIdx.x & 31) % L;
+        float t = 0.f;
+#pragma unroll
+        for (int g = 0; g < E; ++g) t += __shfl_sync(FULL, x, g * L + m);
+        return t;
+    }
+}
+
+// CTAs per SM the lane-group kernel's registers are cut for (its first CTAs also run the
+// dense pre-work, whose 16 x 16 eigen-solves need more than 64 registers)
+template <int CJ1, int CJ2>
+constexpr int lg_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
+
+template <int CJ1, int CJ2, int CJ3, int GB>
+__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fast_sweep_lg(FastArgs A) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int J1 = CJ1, J2 = CJ2, J3 = CJ3, Q = J1 * J2, PI = Q * J3;
+    using LG = LaneGroup<CJ2, GB>;
+    constexpr int VEC = LG::VEC, L = LG::L, E = LG::E;
+    constexpr int NM = (Q + 31) / 32;  // M_k elements per lane
+    extern __shared__ __align__(16) float sm[];
+    if (blockIdx.x < kPreCtas) {  // the wave's dense pre-work, as in k_fast_sweep
+        dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
+        return;
+    }
+    // per warp: the open run's patient row a (floats 0-31) and, when it closes, s (32-63)
+    __shared__ __align__(16) float sSlot[kFastThreads / 32][64];
+    const int I3 = A.d.I3;
+    float *sG = sm;                       // PI
+    float *sGcAll = sG + align4(PI);      // I3 x Q: Gc_k = G x3 c_k
+    float *sMacc = sGcAll + I3 * Q;       // I3 x Q: this CTA's M_k
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int s = tid; s < PI; s += kFastThreads) sG[s] = A.G[s];
+    __syncthreads();
+    for (int s = tid; s < I3 * Q; s += kFastThreads) {
+        const int kk = s / Q, pq = s % Q;
+        float g = 0.f;
+#pragma unroll
+        for (int r = 0; r < J3; ++r) g = fmaf(sG[pq * J3 + r], A.U3[(int64_t)kk * J3 + r], g);
+        sGcAll[s] = g;
+        sMacc[s] = 0.f;
+    }
+    __syncthreads();
+    float *slot = sSlot[warp];
+    const int g = lane / L, m = lane % L;  // entry slot and component group of this lane
+    const bool act = g < E;
+    const int64_t W = (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32);
+    const int64_t w = (int64_t)(blockIdx.x - kPreCtas) * (kFastThreads / 32) + warp;
+    const int64_t lo = A.e_first + w * A.e_count / W, hi = A.e_first + (w + 1) * A.e_count / W;
+    float mreg[NM];
+#pragma unroll
+    for (int t = 0; t < NM; ++t) mreg[t] = 0.f;
+    int mk = -1, ci = -1, ck = -1;  // platform of mreg; the open run (patient, platform)
+    float w2v[VEC], sv[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) w2v[v] = sv[v] = 0.f;
+    auto flush_m = [&]() {  // this warp's M_k shares into the CTA's M
+        if (mk < 0) return;
+#pragma unroll
+        for (int t = 0; t < NM; ++t) {
+            const int idx = lane + 32 * t;
+            if (idx < Q && mreg[t] != 0.f) atomicAdd(sMacc + mk * Q + idx, mreg[t]);
+            mreg[t] = 0.f;
+        }
+    };
+    auto close_run = [&]() {
+        float st[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) st[v] = slot_sum<L, E>(sv[v]);
+        if (lane < L)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) slot[32 + m * VEC + v] = st[v];
+        __syncwarp();
+        if (lane < J1) {  // patient gradient (Gc s)[p], p = lane
+            const float *gc = sGcAll + ck * Q + lane * J2;
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < J2; ++q) acc = fmaf(gc[q], slot[32 + q], acc);
+            atomicAdd(A.gA + (int64_t)ci * A.rs1 + lane, acc);
+        }
+#pragma unroll
+        for (int t = 0; t < NM; ++t) {  // M_k += a s^T
+            const int idx = lane + 32 * t;
+            if (idx < Q) mreg[t] = fmaf(slot[idx / J2], slot[32 + idx % J2], mreg[t]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) sv[v] = 0.f;
+    };
+    auto open_run = [&](int i, int k) {
+        if (k != mk) {
+            flush_m();
+            mk = k;
+        }
+        ci = i;
+        ck = k;
+        if (lane < J1) slot[lane] = __ldg(A.U1 + (int64_t)i * J1 + lane);
+        __syncwarp();
+        const float *gc = sGcAll + k * Q;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {  // w2 = Gc^T a, components m VEC + v
+            float acc = 0.f;
+#pragma unroll
+            for (int p = 0; p < J1; ++p) acc = fmaf(gc[p * J2 + m * VEC + v], slot[p], acc);
+            w2v[v] = acc;
+        }
+    };
+    auto load_rec = [&](int64_t e, bool ok) {
+        Rec r;
+        r.i = r.j = r.k = -1;
+        r.x = 0.f;
+        if (ok) {  // streamed once per epoch: evict-first
+            const int4 v = __ldcs(reinterpret_cast<const int4 *>(A.rec + e));
+            r.i = v.x;
+            r.j = v.y;
+            r.k = v.z;
+            r.x = __int_as_float(v.w);
+        }
+        return r;
+    };
+    Rec nxt = load_rec(lo + g, act && lo + g < hi);
+    for (int64_t base = lo; base < hi; base += E) {
+        const int64_t e = base + g;
+        const bool valid = act && e < hi;
+        const Rec cur = nxt;
+        nxt = load_rec(e + E, act && e + E < hi);  // one step ahead
+        float b[VEC];
+        if (valid) {
+            if constexpr (GB) {
+                const uint2 h = __ldg(reinterpret_cast<const uint2 *>(A.U2h + (int64_t)cur.j * J2 + m * VEC));
+                const float2 lo2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.x));
+                const float2 hi2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.y));
+                b[0] = lo2.x;
+                b[1] = lo2.y;
+                b[2] = hi2.x;
+                b[3] = hi2.y;
+            } else if constexpr (VEC == 4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4 *>(A.U2 + (int64_t)cur.j * J2 + m * VEC));
+                b[0] = t4.x;
+                b[1] = t4.y;
+                b[2] = t4.z;
+                b[3] = t4.w;
+            } else if constexpr (VEC == 2) {
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(A.U2 + (int64_t)cur.j * J2 + m * VEC));
+                b[0] = t2.x;
+                b[1] = t2.y;
+            } else {
+                b[0] = __ldg(A.U2 + (int64_t)cur.j * J2 + m);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) b[v] = 0.f;
+        }
+        // the step's entries by run (one pass when the step lies inside one run)
+        unsigned pend = __ballot_sync(FULL, valid && m == 0);
+        while (pend) {
+            const int lead = __ffs(pend) - 1;
+            const int ri = __shfl_sync(FULL, cur.i, lead), rk = __shfl_sync(FULL, cur.k, lead);
+            if (ri != ci || rk != ck) {
+                if (ci >= 0) close_run();
+                open_run(ri, rk);
+            }
+            const bool mine = valid && cur.i == ci && cur.k == ck;
+            pend &= ~__ballot_sync(FULL, mine && m == 0);
+            float part = 0.f;
+            if (mine)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) part = fmaf(w2v[v], b[v], part);
+            const float xt = group_sum<L>(part);
+            if (mine) {
+                const float r = xt - cur.x;
+                float *gb = A.gB + (int64_t)cur.j * A.rs2 + m * VEC;
+                if constexpr (VEC == 4)
+                    atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
+                else if constexpr (VEC == 2)
+                    atomicAdd(reinterpret_cast<float2 *>(gb), make_float2(r * w2v[0], r * w2v[1]));
+                else
+                    atomicAdd(gb, r * w2v[0]);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) sv[v] = fmaf(r, b[v], sv[v]);
+            }
+        }
+    }
+    if (ci >= 0) close_run();
+    flush_m();
+    __syncthreads();
+    for (int s = tid; s < I3 * Q; s += kFastThreads)
+        if (sMacc[s] != 0.f) atomicAdd(A.macc + s, sMacc[s]);
+}
+
 // The sweep of one wave over every problem of a batch: the same tile work as k_fast_sweep;
 // the CTAs claim tiles from the concatenated tile lists of all problems (toff: prefix
 // offsets) and switch problem (arguments and core in shared memory) between tiles.
@@ -1223,7 +1471,8 @@ template <int CJ>
 __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, float *__restrict__ g, int32_t RS,
                                  const int32_t *__restrict__ cnt, int32_t I, int32_t I3, float lam,
                                  float inv_lr, float inv_n, const float *__restrict__ Ckg,
-                                 float *__restrict__ gram_out, const float *__restrict__ wc, float *sm) {
+                                 float *__restrict__ gram_out, const float *__restrict__ wc, float *sm,
+                                 __nv_bfloat16 *__restrict__ Uh = nullptr) {
     constexpr int J = CJ, JP = (J + 3) & ~3, NL = J * (J + 1) / 2, NLP = (NL + 3) & ~3, JE = (J + 1) & ~1;
     const int64_t r0 = (int64_t)blk * kRowsPerThreadCta;
     if (r0 >= I) return;
@@ -1351,6 +1600,16 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
             } else {
 #pragma unroll
                 for (int p = 0; p < J; ++p) U[row * J + p] = u[p];
+            }
+            if (Uh) {  // the BF16 copy the BF16-gather sweep reads
+                if constexpr (J % 2 == 0) {
+#pragma unroll
+                    for (int p = 0; p < J; p += 2)
+                        *reinterpret_cast<__nv_bfloat162 *>(Uh + row * J + p) = __floats2bfloat162_rn(u[p], u[p + 1]);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < J; ++p) Uh[row * J + p] = __float2bfloat16(u[p]);
+                }
             }
         }
     }
@@ -1920,6 +2179,7 @@ struct RowArgs {
     const float *curv_in;
     float *gram_out;
     const float *wc1, *wc2;  // this wave's entries per (row, platform) of each mode, or null
+    __nv_bfloat16 *U2h;      // BF16 copy of the gene rows to keep current, or null
 };
 
 // End of a wave.  mode 0: CTA 0 = the rest of the core and platform-row step (dense_post),
@@ -1940,7 +2200,7 @@ __device__ void wave_end_rows(const DenseArgs &A, const RowArgs &R, int blk, int
                                   R.inv_n, Ckg, gout, R.wc1, smw);
         else
             wave_rows_thread<CJ2>(mb, mode == 0, R.U2, R.gB, R.rs2, R.cnt2, d.I2, d.I3, A.lam, 1.f / A.lr,
-                                  R.inv_n, Ckg, gout, R.wc2, smw);
+                                  R.inv_n, Ckg, gout, R.wc2, smw, R.U2h);
     } else {
         wave_rows(first, mb, mode == 0, R.U1, R.U2, R.gA, R.gB, R.rs1, R.rs2, R.cnt1, R.cnt2, d, A.lam,
                   1.f / A.lr, R.inv_n, R.curv_in, R.gram_out, R.wc1, R.wc2, smw);
@@ -2033,10 +2293,41 @@ size_t sweep_smem(const Ctx *c) {
     return sizeof(float) * std::max<size_t>(sweep, (size_t)dense_pre_floats(c->d));
 }
 
+// Which sweep kernel a context runs: 1 the lane-group kernel (FP32 gathers), 2 the lane-group
+// kernel gathering gene rows from the BF16 copy, 0 k_fast_sweep (the warp-per-unit kernel for
+// compile-time ranks up to 16, the per-entry kernel otherwise), -1 the tensor-core kernel.
+// The lane-group kernel needs compile-time J1, J2 <= 16, every platform's Gc in shared memory
+// and the set-up table of per-wave row counts.  SNECT_SWEEP_KERNEL=warp in the environment
+// selects k_fast_sweep where the lane-group kernel would run (both are complete sweeps; the
+// switch exists to compare them).
+template <int CJ1, int CJ2, int CJ3>
+int pick_sweep(const Ctx *c) {
+    const int prec = c->cfg.precision;
+    bool lg = false;
+    if constexpr (runs_path<CJ1, CJ2>()) lg = c->wcnt && (int64_t)c->d.I3 * CJ1 * CJ2 <= kGcAll;
+    if (prec == SNECT_BF16_TC) return -1;
+    if (prec == SNECT_BF16) return (lg && CJ2 % 4 == 0) ? 2 : -1;
+    const char *env = getenv("SNECT_SWEEP_KERNEL");
+    if (env && strcmp(env, "warp") == 0) return 0;
+    return lg ? 1 : 0;
+}
+
+// the sweep kernel of a context (sweep_kind >= 0)
+template <int CJ1, int CJ2, int CJ3>
+void (*sweep_kernel(const Ctx *c))(FastArgs) {
+    if constexpr (runs_path<CJ1, CJ2>()) {
+        if (c->sweep_kind == 1) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 0>;
+        if constexpr (CJ2 % 4 == 0)
+            if (c->sweep_kind == 2) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 1>;
+    }
+    return c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
+}
+
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t init_sweep(Ctx *c) {
     const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(c);
-    auto kern = c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
+    c->sweep_kind = pick_sweep<CJ1, CJ2, CJ3>(c);
+    auto kern = sweep_kernel<CJ1, CJ2, CJ3>(c);
     cudaError_t e = cudaFuncSetAttribute(kern,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -2128,6 +2419,9 @@ FastArgs make_fast_args(Ctx *c, int64_t w) {
     A.rs2 = row_stride(c->d.J2, c->d.I3);
     A.err = c->flag + 3;
     A.count_atomics = c->wcnt ? 0 : 1;
+    A.e_first = w * c->wave;
+    A.e_count = c->wave_len[w];
+    A.U2h = c->U2h;
     RowArgs unused;
     make_wave_args(c, w, (int)(w & 1), 0, &A.pre, &unused);
     return A;
@@ -2139,11 +2433,12 @@ cudaError_t run_sweep(Ctx *c, int64_t w) {
     const int64_t nt = A.n_tiles;
     // CTAs 0-2 take the wave's dense pre-work (CTA 0 alone in the tensor-core form), the
     // others the tiles (one resident wave of CTAs)
-    const int pre = c->cfg.precision == SNECT_BF16 ? 1 : kPreCtas;
+    const bool tc = c->sweep_kind < 0;
+    const int pre = tc ? 1 : kPreCtas;
     const int grid = (int)std::min<int64_t>(std::max(1, c->fast_grid - pre), nt) + pre;
     c->launches++;
-    if (c->cfg.precision == SNECT_BF16) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
-    auto kern = c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
+    if (tc) return SNECT_DISPATCH_TC(c->d.J1, c->d.J2, launch_sweep_tc, c, A, grid);
+    auto kern = sweep_kernel<CJ1, CJ2, CJ3>(c);
     kern<<<grid, kFastThreads, sweep_smem<CJ1, CJ2, CJ3>(c), c->stream>>>(A);
     return cudaGetLastError();
 }
@@ -2194,6 +2489,7 @@ void make_wave_args(Ctx *c, int64_t w, int parity, int mode, DenseArgs *Ap, RowA
     R.curv_in = c->curv;
     R.gram_out = c->gram + (size_t)parity * c->gram_stride;
     R.wc1 = R.wc2 = nullptr;
+    R.U2h = c->U2h;
     if (c->wcnt && w >= 0) {
         R.wc1 = c->wcnt + (size_t)w * ((size_t)d.I1 + d.I2) * d.I3;
         R.wc2 = R.wc1 + (size_t)d.I1 * d.I3;
@@ -2209,7 +2505,20 @@ cudaError_t launch_wave_end(Ctx *c, int64_t w, int parity, int mode) {
     return SNECT_DISPATCH_ROWS(c->d.J1, c->d.J2, c->d.J3, launch_wave_end_k, c, A, R, mode, wave_end_smem(c));
 }
 
+__global__ void k_rows_to_bf16(const float *__restrict__ U, int64_t n, __nv_bfloat16 *__restrict__ Uh) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) Uh[t] = __float2bfloat16(U[t]);
+}
+
 }  // namespace
+
+cudaError_t refresh_bf16_rows(Ctx *c) {
+    if (!c->U2h) return cudaSuccess;
+    const int64_t n = (int64_t)c->d.I2 * c->d.J2;
+    k_rows_to_bf16<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->U[1], n, c->U2h);
+    c->launches++;
+    return cudaGetLastError();
+}
 
 int init_fast(Ctx *c) {
     const Dims &d = c->d;
@@ -2231,10 +2540,11 @@ int init_fast(Ctx *c) {
         SNECT_CUDA(c, cudaMalloc((void **)&c->gacc[n], sizeof(float) * nf));
         SNECT_CUDA(c, cudaMemsetAsync(c->gacc[n], 0, sizeof(float) * nf, c->stream));
     }
-    if (c->cfg.precision == SNECT_BF16) {
-        SNECT_CUDA(c, SNECT_DISPATCH_TC(d.J1, d.J2, init_sweep_tc, c));
-    } else {
-        SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
+    SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
+    if (c->sweep_kind < 0) SNECT_CUDA(c, SNECT_DISPATCH_TC(d.J1, d.J2, init_sweep_tc, c));
+    if (c->sweep_kind == 2) {
+        SNECT_CUDA(c, cudaMalloc((void **)&c->U2h, sizeof(__nv_bfloat16) * (size_t)d.I2 * d.J2));
+        SNECT_CUDA(c, refresh_bf16_rows(c));
     }
     SNECT_CUDA(c, cudaMemsetAsync(c->flag + 2, 0, 2 * sizeof(int32_t), c->stream));
     SNECT_CUDA(c, SNECT_DISPATCH_ROWS(d.J1, d.J2, d.J3, set_wave_end_attr, c, wave_end_smem(c)));
@@ -2324,6 +2634,7 @@ void free_fast(Ctx *c) {
     f(c->gacc[0]);
     f(c->gacc[1]);
     f(c->wcnt);
+    f(c->U2h);
 }
 
 }  // namespace snect

@@ -29,19 +29,21 @@ def max_principal_angle(X, Y):
     return float(np.degrees(np.arccos(s.min())))
 
 
-@pytest.mark.parametrize("J", [(16, 16, 5), (32, 32, 5), (16, 32, 5)])
-def test_bf16_reaches_fp32_rmse_on_config1_refit(J, gpu_lib):
+@pytest.mark.parametrize("J,tc", [((16, 16, 5), False), ((16, 16, 5), True), ((32, 32, 5), False),
+                                  ((16, 32, 5), False)])
+def test_bf16_reaches_fp32_rmse_on_config1_refit(J, tc, gpu_lib):
     import paper_1711_08095_gb300 as snect
 
     p = S.config1(J_fit=J)
     out = {}
-    for prec in (snect.FP32, snect.BF16):
+    bf = snect.BF16_TC if tc else snect.BF16
+    for prec in (snect.FP32, bf):
         c = ctx(p, prec)
         c.epoch(p.epochs)
         out[prec] = (c.loss(p.test_idx, p.test_val), c.get_factors())
         c.close()
     l32, (G32, U32) = out[snect.FP32]
-    l16, (G16, U16) = out[snect.BF16]
+    l16, (G16, U16) = out[bf]
     assert np.isfinite(l16["total"])
     assert l16["rmse_test"] <= 1.01 * l32["rmse_test"], (l16["rmse_test"], l32["rmse_test"])
     # distance from the FP64 oracle's sequential run (reported, loosely bounded)
@@ -61,14 +63,15 @@ def test_bf16_reaches_fp32_rmse_on_config1_refit(J, gpu_lib):
         assert l16["rmse_test"] <= 1.2 * ro
 
 
-def test_bf16_sweep_matches_fp32_sweep_after_one_epoch(gpu_lib):
+@pytest.mark.parametrize("tc", [False, True])
+def test_bf16_sweep_matches_fp32_sweep_after_one_epoch(tc, gpu_lib):
     """One epoch from the same start on a paper-shaped problem: the two forms' factors agree
     to BF16 rounding of the contraction inputs (relative 5e-2 of each matrix's scale)."""
     import paper_1711_08095_gb300 as snect
 
     p = S.config2(n_patients=200, nnz=300_000, n_edges=10_000, J_fit=(16, 16, 5))
     res = []
-    for prec in (snect.FP32, snect.BF16):
+    for prec in (snect.FP32, snect.BF16_TC if tc else snect.BF16):
         c = ctx(p, prec)
         c.epoch(1)
         res.append(c.get_factors())

@@ -42,6 +42,24 @@ def test_foldin_matches_oracle(served, n):
         assert np.linalg.norm(got - u_true) <= 0.1 * np.linalg.norm(u_true)
 
 
+def test_foldin_matches_oracle_at_the_largest_query(gpu_lib):
+    """The serving workload's largest query: 75,000 cells (every (gene, platform) pair of a
+    15,000 x 5 model), 19 partial-sum CTAs."""
+    import paper_1711_08095_gb300 as snect
+
+    m = S.serving_model(I=(600, 15000, 5), J=(16, 16, 5))
+    idx = np.array([[0, 0, 0], [1, 1, 1]], np.int32)
+    c = snect.Snect((600, 15000, 5), m.G.shape, idx, np.zeros(2, np.float32), np.zeros((0, 2), np.int32),
+                    np.zeros(0, np.float32), m.G, m.U, lam=m.lam, lam_g=0.0, lr=0.01, batch=1)
+    jk, x, u_true = S.serving_query(m, q=75, size=75000)
+    got = c.foldin(jk, x)
+    c.close()
+    want = oracle.foldin(m.G, m.U[1], m.U[2], jk, x, m.lam)
+    assert jk.shape[0] == 75000
+    assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want), (got, want)
+    assert np.linalg.norm(got - u_true) <= 0.1 * np.linalg.norm(u_true)
+
+
 def test_foldin_is_the_same_alone_and_repeated(served):
     m, c = served
     jk, x, _ = S.serving_query(m, q=3, size=9000)

@@ -15,7 +15,10 @@ pytestmark = pytest.mark.gpu
 
 
 def request_bytes(n, J1):
-    return 12 * n + 4 * math.ceil(n / 4096) * (J1 * J1 + J1)
+    """Arena bytes of a request of n cells: cells (8 B), values (4 B) and the fold-in's
+    per-4,096-cell Gram partials, each rounded up to 256 bytes."""
+    up = lambda x: -(-x // 256) * 256
+    return up(8 * n) + up(4 * n) + up(4 * math.ceil(n / 4096) * (J1 * J1 + J1))
 
 
 @pytest.fixture(scope="module")
@@ -50,19 +53,23 @@ def test_results_are_the_same_alone_and_in_the_mix(served):
     assert st["max_concurrent"] > 1  # requests overlapped on the device
 
 
-def test_admission_follows_the_memory_budget(served):
-    m, c, queries, alone = served
-    big = max(len(x) for _, x, _ in queries)
-    # room for exactly one request of the largest size at a time
-    srv = c.serve(n_slots=6, mem_budget_bytes=request_bytes(15000, 16), max_cells=15000)
-    tickets = [srv.submit(jk, x, 10) for jk, x, _ in queries[:12]]
-    for t, (u0, _, _) in zip(tickets, alone[:12]):
+@pytest.mark.parametrize("fit", [1, 2])
+def test_admission_follows_the_memory_budget(served, fit):
+    """The requests in flight are carved from one arena of exactly the budget: with room for
+    `fit` requests of the largest size and only requests above half of it, never more than
+    `fit` run at once, with slots to spare; results stay those of the requests alone."""
+    m, c, _, _ = served
+    big = [S.serving_query(m, q=100 + q, size=12000 + 250 * q) for q in range(10)]
+    alone = [c.foldin(jk, x) for jk, x, _ in big]
+    srv = c.serve(n_slots=6, mem_budget_bytes=fit * request_bytes(15000, 16), max_cells=15000)
+    tickets = [srv.submit(jk, x, 10) for jk, x, _ in big]
+    for t, u0 in zip(tickets, alone):
         u, _, _, _ = srv.poll(t, 10)
         assert np.array_equal(u, u0)
     st = srv.stats()
     srv.stop()
-    assert st["completed"] == 12
-    assert big <= 15000
+    assert st["completed"] == len(big)
+    assert 1 <= st["max_concurrent"] <= fit, st
 
 
 def test_bad_requests(served):

@@ -11,11 +11,12 @@ value is compared: |gpu - oracle| <= tol (|oracle| + rms), tol 1e-5 for the FP32
 counts of each row's entries per platform in the wave (the row steps' weights) are integers
 and must match exactly.
 
-Every compiled path of the sweep is driven: the statically partitioned per-run sweep
-(10x10x5, 16x16x5), its tile-claiming variant (16x16x5 with 20 platforms, every platform's
+Every compiled path of the sweep is driven: the lane-group and the warp-per-unit per-run
+sweeps (5x5x2, 10x10x5, 16x16x5), the tile-claiming variant (16x16x5 with 20 platforms, every platform's
 Gc beyond the shared-memory budget), the variant that counts with atomics (64 platforms,
-1,024-entry waves), the per-entry sweep (32x32x5, and runtime ranks 3x7x4), and the BF16
-tensor-core sweep (tolerance 16 units of BF16 roundoff: its operands are rounded to BF16).  Each at the initial
+1,024-entry waves), the per-entry sweep (32x32x5, and runtime ranks 3x7x4), and the two BF16
+forms, BF16 gene-row gathers and the tensor-core sweep (tolerance 16 units of BF16 roundoff:
+their operands are rounded to BF16).  Each at the initial
 parameters and again after two epochs, on the first, a middle and the last (ragged) wave.
 """
 import numpy as np
@@ -76,13 +77,20 @@ def check_waves(p, tol, precision=0, wave=0, epochs_between=2):
                                               for s, w, e in report])
 
 
-def test_static_partition_sweep_10x10x5(gpu_lib):
-    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000)
-    check_waves(p, TOL32)
+@pytest.fixture(params=["lanes", "warp"])
+def sweep_kernel(request, monkeypatch):
+    """The two complete sweep kernels for compile-time ranks up to 16: the lane-group kernel
+    (the default) and the warp-per-unit kernel (SNECT_SWEEP_KERNEL=warp, read at set-up)."""
+    if request.param == "warp":
+        monkeypatch.setenv("SNECT_SWEEP_KERNEL", "warp")
+    else:
+        monkeypatch.delenv("SNECT_SWEEP_KERNEL", raising=False)
+    return request.param
 
 
-def test_static_partition_sweep_16x16x5(gpu_lib):
-    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=(16, 16, 5))
+@pytest.mark.parametrize("J", [(5, 5, 2), (10, 10, 5), (16, 16, 5)])
+def test_static_partition_sweep(J, sweep_kernel, gpu_lib):
+    p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=J)
     check_waves(p, TOL32)
 
 
@@ -106,8 +114,11 @@ def test_per_entry_sweep(J, gpu_lib):
     check_waves(p, TOL32)
 
 
-def test_bf16_tensor_core_sweep(gpu_lib):
+@pytest.mark.parametrize("form", ["bf16_gather", "bf16_tensor_cores"])
+def test_bf16_sweeps(form, gpu_lib):
+    """SNECT_BF16 at 16 x 16 x 5 gathers the gene rows from their BF16 copy (the lane-group
+    kernel); SNECT_BF16_TC runs the dense per-entry contractions on tcgen05."""
     import paper_1711_08095_gb300 as snect
 
     p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=(16, 16, 5))
-    check_waves(p, TOL_BF16, precision=snect.BF16)
+    check_waves(p, TOL_BF16, precision=snect.BF16 if form == "bf16_gather" else snect.BF16_TC)
