@@ -44,12 +44,11 @@ WORKLOAD = dict(
     I=[4500, 15000, 5], J=[10, 10, 5], nnz_train=27_000_000, edges=300_000, lam=0.01, lam_g=0.1, lr=0.01,
 )
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per training entry of k_fast_sweep, FP32 core 10x10x5, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry case of the same
-# structure (bench.py --small), scaled to a launch by its entries.  To be re-measured, or set to
-# None, whenever the sweep kernel changes.  None: the kernel has changed since the last capture
-# (12.864 MB per 675,000-entry launch, before the run vectors moved to shared memory).
-SWEEP_DRAM_BYTES_PER_ENTRY = None
+# DRAM bytes (read + write) per training entry of the FP32 sweep kernel (k_fast_sweep_lg, core
+# 10x10x5), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry
+# case of the same structure (bench.py --small): 12.834 MB per 675,000-entry launch, scaled to a
+# launch by its entries.  To be re-measured, or set to None, whenever the sweep kernel changes.
+SWEEP_DRAM_BYTES_PER_ENTRY = 19.01
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
@@ -577,9 +576,9 @@ def batched_form(args, snect, epochs=5):
     nnz = sum(p.nnz for p in cohorts) * len(lam_gs)
     st = torch.cuda.current_stream()
 
-    def contexts():
+    def contexts(precision=snect.FP32):
         return [snect.Snect(p.I, p.J, d["idx"], d["val"], d["edges"], d["w"], d["G0"], d["U0"], lam=p.lam,
-                            lam_g=float(lg), lr=p.lr, batch=0)
+                            lam_g=float(lg), lr=p.lr, batch=0, precision=precision)
                 for p, d in zip(cohorts, dcoh) for lg in lam_gs]
 
     def timed(step, n):
@@ -597,17 +596,19 @@ def batched_form(args, snect, epochs=5):
         return float(np.mean(r)), float(np.max(r))
 
     out = {"problems": len(cohorts) * len(lam_gs), "nnz_per_epoch": int(nnz)}
-    cs = contexts()
-    b = snect.Batch(cs)
-    b.epoch(1)  # warm-up (graph capture)
-    l0 = b.launches
-    ms_b = timed(b.epoch, epochs - 1)
-    out["batched"] = {"nnz_updates_per_s": nnz / (ms_b / 1e3), "ms_per_epoch": ms_b,
-                      "launches_per_epoch": (b.launches - l0) / (epochs - 1)}
-    out["batched"]["mean_rmse_test"], out["batched"]["max_rmse_test"] = rmse(cs)
-    b.close()
-    for c in cs:
-        c.close()
+    for name, prec in (("batched", snect.FP32), ("batched_bf16", snect.BF16)):
+        cs = contexts(prec)
+        b = snect.Batch(cs)
+        b.epoch(1)  # warm-up (autotuning, graph capture)
+        l0 = b.launches
+        ms_b = timed(b.epoch, epochs - 1)
+        out[name] = {"nnz_updates_per_s": nnz / (ms_b / 1e3), "ms_per_epoch": ms_b,
+                     "launches_per_epoch": (b.launches - l0) / (epochs - 1), "autotuned": b.tuning()}
+        out[name]["mean_rmse_test"], out[name]["max_rmse_test"] = rmse(cs)
+        b.close()
+        for c in cs:
+            c.close()
+    ms_b = out["batched"]["ms_per_epoch"]
     cs = contexts()
 
     def one_by_one(n):
@@ -622,7 +623,8 @@ def batched_form(args, snect, epochs=5):
         c.close()
     out["batched_vs_one_by_one"] = ms_s / ms_b
     out["workload"] = ("12 cohorts of 150-1,100 patients x 15,000 genes x 5 (%.2gM-%.2gM entries) x 8 lambda_g in "
-                       "1e-3..1, core 16x16x5, FP32 fast mode; %d epochs from the same start"
+                       "1e-3..1, core 16x16x5, FP32 fast mode (batched_bf16: BF16 gene-row gathers); %d epochs "
+                       "from the same start"
                        % (cohorts[0].nnz / 1e6, cohorts[-1].nnz / 1e6, epochs))
     return out
 
@@ -771,6 +773,8 @@ def main():
                      "frac": (achieved / pk) if achieved else None,
                      "traffic": (SWEEP_DRAM_BYTES_PER_ENTRY * per_launch
                                  if (SWEEP_DRAM_BYTES_PER_ENTRY and not bf16 and tuple(p.J) == (10, 10, 5)) else None),
+                     "limiter": "ncu on the 12M-entry case: DRAM 5-6 % of peak, L2 23-29 %, L1 59 %, issue 61 %; "
+                                "instruction issue and L1 bound the kernel, not HBM",
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 12M-entry case scaled by entries)",
                      "kernel": "%s (one launch per wave)" % {"fp32": "k_fast_sweep_lg", "bf16": "k_fast_sweep_lg (BF16 gathers)",
                                                              "bf16_tc": "k_fast_sweep_tc"}[args.precision],

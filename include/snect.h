@@ -169,17 +169,28 @@ int snect_serve_stop(snect_server *srv);
 int snect_qr_post(snect_ctx *ctx, int32_t *skipped_modes);
 
 /* Batched form: several independent decompositions (e.g. per-cohort sub-tensors, each fitted
- * for several lambda_g) stepped together.  ctxs: n fast-mode FP32 contexts with the same core
- * ranks and the same number of waves (a batch does not own them; they must outlive it).  One
- * epoch of the batch is one CUDA graph: per wave, one sweep launch over the tiles of every
- * problem and one launch of every problem's wave-end steps, then each problem's network
- * pass.  Each context then holds its own updated factors (snect_loss, snect_get_factors).
+ * for several lambda_g) stepped together.  ctxs: n fast-mode contexts with the same core ranks,
+ * the same number of waves and the same sweep (SNECT_FP32, or SNECT_BF16 at 16 x 16 x 5; not
+ * the tensor-core form); a batch does not own them, they must outlive it.  One epoch of the
+ * batch is one CUDA graph: per wave, one sweep launch over every problem (each CTA serves one
+ * problem, the CTAs allotted in proportion to the problems' entries) and one launch of every
+ * problem's wave-end steps, then every problem's network pass.  The first snect_batch_epoch
+ * autotunes the sweep launch (CTAs per SM, fewest entries per warp) by timing wave 0 of every
+ * candidate at the current parameters, then clears what those trial sweeps accumulated and
+ * puts back the curvature state their pre-work rewrote, so the batch steps every problem as
+ * its own epochs would.  Each context then holds its own updated factors (snect_loss,
+ * snect_get_factors).
  * stream: a cudaStream_t or NULL (default stream); snect_batch_epoch is asynchronous.
  * Errors: SNECT_EINVAL (mismatched contexts), SNECT_ECUDA; messages through
  * snect_batch_last_error (NULL: the last failing snect_batch_create). */
 typedef struct snect_batch snect_batch;
 int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, void *stream);
 int snect_batch_epoch(snect_batch *batch, int32_t n_epochs);
+/* The autotuner's choice (zeros before the first epoch): tile CTAs per SM, fewest entries
+ * per warp (0: no floor), and that configuration's sweep time on wave 0 in ms.  Host
+ * pointers, each may be NULL. */
+int snect_batch_tuning(const snect_batch *batch, int32_t *ctas_per_sm, int32_t *min_entries_per_warp,
+                       double *sweep_ms);
 /* kernels the batch has launched so far (its graphs' kernel nodes) */
 int64_t snect_batch_launch_count(const snect_batch *batch);
 const char *snect_batch_last_error(const snect_batch *batch);

@@ -40,6 +40,7 @@ EXPORTS = (
     "snect_qr_post",
     "snect_batch_create",
     "snect_batch_epoch",
+    "snect_batch_tuning",
     "snect_batch_launch_count",
     "snect_batch_last_error",
     "snect_batch_destroy",
@@ -135,6 +136,8 @@ def load(build_if_missing: bool = False):
         "snect_qr_post": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "snect_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(P), i32, P]),
         "snect_batch_epoch": (ctypes.c_int, [P, i32]),
+        "snect_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(ctypes.c_double)]),
         "snect_batch_launch_count": (ctypes.c_int64, [P]),
         "snect_batch_last_error": (ctypes.c_char_p, [P]),
         "snect_batch_destroy": (None, [P]),
@@ -450,6 +453,13 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(self._lib.snect_batch_launch_count(self._h))
+
+    def tuning(self):
+        """The autotuner's choice: dict(ctas_per_sm, min_entries_per_warp, sweep_ms)."""
+        a, m = ctypes.c_int32(), ctypes.c_int32()
+        ms = ctypes.c_double()
+        self._lib.snect_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(m), ctypes.byref(ms))
+        return dict(ctas_per_sm=a.value, min_entries_per_warp=m.value, sweep_ms=ms.value)
 
     def close(self):
         if getattr(self, "_h", None):

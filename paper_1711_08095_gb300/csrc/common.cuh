@@ -79,6 +79,7 @@ struct Ctx {
     float *macc = nullptr;          // per platform: sum over the wave of r a b^T (I3 * J1 * J2)
     float *gram = nullptr;          // moments of U1, U2 (two buffers of gram_stride) + eigenvectors
     int64_t gram_stride = 0;
+    int64_t gram_floats = 0;        // the whole gram buffer (moments, eigenbases, platform systems)
     int32_t fast_grid = 0;          // persistent CTAs of the wave kernel (occupancy)
     float *gacc[2] = {};            // per patient / gene row: gradient sums + entries per platform
     // entries per (wave, row, platform), fixed at set-up: n_waves x (I1 + I2) x I3, patients

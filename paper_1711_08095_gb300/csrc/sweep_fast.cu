@@ -783,18 +783,15 @@ __device__ __forceinline__ float slot_sum(float x) {
 template <int CJ1, int CJ2>
 constexpr int lg_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
 
+// The lane-group sweep of one problem's wave by the CTA's warps: W warps share the wave,
+// this CTA's warps are w0, w0 + 1, ...  (sm: the CTA's dynamic shared memory)
 template <int CJ1, int CJ2, int CJ3, int GB>
-__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fast_sweep_lg(FastArgs A) {
+__device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int64_t W, int64_t w0) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int J1 = CJ1, J2 = CJ2, J3 = CJ3, Q = J1 * J2, PI = Q * J3;
     using LG = LaneGroup<CJ2, GB>;
     constexpr int VEC = LG::VEC, L = LG::L, E = LG::E;
     constexpr int NM = (Q + 31) / 32;  // M_k elements per lane
-    extern __shared__ __align__(16) float sm[];
-    if (blockIdx.x < kPreCtas) {  // the wave's dense pre-work, as in k_fast_sweep
-        dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
-        return;
-    }
     // per warp: the open run's patient row a (floats 0-31) and, when it closes, s (32-63)
     __shared__ __align__(16) float sSlot[kFastThreads / 32][64];
     const int I3 = A.d.I3;
@@ -816,8 +813,7 @@ __global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fas
     float *slot = sSlot[warp];
     const int g = lane / L, m = lane % L;  // entry slot and component group of this lane
     const bool act = g < E;
-    const int64_t W = (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32);
-    const int64_t w = (int64_t)(blockIdx.x - kPreCtas) * (kFastThreads / 32) + warp;
+    const int64_t w = w0 + warp;
     const int64_t lo = A.e_first + w * A.e_count / W, hi = A.e_first + (w + 1) * A.e_count / W;
     float mreg[NM];
 #pragma unroll
@@ -958,6 +954,38 @@ __global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fas
     __syncthreads();
     for (int s = tid; s < I3 * Q; s += kFastThreads)
         if (sMacc[s] != 0.f) atomicAdd(A.macc + s, sMacc[s]);
+}
+
+template <int CJ1, int CJ2, int CJ3, int GB>
+__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fast_sweep_lg(FastArgs A) {
+    extern __shared__ __align__(16) float sm[];
+    if (blockIdx.x < kPreCtas) {  // the wave's dense pre-work, as in k_fast_sweep
+        dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
+        return;
+    }
+    lg_sweep_body<CJ1, CJ2, CJ3, GB>(A, sm, (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32),
+                                     (int64_t)(blockIdx.x - kPreCtas) * (kFastThreads / 32));
+}
+
+// The lane-group sweep of one wave over every problem of a batch.  CTAs 0 .. P-1 take each
+// problem's dense pre-work; every other CTA serves one problem (cta_prob), as CTA number
+// cta_rank of the prob_ctas[p] CTAs the batch's autotuned allotment gave that problem.
+template <int CJ1, int CJ2, int CJ3, int GB>
+__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>())
+    k_batch_sweep_lg(const FastArgs *__restrict__ probs, const int32_t *__restrict__ cta_prob,
+                     const int32_t *__restrict__ cta_rank, const int32_t *__restrict__ prob_ctas, int32_t P) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ FastArgs sArgs;
+    if ((int)blockIdx.x < P) {
+        dense_pre<CJ1, CJ2, CJ3>(probs[blockIdx.x].pre, sm, -1);
+        return;
+    }
+    const int b = (int)blockIdx.x - P;
+    const int pid = cta_prob[b];
+    if (threadIdx.x == 0) sArgs = probs[pid];
+    __syncthreads();
+    lg_sweep_body<CJ1, CJ2, CJ3, GB>(sArgs, sm, (int64_t)prob_ctas[pid] * (kFastThreads / 32),
+                                     (int64_t)cta_rank[b] * (kFastThreads / 32));
 }
 
 // The sweep of one wave over every problem of a batch: the same tile work as k_fast_sweep;
@@ -2530,6 +2558,7 @@ int init_fast(Ctx *c) {
     // + eigenvectors and eigenvalues of Ma, Mb, Cn + the platform systems' inverses
     const int64_t gf = 2 * c->gram_stride + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3 + d.J1 + d.J2 + d.J3 +
                        (int64_t)d.I3 * d.J3 * d.J3;
+    c->gram_floats = gf;
     SNECT_CUDA(c, cudaMalloc((void **)&c->gram, sizeof(float) * gf));
     SNECT_CUDA(c, cudaMemsetAsync(c->gram, 0, sizeof(float) * gf, c->stream));
     // platform curvatures for the row steps (formed by each wave's pre-work)
@@ -2666,9 +2695,210 @@ struct Batch {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::string err;
+    // the lane-group batch sweep (contexts of sweep kind 1 or 2): per wave, the tile CTAs'
+    // problem and rank and each problem's CTA count, from the autotuned allotment
+    int32_t kind = 0;
+    std::vector<int32_t> lg_tiles;        // per wave: tile CTAs
+    std::vector<int64_t> lg_off;          // per wave: offset of its (prob, rank) arrays in d_cta
+    int32_t *d_cta = nullptr;
+    int32_t *d_prob_ctas = nullptr;       // [n_waves][P]
+    int32_t tune_cps = 0;                 // autotuned: tile CTAs per SM
+    int32_t tune_min_entries = 0;         // autotuned: fewest entries a warp is given
+    double tune_ms = 0.0;                 // the chosen configuration's sweep time on wave 0
+    void *d_bf = nullptr;                 // BF16 copies to refresh after the network passes
+    int64_t bf_max = 0;
 };
 
 namespace {
+
+struct BfRows {
+    const float *U2;
+    __nv_bfloat16 *U2h;
+    int64_t n;
+};
+
+__global__ void k_batch_rows_to_bf16(const BfRows *__restrict__ a) {
+    const BfRows r = a[blockIdx.y];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r.n; t += (int64_t)gridDim.x * blockDim.x)
+        r.U2h[t] = __float2bfloat16(r.U2[t]);
+}
+
+// the lane-group sweep's allotment of tile CTAs to the problems of wave w: about `tiles` CTAs
+// in proportion to each problem's entries (at least one CTA for a problem with entries), and
+// no more than one warp per min_e entries when min_e > 0
+void lg_allot(const Batch *b, int64_t w, int tiles, int64_t min_e, std::vector<int32_t> &prob,
+              std::vector<int32_t> &rank, std::vector<int32_t> &pc) {
+    const int P = b->P;
+    int64_t N = 0;
+    for (int p = 0; p < P; ++p) N += b->ctx[p]->wave_len[w];
+    prob.clear();
+    rank.clear();
+    pc.assign((size_t)P, 0);
+    for (int p = 0; p < P; ++p) {
+        const int64_t n = b->ctx[p]->wave_len[w];
+        if (n <= 0) continue;
+        int64_t c = std::max<int64_t>(1, (int64_t)tiles * n / std::max<int64_t>(N, 1));
+        if (min_e > 0) c = std::min<int64_t>(c, std::max<int64_t>(1, (n + 8 * min_e - 1) / (8 * min_e)));
+        pc[p] = (int32_t)c;
+        for (int64_t r = 0; r < c; ++r) {
+            prob.push_back(p);
+            rank.push_back((int32_t)r);
+        }
+    }
+}
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t batch_lg_launch(Batch *b, const FastArgs *d_fast_w, const int32_t *d_prob, const int32_t *d_rank,
+                            const int32_t *d_pc, int tiles, cudaStream_t st) {
+    if constexpr (runs_path<CJ1, CJ2>()) {
+        const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]);
+        if (b->kind == 2) {
+            if constexpr (CJ2 % 4 == 0) {
+                k_batch_sweep_lg<CJ1, CJ2, CJ3, 1><<<b->P + tiles, kFastThreads, smem, st>>>(d_fast_w, d_prob, d_rank,
+                                                                                          d_pc, b->P);
+                return cudaGetLastError();
+            }
+            return cudaErrorInvalidValue;
+        }
+        k_batch_sweep_lg<CJ1, CJ2, CJ3, 0><<<b->P + tiles, kFastThreads, smem, st>>>(d_fast_w, d_prob, d_rank, d_pc,
+                                                                                  b->P);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t batch_lg_attr(Batch *b, int *per_sm) {
+    *per_sm = 1;
+    if constexpr (runs_path<CJ1, CJ2>()) {
+        const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]);
+        auto set = [&](auto kern) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kFastThreads, smem);
+            return e;
+        };
+        if (b->kind == 2) {
+            if constexpr (CJ2 % 4 == 0) return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 1>);
+            return cudaErrorInvalidValue;
+        }
+        return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 0>);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// every problem's wave accumulators back to zero (after an autotuning launch)
+cudaError_t batch_clear_acc(Batch *b, cudaStream_t st) {
+    for (Ctx *c : b->ctx) {
+        const Dims &d = c->d;
+        cudaError_t e = cudaMemsetAsync(c->gacc[0], 0, sizeof(float) * d.I1 * row_stride(d.J1, d.I3), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->gacc[1], 0, sizeof(float) * (size_t)d.I2 * row_stride(d.J2, d.I3), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, sizeof(float) * d.I3 * d.J1 * d.J2, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Autotuner of the lane-group batch sweep: every candidate (tile CTAs per SM, fewest entries
+// per warp) sweeps wave 0 at the current parameters, timed with CUDA events (best of two after
+// a warm-up launch); its accumulations are cleared again.  Then the per-wave allotment tables
+// of the fastest candidate are built and uploaded.
+cudaError_t batch_lg_tune(Batch *b, cudaStream_t st) {
+    const Dims &d = b->d;
+    int per_sm = 1, sms = 1;
+    cudaError_t e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_lg_attr, b, &per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->device);
+    if (e != cudaSuccess) return e;
+    // the trial sweeps' dense pre-work rewrites each problem's curvature state (moments,
+    // eigenbases, platform systems): saved here and put back afterwards
+    std::vector<float *> saved(b->P, nullptr);
+    for (int p = 0; p < b->P && e == cudaSuccess; ++p) {
+        Ctx *c = b->ctx[p];
+        const size_t nf = (size_t)c->gram_floats + curv_stride(c);
+        e = cudaMalloc((void **)&saved[p], sizeof(float) * nf);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(saved[p], c->gram, sizeof(float) * c->gram_floats, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(saved[p] + c->gram_floats, c->curv, sizeof(float) * curv_stride(c),
+                                cudaMemcpyDeviceToDevice, st);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<int32_t> prob, rank, pc;
+    double best = 1e30;
+    for (int cps = 2; cps <= std::max(2, per_sm) && e == cudaSuccess; ++cps) {
+        for (int64_t me : {(int64_t)0, (int64_t)2048}) {
+            if (e != cudaSuccess) break;
+            const int tiles = std::max(cps * sms - b->P, b->P);
+            lg_allot(b, 0, tiles, me, prob, rank, pc);
+            const int T = (int)prob.size();
+            std::vector<int32_t> h(prob);
+            h.insert(h.end(), rank.begin(), rank.end());
+            h.insert(h.end(), pc.begin(), pc.end());
+            int32_t *dt = nullptr;
+            e = cudaMalloc((void **)&dt, sizeof(int32_t) * h.size());
+            if (e == cudaSuccess) e = cudaMemcpy(dt, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice);
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_lg_launch, b, b->d_fast, dt, dt + T, dt + 2 * T,
+                                             T, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = batch_clear_acc(b, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_best = std::min(ms_best, ms);
+            }
+            if (dt) cudaFree(dt);
+            if (e == cudaSuccess && ms_best < best) {
+                best = ms_best;
+                b->tune_cps = cps;
+                b->tune_min_entries = (int32_t)me;
+                b->tune_ms = ms_best;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int p = 0; p < b->P; ++p) {
+        Ctx *c = b->ctx[p];
+        if (saved[p] && e == cudaSuccess) {
+            e = cudaMemcpyAsync(c->gram, saved[p], sizeof(float) * c->gram_floats, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->curv, saved[p] + c->gram_floats, sizeof(float) * curv_stride(c),
+                                    cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (float *q : saved)
+        if (q) cudaFree(q);
+    if (e != cudaSuccess) return e;
+    // the chosen allotment for every wave
+    const int tiles = std::max(b->tune_cps * sms - b->P, b->P);
+    std::vector<int32_t> all, allpc;
+    b->lg_tiles.assign((size_t)b->n_waves, 0);
+    b->lg_off.assign((size_t)b->n_waves, 0);
+    for (int64_t w = 0; w < b->n_waves; ++w) {
+        lg_allot(b, w, tiles, b->tune_min_entries, prob, rank, pc);
+        b->lg_off[w] = (int64_t)all.size();
+        b->lg_tiles[w] = (int32_t)prob.size();
+        all.insert(all.end(), prob.begin(), prob.end());
+        all.insert(all.end(), rank.begin(), rank.end());
+        allpc.insert(allpc.end(), pc.begin(), pc.end());
+    }
+    e = cudaMalloc((void **)&b->d_cta, sizeof(int32_t) * std::max<size_t>(1, all.size()));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_cta, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_prob_ctas, sizeof(int32_t) * std::max<size_t>(1, allpc.size()));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_prob_ctas, allpc.data(), sizeof(int32_t) * allpc.size(), cudaMemcpyHostToDevice);
+    return e;
+}
 
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
@@ -2729,12 +2959,25 @@ int batch_build_graph(Batch *b) {
         e = cudaMemsetAsync(b->d_ctr, 0, sizeof(int32_t) * b->n_waves, cap);
         b->epoch_kernels = 0;
         for (int64_t w = 0; w < b->n_waves && e == cudaSuccess; ++w) {
-            e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_sweep_k, b, w, cap);
+            if (b->kind > 0) {
+                const int T = b->lg_tiles[w];
+                const int32_t *tab = b->d_cta + b->lg_off[w];
+                e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_lg_launch, b, b->d_fast + w * b->P, tab, tab + T,
+                                         b->d_prob_ctas + w * b->P, T, cap);
+            } else {
+                e = SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, batch_sweep_k, b, w, cap);
+            }
             if (e == cudaSuccess) e = SNECT_DISPATCH_ROWS(d.J1, d.J2, d.J3, batch_wave_end_k, b, w, cap);
             b->epoch_kernels += 2;
         }
         if (e == cudaSuccess)  // every problem's network pass
             e = launch_batch_edge_pass(b->d_edge, b->P, b->edge_cells, b->edge_heavy, cap, &b->epoch_kernels);
+        if (e == cudaSuccess && b->d_bf) {  // the BF16 gene-row copies after the passes
+            k_batch_rows_to_bf16<<<dim3((unsigned)std::min<int64_t>(ceil_div(b->bf_max, 256), 1024), b->P), 256, 0,
+                                   cap>>>(static_cast<const BfRows *>(b->d_bf));
+            e = cudaGetLastError();
+            b->epoch_kernels += 1;
+        }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -2757,6 +3000,9 @@ void batch_free(Batch *b) {
     cudaFree(b->d_boff);
     cudaFree(b->d_ctr);
     cudaFree(b->d_edge);
+    cudaFree(b->d_cta);
+    cudaFree(b->d_prob_ctas);
+    cudaFree(b->d_bf);
 }
 
 thread_local std::string g_batch_error;
@@ -2784,8 +3030,11 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     };
     for (Ctx *c : b->ctx) {
         if (!c) return bad("null context");
-        if (c->cfg.batch != 0 || c->cfg.precision != SNECT_FP32)
-            return bad("a batch takes fast-mode FP32 contexts");
+        if (c->cfg.batch != 0 || c->sweep_kind < 0)
+            return bad("a batch takes fast-mode contexts whose sweep runs on the FP32 cores "
+                       "(SNECT_FP32, or SNECT_BF16 at 16 x 16 x 5)");
+        if (c->sweep_kind != c0->sweep_kind)
+            return bad("every problem of a batch must run the same sweep kernel (precision and ranks)");
         if (c->d.J1 != c0->d.J1 || c->d.J2 != c0->d.J2 || c->d.J3 != c0->d.J3)
             return bad("every problem of a batch must have the same core ranks");
         if (c->n_waves != c0->n_waves) return bad("every problem of a batch must have the same number of waves");
@@ -2793,6 +3042,7 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     }
     b->d = c0->d;
     b->n_waves = c0->n_waves;
+    b->kind = c0->sweep_kind;
     const int64_t W = b->n_waves, P = n;
     std::vector<FastArgs> hf((size_t)(W * P));
     std::vector<DenseArgs> hd((size_t)(W * P));
@@ -2837,6 +3087,14 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
         b->edge_heavy = std::max<int64_t>(b->edge_heavy, he.back().n_heavy);
     }
     up((void **)&b->d_edge, he.data(), sizeof(EdgeArgs) * he.size());
+    if (b->kind == 2) {
+        std::vector<BfRows> hb;
+        for (Ctx *c : b->ctx) {
+            hb.push_back(BfRows{c->U[1], c->U2h, (int64_t)c->d.I2 * c->d.J2});
+            b->bf_max = std::max<int64_t>(b->bf_max, hb.back().n);
+        }
+        up((void **)&b->d_bf, hb.data(), sizeof(BfRows) * hb.size());
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctr, sizeof(int32_t) * std::max<int64_t>(1, W));
     if (e == cudaSuccess) e = SNECT_DISPATCH_RANKS(b->d.J1, b->d.J2, b->d.J3, batch_sweep_attr, b);
     if (e != cudaSuccess) {
@@ -2856,6 +3114,7 @@ int snect_batch_epoch(snect_batch *h, int32_t n_epochs) {
         // the contexts' own set-up work must be finished before the batch graph runs
         for (Ctx *c : b->ctx)
             if (cudaStreamSynchronize(c->stream) != cudaSuccess) return batch_fail(b, SNECT_ECUDA, "context stream");
+        if (b->kind > 0 && !b->d_cta) BATCH_CUDA(b, batch_lg_tune(b, b->stream));
         int rc = batch_build_graph(b);
         if (rc) return rc;
     }
@@ -2864,6 +3123,16 @@ int snect_batch_epoch(snect_batch *h, int32_t n_epochs) {
         b->launches += b->epoch_kernels;
     }
     for (Ctx *c : b->ctx) c->param_version++;
+    return SNECT_OK;
+}
+
+int snect_batch_tuning(const snect_batch *h, int32_t *ctas_per_sm, int32_t *min_entries_per_warp,
+                       double *sweep_ms) {
+    const Batch *b = reinterpret_cast<const Batch *>(h);
+    if (!b) return SNECT_EINVAL;
+    if (ctas_per_sm) *ctas_per_sm = b->tune_cps;
+    if (min_entries_per_warp) *min_entries_per_warp = b->tune_min_entries;
+    if (sweep_ms) *sweep_ms = b->tune_ms;
     return SNECT_OK;
 }
 

@@ -1,8 +1,8 @@
 """Batched form: several independent decompositions stepped together (snect_batch_*), through
 the C ABI.
 
-A batch runs, per wave, one sweep launch over the tiles of every problem and one launch of
-every problem's wave-end steps.  Each problem must end where it ends when run alone: the
+A batch runs, per wave, one sweep launch over every problem (CTAs allotted by entries, the
+launch shape autotuned at the first epoch) and one launch of every problem's wave-end steps.  Each problem must end where it ends when run alone: the
 fast sweep accumulates with atomics, so the comparison is to FP32 rounding after one epoch
 and on test RMSE after several.
 """
@@ -29,13 +29,15 @@ def cohorts():
     return [(p, lg) for p in ps for lg in (0.01, 0.3)]
 
 
-def run(cohorts, epochs, batched):
+def run(cohorts, epochs, batched, **kw):
     import paper_1711_08095_gb300 as snect
 
-    cs = [ctx(p, lam_g=lg) for p, lg in cohorts]
+    cs = [ctx(p, lam_g=lg, **kw) for p, lg in cohorts]
     if batched:
         b = snect.Batch(cs)
         b.epoch(epochs)
+        t = b.tuning()
+        assert t["ctas_per_sm"] >= 2 and t["sweep_ms"] > 0, t  # the autotuner ran
         b.close()
     else:
         for c in cs:
@@ -53,6 +55,20 @@ def test_batch_matches_separate_runs_after_one_epoch(cohorts, gpu_lib):
             scale = float(np.sqrt(np.mean(a.astype(np.float64) ** 2)))
             assert np.isfinite(b).all()
             assert np.abs(a - b).max() <= 1e-3 * scale + 1e-6, np.abs(a - b).max() / scale
+
+
+def test_bf16_batch_matches_separate_bf16_runs(cohorts, gpu_lib):
+    """Contexts whose sweep gathers gene rows in BF16 batch together; the batch keeps each
+    context's BF16 copy current (wave ends and network passes)."""
+    import paper_1711_08095_gb300 as snect
+
+    alone = run(cohorts, 2, False, precision=snect.BF16)
+    batched = run(cohorts, 2, True, precision=snect.BF16)
+    for ((Ga, Ua), la), ((Gb, Ub), lb) in zip(alone, batched):
+        for a, b in zip([Ga] + Ua, [Gb] + Ub):
+            scale = float(np.sqrt(np.mean(a.astype(np.float64) ** 2)))
+            assert np.abs(a - b).max() <= 1e-3 * scale + 1e-6, np.abs(a - b).max() / scale
+        assert abs(lb["rmse_test"] - la["rmse_test"]) <= 1e-3 * la["rmse_test"]
 
 
 def test_batch_reaches_separate_rmse(cohorts, gpu_lib):
