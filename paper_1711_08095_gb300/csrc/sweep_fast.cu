@@ -873,7 +873,7 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
             w2v[v] = acc;
         }
     };
-    auto load_rec = [&](int64_t e, bool ok) {
+    auto load_rec = [&](int e, bool ok) {
         Rec r;
         r.i = r.j = r.k = -1;
         r.x = 0.f;
@@ -886,16 +886,19 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
         }
         return r;
     };
-    Rec nxt = load_rec(lo + g, act && lo + g < hi);
-    for (int64_t base = lo; base < hi; base += E) {
-        const int64_t e = base + g;
-        const bool valid = act && e < hi;
+    // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
+    const int lo32 = (int)lo, hi32 = (int)hi;
+    Rec nxt = load_rec(lo32 + g, act && lo32 + g < hi32);
+    for (int base = lo32; base < hi32; base += E) {
+        const int e = base + g;
+        const bool valid = act && e < hi32;
         const Rec cur = nxt;
-        nxt = load_rec(e + E, act && e + E < hi);  // one step ahead
+        nxt = load_rec(e + E, act && e + E < hi32);  // one step ahead
         float b[VEC];
         if (valid) {
+            const int bo = cur.j * J2 + m * VEC;
             if constexpr (GB) {
-                const uint2 h = __ldg(reinterpret_cast<const uint2 *>(A.U2h + (int64_t)cur.j * J2 + m * VEC));
+                const uint2 h = __ldg(reinterpret_cast<const uint2 *>(A.U2h + bo));
                 const float2 lo2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.x));
                 const float2 hi2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.y));
                 b[0] = lo2.x;
@@ -903,23 +906,47 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
                 b[2] = hi2.x;
                 b[3] = hi2.y;
             } else if constexpr (VEC == 4) {
-                const float4 t4 = __ldg(reinterpret_cast<const float4 *>(A.U2 + (int64_t)cur.j * J2 + m * VEC));
+                const float4 t4 = __ldg(reinterpret_cast<const float4 *>(A.U2 + bo));
                 b[0] = t4.x;
                 b[1] = t4.y;
                 b[2] = t4.z;
                 b[3] = t4.w;
             } else if constexpr (VEC == 2) {
-                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(A.U2 + (int64_t)cur.j * J2 + m * VEC));
+                const float2 t2 = __ldg(reinterpret_cast<const float2 *>(A.U2 + bo));
                 b[0] = t2.x;
                 b[1] = t2.y;
             } else {
-                b[0] = __ldg(A.U2 + (int64_t)cur.j * J2 + m);
+                b[0] = __ldg(A.U2 + bo);
             }
         } else {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) b[v] = 0.f;
         }
-        // the step's entries by run (one pass when the step lies inside one run)
+        // an entry's residual, its gene-row gradient and its share of s (b = 0 off the wave)
+        auto entry = [&](bool mine) {
+            float part = 0.f;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) part = fmaf(w2v[v], b[v], part);
+            const float xt = group_sum<L>(mine ? part : 0.f);
+            if (mine) {
+                const float r = xt - cur.x;
+                float *gb = A.gB + cur.j * A.rs2 + m * VEC;
+                if constexpr (VEC == 4)
+                    atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
+                else if constexpr (VEC == 2)
+                    atomicAdd(reinterpret_cast<float2 *>(gb), make_float2(r * w2v[0], r * w2v[1]));
+                else
+                    atomicAdd(gb, r * w2v[0]);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) sv[v] = fmaf(r, b[v], sv[v]);
+            }
+        };
+        // the common case: every entry of the step lies in the open run
+        if (__all_sync(FULL, !valid || (cur.i == ci && cur.k == ck))) {
+            entry(valid);
+            continue;
+        }
+        // otherwise the step's entries run by run
         unsigned pend = __ballot_sync(FULL, valid && m == 0);
         while (pend) {
             const int lead = __ffs(pend) - 1;
@@ -930,23 +957,7 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
             }
             const bool mine = valid && cur.i == ci && cur.k == ck;
             pend &= ~__ballot_sync(FULL, mine && m == 0);
-            float part = 0.f;
-            if (mine)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) part = fmaf(w2v[v], b[v], part);
-            const float xt = group_sum<L>(part);
-            if (mine) {
-                const float r = xt - cur.x;
-                float *gb = A.gB + (int64_t)cur.j * A.rs2 + m * VEC;
-                if constexpr (VEC == 4)
-                    atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
-                else if constexpr (VEC == 2)
-                    atomicAdd(reinterpret_cast<float2 *>(gb), make_float2(r * w2v[0], r * w2v[1]));
-                else
-                    atomicAdd(gb, r * w2v[0]);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) sv[v] = fmaf(r, b[v], sv[v]);
-            }
+            entry(mine);
         }
     }
     if (ci >= 0) close_run();
@@ -2328,11 +2339,16 @@ size_t sweep_smem(const Ctx *c) {
 // and the set-up table of per-wave row counts.  SNECT_SWEEP_KERNEL=warp in the environment
 // selects k_fast_sweep where the lane-group kernel would run (both are complete sweeps; the
 // switch exists to compare them).
+int row_stride(int J, int I3);
+
 template <int CJ1, int CJ2, int CJ3>
 int pick_sweep(const Ctx *c) {
     const int prec = c->cfg.precision;
     bool lg = false;
-    if constexpr (runs_path<CJ1, CJ2>()) lg = c->wcnt && (int64_t)c->d.I3 * CJ1 * CJ2 <= kGcAll;
+    if constexpr (runs_path<CJ1, CJ2>())
+        lg = c->wcnt && (int64_t)c->d.I3 * CJ1 * CJ2 <= kGcAll &&
+             (int64_t)c->d.I2 * row_stride(CJ2, c->d.I3) < INT32_MAX &&
+             (int64_t)c->d.I1 * row_stride(CJ1, c->d.I3) < INT32_MAX;  // 32-bit offsets in the sweep
     if (prec == SNECT_BF16_TC) return -1;
     if (prec == SNECT_BF16) return (lg && CJ2 % 4 == 0) ? 2 : -1;
     const char *env = getenv("SNECT_SWEEP_KERNEL");
