@@ -175,7 +175,8 @@ int snect_qr_post(snect_ctx *ctx, int32_t *skipped_modes);
  * batch is one CUDA graph: per wave, one sweep launch over every problem (each CTA serves one
  * problem, the CTAs allotted in proportion to the problems' entries) and one launch of every
  * problem's wave-end steps, then every problem's network pass.  The first snect_batch_epoch
- * autotunes the sweep launch (CTAs per SM, fewest entries per warp) by timing wave 0 of every
+ * autotunes the sweep launch (CTAs per SM, CTAs per resident slot, fewest entries per warp) by
+ * timing wave 0 of every
  * candidate at the current parameters, then clears what those trial sweeps accumulated and
  * puts back the curvature state their pre-work rewrote, so the batch steps every problem as
  * its own epochs would.  Each context then holds its own updated factors (snect_loss,
@@ -186,11 +187,12 @@ int snect_qr_post(snect_ctx *ctx, int32_t *skipped_modes);
 typedef struct snect_batch snect_batch;
 int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, void *stream);
 int snect_batch_epoch(snect_batch *batch, int32_t n_epochs);
-/* The autotuner's choice (zeros before the first epoch): tile CTAs per SM, fewest entries
- * per warp (0: no floor), and that configuration's sweep time on wave 0 in ms.  Host
- * pointers, each may be NULL. */
-int snect_batch_tuning(const snect_batch *batch, int32_t *ctas_per_sm, int32_t *min_entries_per_warp,
-                       double *sweep_ms);
+/* The autotuner's choice (zeros before the first epoch): resident tile CTAs per SM, tile CTAs
+ * launched per resident slot (above 1, each CTA takes a smaller share and fewer problems are
+ * in flight at once), fewest entries per warp (0: no floor), and that configuration's sweep
+ * time on wave 0 in ms.  Host pointers, each may be NULL. */
+int snect_batch_tuning(const snect_batch *batch, int32_t *ctas_per_sm, int32_t *oversubscription,
+                       int32_t *min_entries_per_warp, double *sweep_ms);
 /* kernels the batch has launched so far (its graphs' kernel nodes) */
 int64_t snect_batch_launch_count(const snect_batch *batch);
 const char *snect_batch_last_error(const snect_batch *batch);

@@ -136,7 +136,7 @@ def load(build_if_missing: bool = False):
         "snect_qr_post": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "snect_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(P), i32, P]),
         "snect_batch_epoch": (ctypes.c_int, [P, i32]),
-        "snect_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32),
+        "snect_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                               ctypes.POINTER(ctypes.c_double)]),
         "snect_batch_launch_count": (ctypes.c_int64, [P]),
         "snect_batch_last_error": (ctypes.c_char_p, [P]),
@@ -455,11 +455,12 @@ class Batch:
         return int(self._lib.snect_batch_launch_count(self._h))
 
     def tuning(self):
-        """The autotuner's choice: dict(ctas_per_sm, min_entries_per_warp, sweep_ms)."""
-        a, m = ctypes.c_int32(), ctypes.c_int32()
+        """The autotuner's choice: dict(ctas_per_sm, oversubscription, min_entries_per_warp,
+        sweep_ms)."""
+        a, o, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         ms = ctypes.c_double()
-        self._lib.snect_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(m), ctypes.byref(ms))
-        return dict(ctas_per_sm=a.value, min_entries_per_warp=m.value, sweep_ms=ms.value)
+        self._lib.snect_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(o), ctypes.byref(m), ctypes.byref(ms))
+        return dict(ctas_per_sm=a.value, oversubscription=o.value, min_entries_per_warp=m.value, sweep_ms=ms.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -888,15 +888,10 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     };
     // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
     const int lo32 = (int)lo, hi32 = (int)hi;
-    Rec nxt = load_rec(lo32 + g, act && lo32 + g < hi32);
-    for (int base = lo32; base < hi32; base += E) {
-        const int e = base + g;
-        const bool valid = act && e < hi32;
-        const Rec cur = nxt;
-        nxt = load_rec(e + E, act && e + E < hi32);  // one step ahead
-        float b[VEC];
-        if (valid) {
-            const int bo = cur.j * J2 + m * VEC;
+    // this lane's VEC components of the gene row of record r (zeros when !ok)
+    auto gather = [&](const Rec &r, bool ok, float (&b)[VEC]) {
+        if (ok) {
+            const int bo = r.j * J2 + m * VEC;
             if constexpr (GB) {
                 const uint2 h = __ldg(reinterpret_cast<const uint2 *>(A.U2h + bo));
                 const float2 lo2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.x));
@@ -922,6 +917,18 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
 #pragma unroll
             for (int v = 0; v < VEC; ++v) b[v] = 0.f;
         }
+    };
+    // software pipeline: records two steps ahead, gene rows one step ahead
+    Rec cur = load_rec(lo32 + g, act && lo32 + g < hi32);
+    Rec nxt = load_rec(lo32 + g + E, act && lo32 + g + E < hi32);
+    float b[VEC];
+    gather(cur, act && lo32 + g < hi32, b);
+    for (int base = lo32; base < hi32; base += E) {
+        const int e = base + g;
+        const bool valid = act && e < hi32;
+        const Rec nn = load_rec(e + 2 * E, act && e + 2 * E < hi32);
+        float bn[VEC];
+        gather(nxt, act && e + E < hi32, bn);
         // an entry's residual, its gene-row gradient and its share of s (b = 0 off the wave)
         auto entry = [&](bool mine) {
             float part = 0.f;
@@ -941,24 +948,26 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
                 for (int v = 0; v < VEC; ++v) sv[v] = fmaf(r, b[v], sv[v]);
             }
         };
-        // the common case: every entry of the step lies in the open run
         if (__all_sync(FULL, !valid || (cur.i == ci && cur.k == ck))) {
-            entry(valid);
-            continue;
-        }
-        // otherwise the step's entries run by run
-        unsigned pend = __ballot_sync(FULL, valid && m == 0);
-        while (pend) {
-            const int lead = __ffs(pend) - 1;
-            const int ri = __shfl_sync(FULL, cur.i, lead), rk = __shfl_sync(FULL, cur.k, lead);
-            if (ri != ci || rk != ck) {
-                if (ci >= 0) close_run();
-                open_run(ri, rk);
+            entry(valid);  // the common case: every entry of the step lies in the open run
+        } else {           // otherwise the step's entries run by run
+            unsigned pend = __ballot_sync(FULL, valid && m == 0);
+            while (pend) {
+                const int lead = __ffs(pend) - 1;
+                const int ri = __shfl_sync(FULL, cur.i, lead), rk = __shfl_sync(FULL, cur.k, lead);
+                if (ri != ci || rk != ck) {
+                    if (ci >= 0) close_run();
+                    open_run(ri, rk);
+                }
+                const bool mine = valid && cur.i == ci && cur.k == ck;
+                pend &= ~__ballot_sync(FULL, mine && m == 0);
+                entry(mine);
             }
-            const bool mine = valid && cur.i == ci && cur.k == ck;
-            pend &= ~__ballot_sync(FULL, mine && m == 0);
-            entry(mine);
         }
+        cur = nxt;
+        nxt = nn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) b[v] = bn[v];
     }
     if (ci >= 0) close_run();
     flush_m();
@@ -2719,6 +2728,7 @@ struct Batch {
     int32_t *d_cta = nullptr;
     int32_t *d_prob_ctas = nullptr;       // [n_waves][P]
     int32_t tune_cps = 0;                 // autotuned: tile CTAs per SM
+    int32_t tune_over = 0;                // autotuned: tile CTAs per resident CTA slot
     int32_t tune_min_entries = 0;         // autotuned: fewest entries a warp is given
     double tune_ms = 0.0;                 // the chosen configuration's sweep time on wave 0
     void *d_bf = nullptr;                 // BF16 copies to refresh after the network passes
@@ -2818,10 +2828,13 @@ cudaError_t batch_clear_acc(Batch *b, cudaStream_t st) {
     return cudaSuccess;
 }
 
-// Autotuner of the lane-group batch sweep: every candidate (tile CTAs per SM, fewest entries
-// per warp) sweeps wave 0 at the current parameters, timed with CUDA events (best of two after
-// a warm-up launch); its accumulations are cleared again.  Then the per-wave allotment tables
-// of the fastest candidate are built and uploaded.
+// Autotuner of the lane-group batch sweep: every candidate (resident tile CTAs per SM, tile
+// CTAs per resident slot, fewest entries per warp) sweeps wave 0 at the current parameters,
+// timed with CUDA events (best of two after a warm-up launch); its accumulations are cleared
+// again.  Then the per-wave allotment tables of the fastest candidate are built and uploaded.
+// More tile CTAs than resident slots make each CTA's share smaller; the CTAs are dispatched in
+// index order, which follows the problems, so fewer problems' factors and accumulators are in
+// use at once (the batch's rows and accumulators together outgrow the L2).
 cudaError_t batch_lg_tune(Batch *b, cudaStream_t st) {
     const Dims &d = b->d;
     int per_sm = 1, sms = 1;
@@ -2846,10 +2859,11 @@ cudaError_t batch_lg_tune(Batch *b, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     std::vector<int32_t> prob, rank, pc;
     double best = 1e30;
-    for (int cps = 2; cps <= std::max(2, per_sm) && e == cudaSuccess; ++cps) {
+    for (int cps = 2; cps <= std::max(2, per_sm) && e == cudaSuccess; ++cps)
+      for (int over : {1, 4})
         for (int64_t me : {(int64_t)0, (int64_t)2048}) {
             if (e != cudaSuccess) break;
-            const int tiles = std::max(cps * sms - b->P, b->P);
+            const int tiles = std::max(over * cps * sms - b->P, b->P);
             lg_allot(b, 0, tiles, me, prob, rank, pc);
             const int T = (int)prob.size();
             std::vector<int32_t> h(prob);
@@ -2875,11 +2889,11 @@ cudaError_t batch_lg_tune(Batch *b, cudaStream_t st) {
             if (e == cudaSuccess && ms_best < best) {
                 best = ms_best;
                 b->tune_cps = cps;
+                b->tune_over = over;
                 b->tune_min_entries = (int32_t)me;
                 b->tune_ms = ms_best;
             }
         }
-    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     for (int p = 0; p < b->P; ++p) {
@@ -2896,7 +2910,7 @@ cudaError_t batch_lg_tune(Batch *b, cudaStream_t st) {
         if (q) cudaFree(q);
     if (e != cudaSuccess) return e;
     // the chosen allotment for every wave
-    const int tiles = std::max(b->tune_cps * sms - b->P, b->P);
+    const int tiles = std::max(b->tune_over * b->tune_cps * sms - b->P, b->P);
     std::vector<int32_t> all, allpc;
     b->lg_tiles.assign((size_t)b->n_waves, 0);
     b->lg_off.assign((size_t)b->n_waves, 0);
@@ -3142,11 +3156,12 @@ int snect_batch_epoch(snect_batch *h, int32_t n_epochs) {
     return SNECT_OK;
 }
 
-int snect_batch_tuning(const snect_batch *h, int32_t *ctas_per_sm, int32_t *min_entries_per_warp,
-                       double *sweep_ms) {
+int snect_batch_tuning(const snect_batch *h, int32_t *ctas_per_sm, int32_t *oversubscription,
+                       int32_t *min_entries_per_warp, double *sweep_ms) {
     const Batch *b = reinterpret_cast<const Batch *>(h);
     if (!b) return SNECT_EINVAL;
     if (ctas_per_sm) *ctas_per_sm = b->tune_cps;
+    if (oversubscription) *oversubscription = b->tune_over;
     if (min_entries_per_warp) *min_entries_per_warp = b->tune_min_entries;
     if (sweep_ms) *sweep_ms = b->tune_ms;
     return SNECT_OK;
