@@ -35,6 +35,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "contract.cuh"
 #include "tc.cuh"
 
@@ -732,12 +734,14 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
 // platform, then patient), so no tile claim and no CTA barrier sit in the loop; a run cut by a
 // range boundary is closed by both warps, each adding its part (every sum is linear).
 //
-// GB = 1 gathers the gene rows from a BF16 copy of U2 (VEC = 4 BF16 = 8 bytes per lane); all
-// arithmetic, the gradients and the factors stay FP32.
+// GB = 1 gathers the gene rows from a BF16 copy of U2 (VEC = 8 BF16 = 16 bytes per lane, so
+// 2 lanes per entry at J2 = 16); all arithmetic, the gradients and the factors stay FP32.
 
+// BF16 gathers take 8 components per lane (one 16-byte load of a 32-byte row, 2 lanes per
+// entry, 16 entries per warp step); FP32 gathers 4 (one 16-byte load), else 2 or 1.
 template <int CJ2, int GB>
 struct LaneGroup {
-    static constexpr int VEC = (GB || CJ2 % 4 == 0) ? 4 : (CJ2 % 2 == 0 ? 2 : 1);
+    static constexpr int VEC = GB ? 8 : (CJ2 % 4 == 0 ? 4 : (CJ2 % 2 == 0 ? 2 : 1));
     static constexpr int L = CJ2 / VEC;  // lanes per entry
     static constexpr int E = 32 / L;     // entries per step
 };
@@ -780,7 +784,7 @@ __device__ __forceinline__ float slot_sum(float x) {
 
 // CTAs per SM the lane-group kernel's registers are cut for (its first CTAs also run the
 // dense pre-work, whose 16 x 16 eigen-solves need more than 64 registers)
-template <int CJ1, int CJ2>
+template <int CJ1, int CJ2, int GB = 0>
 constexpr int lg_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
 
 // The lane-group sweep of one problem's wave by the CTA's warps: W warps share the wave,
@@ -888,47 +892,62 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     };
     // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
     const int lo32 = (int)lo, hi32 = (int)hi;
-    // this lane's VEC components of the gene row of record r (zeros when !ok)
-    auto gather = [&](const Rec &r, bool ok, float (&b)[VEC]) {
-        if (ok) {
+    // this lane's VEC components of the gene row of record r (zeros when !ok), as loaded: VEC
+    // floats, or for BF16 gathers 8 BF16 values in one 16-byte word (unpacked when used, so the
+    // prefetched row takes 4 registers)
+    struct FRow {
+        float v[VEC];
+    };
+    using Raw = std::conditional_t<GB != 0, uint4, FRow>;
+    auto load_row = [&](const Rec &r, bool ok) {
+        Raw x;
+        if constexpr (GB) {
+            x = ok ? __ldg(reinterpret_cast<const uint4 *>(A.U2h + r.j * J2 + m * VEC)) : make_uint4(0u, 0u, 0u, 0u);
+        } else {
             const int bo = r.j * J2 + m * VEC;
-            if constexpr (GB) {
-                const uint2 h = __ldg(reinterpret_cast<const uint2 *>(A.U2h + bo));
-                const float2 lo2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.x));
-                const float2 hi2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h.y));
-                b[0] = lo2.x;
-                b[1] = lo2.y;
-                b[2] = hi2.x;
-                b[3] = hi2.y;
+            if (!ok) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) x.v[v] = 0.f;
             } else if constexpr (VEC == 4) {
                 const float4 t4 = __ldg(reinterpret_cast<const float4 *>(A.U2 + bo));
-                b[0] = t4.x;
-                b[1] = t4.y;
-                b[2] = t4.z;
-                b[3] = t4.w;
+                x.v[0] = t4.x;
+                x.v[1] = t4.y;
+                x.v[2] = t4.z;
+                x.v[3] = t4.w;
             } else if constexpr (VEC == 2) {
                 const float2 t2 = __ldg(reinterpret_cast<const float2 *>(A.U2 + bo));
-                b[0] = t2.x;
-                b[1] = t2.y;
+                x.v[0] = t2.x;
+                x.v[1] = t2.y;
             } else {
-                b[0] = __ldg(A.U2 + bo);
+                x.v[0] = __ldg(A.U2 + bo);
+            }
+        }
+        return x;
+    };
+    auto unpack = [&](const Raw &x, float (&b)[VEC]) {
+        if constexpr (GB) {  // BF16 values are the upper halves of FP32 words
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                b[2 * t] = __uint_as_float(w[t] << 16);
+                b[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
             }
         } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) b[v] = 0.f;
+            for (int v = 0; v < VEC; ++v) b[v] = x.v[v];
         }
     };
     // software pipeline: records two steps ahead, gene rows one step ahead
     Rec cur = load_rec(lo32 + g, act && lo32 + g < hi32);
     Rec nxt = load_rec(lo32 + g + E, act && lo32 + g + E < hi32);
-    float b[VEC];
-    gather(cur, act && lo32 + g < hi32, b);
+    Raw bnext = load_row(cur, act && lo32 + g < hi32);
     for (int base = lo32; base < hi32; base += E) {
         const int e = base + g;
         const bool valid = act && e < hi32;
+        float b[VEC];
+        unpack(bnext, b);
         const Rec nn = load_rec(e + 2 * E, act && e + 2 * E < hi32);
-        float bn[VEC];
-        gather(nxt, act && e + E < hi32, bn);
+        bnext = load_row(nxt, act && e + E < hi32);
         // an entry's residual, its gene-row gradient and its share of s (b = 0 off the wave)
         auto entry = [&](bool mine) {
             float part = 0.f;
@@ -938,7 +957,11 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
             if (mine) {
                 const float r = xt - cur.x;
                 float *gb = A.gB + cur.j * A.rs2 + m * VEC;
-                if constexpr (VEC == 4)
+                if constexpr (VEC == 8) {
+                    atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
+                    atomicAdd(reinterpret_cast<float4 *>(gb) + 1,
+                              make_float4(r * w2v[4], r * w2v[5], r * w2v[6], r * w2v[7]));
+                } else if constexpr (VEC == 4)
                     atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
                 else if constexpr (VEC == 2)
                     atomicAdd(reinterpret_cast<float2 *>(gb), make_float2(r * w2v[0], r * w2v[1]));
@@ -966,8 +989,6 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
         }
         cur = nxt;
         nxt = nn;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) b[v] = bn[v];
     }
     if (ci >= 0) close_run();
     flush_m();
@@ -977,7 +998,7 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
 }
 
 template <int CJ1, int CJ2, int CJ3, int GB>
-__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fast_sweep_lg(FastArgs A) {
+__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2, GB>()) k_fast_sweep_lg(FastArgs A) {
     extern __shared__ __align__(16) float sm[];
     if (blockIdx.x < kPreCtas) {  // the wave's dense pre-work, as in k_fast_sweep
         dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
@@ -991,7 +1012,7 @@ __global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>()) k_fas
 // problem's dense pre-work; every other CTA serves one problem (cta_prob), as CTA number
 // cta_rank of the prob_ctas[p] CTAs the batch's autotuned allotment gave that problem.
 template <int CJ1, int CJ2, int CJ3, int GB>
-__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2>())
+__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2, GB>())
     k_batch_sweep_lg(const FastArgs *__restrict__ probs, const int32_t *__restrict__ cta_prob,
                      const int32_t *__restrict__ cta_rank, const int32_t *__restrict__ prob_ctas, int32_t P) {
     extern __shared__ __align__(16) float sm[];
@@ -2359,7 +2380,7 @@ int pick_sweep(const Ctx *c) {
              (int64_t)c->d.I2 * row_stride(CJ2, c->d.I3) < INT32_MAX &&
              (int64_t)c->d.I1 * row_stride(CJ1, c->d.I3) < INT32_MAX;  // 32-bit offsets in the sweep
     if (prec == SNECT_BF16_TC) return -1;
-    if (prec == SNECT_BF16) return (lg && CJ2 % 4 == 0) ? 2 : -1;
+    if (prec == SNECT_BF16) return (lg && CJ2 % 8 == 0) ? 2 : -1;
     const char *env = getenv("SNECT_SWEEP_KERNEL");
     if (env && strcmp(env, "warp") == 0) return 0;
     return lg ? 1 : 0;
@@ -2370,7 +2391,7 @@ template <int CJ1, int CJ2, int CJ3>
 void (*sweep_kernel(const Ctx *c))(FastArgs) {
     if constexpr (runs_path<CJ1, CJ2>()) {
         if (c->sweep_kind == 1) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 0>;
-        if constexpr (CJ2 % 4 == 0)
+        if constexpr (CJ2 % 8 == 0)
             if (c->sweep_kind == 2) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 1>;
     }
     return c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
@@ -2779,7 +2800,7 @@ cudaError_t batch_lg_launch(Batch *b, const FastArgs *d_fast_w, const int32_t *d
     if constexpr (runs_path<CJ1, CJ2>()) {
         const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]);
         if (b->kind == 2) {
-            if constexpr (CJ2 % 4 == 0) {
+            if constexpr (CJ2 % 8 == 0) {
                 k_batch_sweep_lg<CJ1, CJ2, CJ3, 1><<<b->P + tiles, kFastThreads, smem, st>>>(d_fast_w, d_prob, d_rank,
                                                                                           d_pc, b->P);
                 return cudaGetLastError();
@@ -2807,7 +2828,7 @@ cudaError_t batch_lg_attr(Batch *b, int *per_sm) {
             return e;
         };
         if (b->kind == 2) {
-            if constexpr (CJ2 % 4 == 0) return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 1>);
+            if constexpr (CJ2 % 8 == 0) return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 1>);
             return cudaErrorInvalidValue;
         }
         return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 0>);
