@@ -734,14 +734,15 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
 // platform, then patient), so no tile claim and no CTA barrier sit in the loop; a run cut by a
 // range boundary is closed by both warps, each adding its part (every sum is linear).
 //
-// GB = 1 gathers the gene rows from a BF16 copy of U2 (VEC = 8 BF16 = 16 bytes per lane, so
-// 2 lanes per entry at J2 = 16); all arithmetic, the gradients and the factors stay FP32.
+// GB = 1 gathers the gene rows from a BF16 copy of U2 (VEC = 4 BF16 = 8 bytes per lane); all
+// arithmetic, the gradients and the factors stay FP32.
 
-// BF16 gathers take 8 components per lane (one 16-byte load of a 32-byte row, 2 lanes per
-// entry, 16 entries per warp step); FP32 gathers 4 (one 16-byte load), else 2 or 1.
+// 4 components per lane where J2 allows (FP32: one 16-byte load; BF16: one 8-byte load),
+// else 2 or 1.  (8 BF16 components per lane, 2 lanes per entry at J2 = 16, was measured slower:
+// 16-entry steps cross patient runs twice as often and a run's close costs twice the shuffles.)
 template <int CJ2, int GB>
 struct LaneGroup {
-    static constexpr int VEC = GB ? 8 : (CJ2 % 4 == 0 ? 4 : (CJ2 % 2 == 0 ? 2 : 1));
+    static constexpr int VEC = (GB || CJ2 % 4 == 0) ? 4 : (CJ2 % 2 == 0 ? 2 : 1);
     static constexpr int L = CJ2 / VEC;  // lanes per entry
     static constexpr int E = 32 / L;     // entries per step
 };
@@ -893,16 +894,16 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
     const int lo32 = (int)lo, hi32 = (int)hi;
     // this lane's VEC components of the gene row of record r (zeros when !ok), as loaded: VEC
-    // floats, or for BF16 gathers 8 BF16 values in one 16-byte word (unpacked when used, so the
-    // prefetched row takes 4 registers)
+    // floats, or for BF16 gathers 4 BF16 values in one 8-byte word (unpacked when used, so the
+    // prefetched row takes 2 registers)
     struct FRow {
         float v[VEC];
     };
-    using Raw = std::conditional_t<GB != 0, uint4, FRow>;
+    using Raw = std::conditional_t<GB != 0, uint2, FRow>;
     auto load_row = [&](const Rec &r, bool ok) {
         Raw x;
         if constexpr (GB) {
-            x = ok ? __ldg(reinterpret_cast<const uint4 *>(A.U2h + r.j * J2 + m * VEC)) : make_uint4(0u, 0u, 0u, 0u);
+            x = ok ? __ldg(reinterpret_cast<const uint2 *>(A.U2h + r.j * J2 + m * VEC)) : make_uint2(0u, 0u);
         } else {
             const int bo = r.j * J2 + m * VEC;
             if (!ok) {
@@ -926,9 +927,9 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     };
     auto unpack = [&](const Raw &x, float (&b)[VEC]) {
         if constexpr (GB) {  // BF16 values are the upper halves of FP32 words
-            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t w[2] = {x.x, x.y};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < 2; ++t) {
                 b[2 * t] = __uint_as_float(w[t] << 16);
                 b[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
             }
@@ -957,11 +958,7 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
             if (mine) {
                 const float r = xt - cur.x;
                 float *gb = A.gB + cur.j * A.rs2 + m * VEC;
-                if constexpr (VEC == 8) {
-                    atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
-                    atomicAdd(reinterpret_cast<float4 *>(gb) + 1,
-                              make_float4(r * w2v[4], r * w2v[5], r * w2v[6], r * w2v[7]));
-                } else if constexpr (VEC == 4)
+                if constexpr (VEC == 4)
                     atomicAdd(reinterpret_cast<float4 *>(gb), make_float4(r * w2v[0], r * w2v[1], r * w2v[2], r * w2v[3]));
                 else if constexpr (VEC == 2)
                     atomicAdd(reinterpret_cast<float2 *>(gb), make_float2(r * w2v[0], r * w2v[1]));
@@ -2288,8 +2285,11 @@ __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, i
 
 // The end of one wave for every problem of a batch: per problem one CTA takes the dense step
 // and the next ones its row steps (boff: prefix offsets of the problems' CTAs).
-template <int CJ1, int CJ2, int CJ3>
-__global__ void __launch_bounds__(256)
+// MINB: CTAs per SM the registers are cut for.  At 16 x 16 the thread-per-row step wants ~254
+// registers (one CTA per SM); MINB = 2 caps it at 128, letting part of each row's packed
+// Cholesky factor spill to L1-cached local memory in exchange for twice the rows in flight.
+template <int CJ1, int CJ2, int CJ3, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
     k_batch_wave_end(const DenseArgs *__restrict__ dargs, const RowArgs *__restrict__ rargs,
                      const int32_t *__restrict__ boff, int32_t P) {
     extern __shared__ __align__(16) float smw[];
@@ -2380,7 +2380,7 @@ int pick_sweep(const Ctx *c) {
              (int64_t)c->d.I2 * row_stride(CJ2, c->d.I3) < INT32_MAX &&
              (int64_t)c->d.I1 * row_stride(CJ1, c->d.I3) < INT32_MAX;  // 32-bit offsets in the sweep
     if (prec == SNECT_BF16_TC) return -1;
-    if (prec == SNECT_BF16) return (lg && CJ2 % 8 == 0) ? 2 : -1;
+    if (prec == SNECT_BF16) return (lg && CJ2 % 4 == 0) ? 2 : -1;
     const char *env = getenv("SNECT_SWEEP_KERNEL");
     if (env && strcmp(env, "warp") == 0) return 0;
     return lg ? 1 : 0;
@@ -2391,7 +2391,7 @@ template <int CJ1, int CJ2, int CJ3>
 void (*sweep_kernel(const Ctx *c))(FastArgs) {
     if constexpr (runs_path<CJ1, CJ2>()) {
         if (c->sweep_kind == 1) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 0>;
-        if constexpr (CJ2 % 8 == 0)
+        if constexpr (CJ2 % 4 == 0)
             if (c->sweep_kind == 2) return k_fast_sweep_lg<CJ1, CJ2, CJ3, 1>;
     }
     return c->wcnt ? k_fast_sweep<CJ1, CJ2, CJ3, false> : k_fast_sweep<CJ1, CJ2, CJ3, true>;
@@ -2753,6 +2753,7 @@ struct Batch {
     int32_t tune_min_entries = 0;         // autotuned: fewest entries a warp is given
     double tune_ms = 0.0;                 // the chosen configuration's sweep time on wave 0
     void *d_bf = nullptr;                 // BF16 copies to refresh after the network passes
+    int32_t we_minb = 1;                  // wave-end variant: CTAs per SM its registers are cut for
     int64_t bf_max = 0;
 };
 
@@ -2800,7 +2801,7 @@ cudaError_t batch_lg_launch(Batch *b, const FastArgs *d_fast_w, const int32_t *d
     if constexpr (runs_path<CJ1, CJ2>()) {
         const size_t smem = sweep_smem<CJ1, CJ2, CJ3>(b->ctx[0]);
         if (b->kind == 2) {
-            if constexpr (CJ2 % 8 == 0) {
+            if constexpr (CJ2 % 4 == 0) {
                 k_batch_sweep_lg<CJ1, CJ2, CJ3, 1><<<b->P + tiles, kFastThreads, smem, st>>>(d_fast_w, d_prob, d_rank,
                                                                                           d_pc, b->P);
                 return cudaGetLastError();
@@ -2828,7 +2829,7 @@ cudaError_t batch_lg_attr(Batch *b, int *per_sm) {
             return e;
         };
         if (b->kind == 2) {
-            if constexpr (CJ2 % 8 == 0) return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 1>);
+            if constexpr (CJ2 % 4 == 0) return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 1>);
             return cudaErrorInvalidValue;
         }
         return set(k_batch_sweep_lg<CJ1, CJ2, CJ3, 0>);
@@ -2962,18 +2963,24 @@ cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int CJ1, int CJ2, int CJ3>
-cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
+template <int CJ1, int CJ2, int CJ3, int MINB>
+cudaError_t batch_wave_end_launch(Batch *b, int64_t w, cudaStream_t st) {
     const size_t smem = wave_end_smem(b->ctx[0]);
-    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_batch_wave_end<CJ1, CJ2, CJ3><<<b->wave_end_blocks, 256, smem, st>>>(b->d_dense + w * b->P, b->d_rows + w * b->P,
-                                                                     b->d_boff, b->P);
+    k_batch_wave_end<CJ1, CJ2, CJ3, MINB><<<b->wave_end_blocks, 256, smem, st>>>(
+        b->d_dense + w * b->P, b->d_rows + w * b->P, b->d_boff, b->P);
     return cudaGetLastError();
+}
+
+template <int CJ1, int CJ2, int CJ3>
+cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
+    if (b->we_minb == 2) return batch_wave_end_launch<CJ1, CJ2, CJ3, 2>(b, w, st);
+    return batch_wave_end_launch<CJ1, CJ2, CJ3, 1>(b, w, st);
 }
 
 template <int CJ1, int CJ2, int CJ3>
@@ -3094,6 +3101,11 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     b->d = c0->d;
     b->n_waves = c0->n_waves;
     b->kind = c0->sweep_kind;
+    {  // wave-end variant (both compute the same numbers); SNECT_BATCH_WAVE_END_CTAS=2 picks
+       // the one cut to 128 registers
+        const char *env = getenv("SNECT_BATCH_WAVE_END_CTAS");
+        b->we_minb = (env && strcmp(env, "2") == 0) ? 2 : 1;
+    }
     const int64_t W = b->n_waves, P = n;
     std::vector<FastArgs> hf((size_t)(W * P));
     std::vector<DenseArgs> hd((size_t)(W * P));
