@@ -2285,11 +2285,8 @@ __global__ void __launch_bounds__(256) k_fast_wave_end(DenseArgs A, RowArgs R, i
 
 // The end of one wave for every problem of a batch: per problem one CTA takes the dense step
 // and the next ones its row steps (boff: prefix offsets of the problems' CTAs).
-// MINB: CTAs per SM the registers are cut for.  At 16 x 16 the thread-per-row step wants ~254
-// registers (one CTA per SM); MINB = 2 caps it at 128, letting part of each row's packed
-// Cholesky factor spill to L1-cached local memory in exchange for twice the rows in flight.
-template <int CJ1, int CJ2, int CJ3, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB)
+template <int CJ1, int CJ2, int CJ3>
+__global__ void __launch_bounds__(256)
     k_batch_wave_end(const DenseArgs *__restrict__ dargs, const RowArgs *__restrict__ rargs,
                      const int32_t *__restrict__ boff, int32_t P) {
     extern __shared__ __align__(16) float smw[];
@@ -2753,7 +2750,6 @@ struct Batch {
     int32_t tune_min_entries = 0;         // autotuned: fewest entries a warp is given
     double tune_ms = 0.0;                 // the chosen configuration's sweep time on wave 0
     void *d_bf = nullptr;                 // BF16 copies to refresh after the network passes
-    int32_t we_minb = 1;                  // wave-end variant: CTAs per SM its registers are cut for
     int64_t bf_max = 0;
 };
 
@@ -2963,24 +2959,18 @@ cudaError_t batch_sweep_k(Batch *b, int64_t w, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int CJ1, int CJ2, int CJ3, int MINB>
-cudaError_t batch_wave_end_launch(Batch *b, int64_t w, cudaStream_t st) {
-    const size_t smem = wave_end_smem(b->ctx[0]);
-    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    k_batch_wave_end<CJ1, CJ2, CJ3, MINB><<<b->wave_end_blocks, 256, smem, st>>>(
-        b->d_dense + w * b->P, b->d_rows + w * b->P, b->d_boff, b->P);
-    return cudaGetLastError();
-}
-
 template <int CJ1, int CJ2, int CJ3>
 cudaError_t batch_wave_end_k(Batch *b, int64_t w, cudaStream_t st) {
-    if (b->we_minb == 2) return batch_wave_end_launch<CJ1, CJ2, CJ3, 2>(b, w, st);
-    return batch_wave_end_launch<CJ1, CJ2, CJ3, 1>(b, w, st);
+    const size_t smem = wave_end_smem(b->ctx[0]);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_wave_end<CJ1, CJ2, CJ3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    k_batch_wave_end<CJ1, CJ2, CJ3><<<b->wave_end_blocks, 256, smem, st>>>(b->d_dense + w * b->P, b->d_rows + w * b->P,
+                                                                     b->d_boff, b->P);
+    return cudaGetLastError();
 }
 
 template <int CJ1, int CJ2, int CJ3>
@@ -3101,11 +3091,7 @@ int snect_batch_create(snect_batch **out, snect_ctx *const *ctxs, int32_t n, voi
     b->d = c0->d;
     b->n_waves = c0->n_waves;
     b->kind = c0->sweep_kind;
-    {  // wave-end variant (both compute the same numbers); SNECT_BATCH_WAVE_END_CTAS=2 picks
-       // the one cut to 128 registers
-        const char *env = getenv("SNECT_BATCH_WAVE_END_CTAS");
-        b->we_minb = (env && strcmp(env, "2") == 0) ? 2 : 1;
-    }
+
     const int64_t W = b->n_waves, P = n;
     std::vector<FastArgs> hf((size_t)(W * P));
     std::vector<DenseArgs> hd((size_t)(W * P));
