@@ -731,18 +731,23 @@ def main():
                                                       h["tidx"], h["tval"]])
     d2h = 6 * 8 + sum(int(np.prod(u.shape)) * 4 for u in p.U0) + int(np.prod(p.G0.shape)) * 4
     job_epochs = 10
-    e2e_times = []
+    e2e_times, phases = [], []
     for _ in range(args.e2e_jobs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c = snect.Snect(p.I, p.J, h["idx"], h["val"], h["edges"], h["w"], h["G0"], h["U0"], lam=p.lam,
                         lam_g=p.lam_g, lr=p.lr, batch=0, precision=prec)
+        t1 = time.perf_counter()  # snect_init returns after its set-up work has finished
         c.epoch(job_epochs)
-        job_loss = c.loss(h["tidx"], h["tval"])
+        job_loss = c.loss(h["tidx"], h["tval"])  # synchronises: the epochs are done
+        t2 = time.perf_counter()
         c.get_factors()
-        e2e_times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        e2e_times.append(t3 - t0)
+        phases.append((t1 - t0, t2 - t1, t3 - t2))
         c.close()
     e2e_s = statistics.median(e2e_times)
+    ph = phases[e2e_times.index(sorted(e2e_times)[len(e2e_times) // 2])] if phases else (0, 0, 0)
 
     pk, pk_kind = peaks()
     # roofline of the sweep kernel: algorithmic bytes per entry = 16 (entry record) +
@@ -767,7 +772,10 @@ def main():
                 "d2h_bytes_per_step": int(d2h),
                 "step": "one training job: snect_init from pinned host buffers, %d epochs, objective and "
                         "factors read back (median of %d jobs, %.1f ms)" % (job_epochs, len(e2e_times), e2e_s * 1e3),
-                "jobs_ms": [round(x * 1e3, 2) for x in e2e_times]},
+                "jobs_ms": [round(x * 1e3, 2) for x in e2e_times],
+                "median_job_phases_ms": {"init: host-to-device copy and set-up": round(ph[0] * 1e3, 3),
+                                         "epochs (graph capture on the first) and objective": round(ph[1] * 1e3, 3),
+                                         "factors read back": round(ph[2] * 1e3, 3)}},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
                      "frac": (achieved / pk) if achieved else None,
