@@ -14,22 +14,25 @@ namespace snect {
 namespace {
 thread_local std::string g_init_error;
 
+// A context's device buffers come from the library's per-device memory pool, in stream order on
+// the context's stream: memory a destroyed context returns stays mapped in the pool, so the
+// next context's set-up reuses it instead of mapping and unmapping hundreds of megabytes.
 template <typename T>
 int dmalloc(Ctx *c, T **p, int64_t count) {
     *p = nullptr;
     if (count <= 0) return SNECT_OK;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+    cudaError_t e = scratch_alloc(c, p, sizeof(T) * (size_t)count);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
-        return fail(c, SNECT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return fail(c, SNECT_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     }
     return SNECT_OK;
 }
 
 template <typename T>
-void dfree(T *&p) {
-    if (p) cudaFree(p);
+void dfree(Ctx *c, T *&p) {
+    if (p) cudaFreeAsync(p, c->stream);
     p = nullptr;
 }
 
@@ -62,35 +65,35 @@ void free_all(Ctx *c) {
     c->aux_begin.clear();
     c->aux_end.clear();
     free_fast(c);
-    dfree(c->rec);
+    dfree(c, c->rec);
     for (int m = 0; m < 3; ++m) {
-        dfree(c->cnt[m]);
-        dfree(c->U[m]);
-        dfree(c->grp_pos[m]);
-        dfree(c->grp_head[m]);
+        dfree(c, c->cnt[m]);
+        dfree(c, c->U[m]);
+        dfree(c, c->grp_pos[m]);
+        dfree(c, c->grp_head[m]);
     }
-    dfree(c->G);
-    dfree(c->edges);
-    dfree(c->ew);
-    dfree(c->csr_ptr);
-    dfree(c->csr_col);
-    dfree(c->csr_w);
-    dfree(c->heavy_rows);
-    dfree(c->snap);
-    dfree(c->gbuf);
-    dfree(c->part);
-    dfree(c->wtable);
-    dfree(c->fold_part);
-    dfree(c->q_jk);
-    dfree(c->q_val);
-    dfree(c->q_u);
-    dfree(c->q_status);
-    dfree(c->score);
-    dfree(c->taken);
-    dfree(c->top_i);
-    dfree(c->top_s);
-    dfree(c->lacc);
-    dfree(c->flag);
+    dfree(c, c->G);
+    dfree(c, c->edges);
+    dfree(c, c->ew);
+    dfree(c, c->csr_ptr);
+    dfree(c, c->csr_col);
+    dfree(c, c->csr_w);
+    dfree(c, c->heavy_rows);
+    dfree(c, c->snap);
+    dfree(c, c->gbuf);
+    dfree(c, c->part);
+    dfree(c, c->wtable);
+    dfree(c, c->fold_part);
+    dfree(c, c->q_jk);
+    dfree(c, c->q_val);
+    dfree(c, c->q_u);
+    dfree(c, c->q_status);
+    dfree(c, c->score);
+    dfree(c, c->taken);
+    dfree(c, c->top_i);
+    dfree(c, c->top_s);
+    dfree(c, c->lacc);
+    dfree(c, c->flag);
 }
 
 int check_config(const snect_config *cfg, std::string *why) {
@@ -174,9 +177,9 @@ int build_epoch_graph(Ctx *c) {
 
 int ensure_query_capacity(Ctx *c, int64_t n) {
     if (n <= c->q_cap) return SNECT_OK;
-    dfree(c->q_jk);
-    dfree(c->q_val);
-    dfree(c->fold_part);
+    dfree(c, c->q_jk);
+    dfree(c, c->q_val);
+    dfree(c, c->fold_part);
     c->q_cap = 0;
     int64_t cap = std::max<int64_t>(n, 1 << 16);
     int rc = dmalloc(c, &c->q_jk, cap);

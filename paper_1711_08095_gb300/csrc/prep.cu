@@ -385,13 +385,16 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     c->max_degree = hf[1];
     if (c->max_degree > kHeavyDegree) {  // hub rows for the chunked network pass
         std::vector<int32_t> ptr((size_t)I2 + 1), heavy;
-        SNECT_CUDA(c, cudaMemcpy(ptr.data(), c->csr_ptr, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+        SNECT_CUDA(c, cudaMemcpyAsync(ptr.data(), c->csr_ptr, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost,
+                                      c->stream));
+        SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int32_t k = 0; k < I2; ++k)
             if (ptr[k + 1] - ptr[k] > kHeavyDegree) heavy.push_back(k);
         c->n_heavy = (int64_t)heavy.size();
-        SNECT_CUDA(c, cudaMalloc((void **)&c->heavy_rows, sizeof(int32_t) * heavy.size()));
-        SNECT_CUDA(c, cudaMemcpy(c->heavy_rows, heavy.data(), sizeof(int32_t) * heavy.size(),
-                                 cudaMemcpyHostToDevice));
+        SNECT_CUDA(c, scratch_alloc(c, &c->heavy_rows, sizeof(int32_t) * heavy.size()));
+        SNECT_CUDA(c, cudaMemcpyAsync(c->heavy_rows, heavy.data(), sizeof(int32_t) * heavy.size(),
+                                      cudaMemcpyHostToDevice, c->stream));
+        SNECT_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
     }
     return SNECT_OK;
 }
@@ -452,7 +455,7 @@ int prep_fast_tiles(Ctx *c) {
         // larger than the entries themselves (else the sweep counts them with atomics)
         const int64_t cells = c->n_waves * ((int64_t)c->d.I1 + c->d.I2) * I3;
         if ((size_t)cells * sizeof(float) <= std::max<size_t>((size_t)64 << 20, sizeof(Rec) * (size_t)n)) {
-            if (cudaMalloc((void **)&c->wcnt, sizeof(float) * cells) == cudaSuccess) {
+            if (scratch_alloc(c, &c->wcnt, sizeof(float) * cells) == cudaSuccess) {
                 cudaMemsetAsync(c->wcnt, 0, sizeof(float) * cells, c->stream);
                 k_wave_row_counts<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, c->d.I1, c->d.I2, I3,
                                                                            c->wcnt);
@@ -501,14 +504,15 @@ int prep_fast_tiles(Ctx *c) {
     }
     c->n_tiles = (int64_t)ts.size();
     auto upload = [&](int32_t **dst, const std::vector<int32_t> &v) -> int {
-        SNECT_CUDA(c, cudaMalloc((void **)dst, sizeof(int32_t) * v.size()));
-        SNECT_CUDA(c, cudaMemcpy(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
+        SNECT_CUDA(c, scratch_alloc(c, dst, sizeof(int32_t) * v.size()));
+        SNECT_CUDA(c, cudaMemcpyAsync(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, c->stream));
         return SNECT_OK;
     };
     if ((rc = upload(&c->tile_start, ts)) || (rc = upload(&c->tile_len, tl)) || (rc = upload(&c->tile_k, tk)))
         return rc;
-    SNECT_CUDA(c, cudaMalloc((void **)&c->wave_nk, sizeof(float) * nk.size()));
-    SNECT_CUDA(c, cudaMemcpy(c->wave_nk, nk.data(), sizeof(float) * nk.size(), cudaMemcpyHostToDevice));
+    SNECT_CUDA(c, scratch_alloc(c, &c->wave_nk, sizeof(float) * nk.size()));
+    SNECT_CUDA(c, cudaMemcpyAsync(c->wave_nk, nk.data(), sizeof(float) * nk.size(), cudaMemcpyHostToDevice, c->stream));
+    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
     return SNECT_OK;
 }
 

@@ -2593,8 +2593,8 @@ cudaError_t refresh_bf16_rows(Ctx *c) {
 
 int init_fast(Ctx *c) {
     const Dims &d = c->d;
-    SNECT_CUDA(c, cudaMalloc((void **)&c->tile_ctr, sizeof(int32_t) * std::max<int64_t>(1, c->n_waves)));
-    SNECT_CUDA(c, cudaMalloc((void **)&c->macc, sizeof(float) * d.I3 * d.J1 * d.J2));
+    SNECT_CUDA(c, scratch_alloc(c, &c->tile_ctr, sizeof(int32_t) * std::max<int64_t>(1, c->n_waves)));
+    SNECT_CUDA(c, scratch_alloc(c, &c->macc, sizeof(float) * d.I3 * d.J1 * d.J2));
     SNECT_CUDA(c, cudaMemsetAsync(c->macc, 0, sizeof(float) * d.I3 * d.J1 * d.J2, c->stream));
     // moments: two buffers (this wave's, the previous wave's) + warm-start eigenvectors
     c->gram_stride = ((int64_t)d.J1 * d.J1 + d.J2 * d.J2 + 3) & ~3;
@@ -2602,20 +2602,20 @@ int init_fast(Ctx *c) {
     const int64_t gf = 2 * c->gram_stride + d.J1 * d.J1 + d.J2 * d.J2 + d.J3 * d.J3 + d.J1 + d.J2 + d.J3 +
                        (int64_t)d.I3 * d.J3 * d.J3;
     c->gram_floats = gf;
-    SNECT_CUDA(c, cudaMalloc((void **)&c->gram, sizeof(float) * gf));
+    SNECT_CUDA(c, scratch_alloc(c, &c->gram, sizeof(float) * gf));
     SNECT_CUDA(c, cudaMemsetAsync(c->gram, 0, sizeof(float) * gf, c->stream));
     // platform curvatures for the row steps (formed by each wave's pre-work)
-    SNECT_CUDA(c, cudaMalloc((void **)&c->curv, sizeof(float) * curv_stride(c)));
+    SNECT_CUDA(c, scratch_alloc(c, &c->curv, sizeof(float) * curv_stride(c)));
     SNECT_CUDA(c, cudaMemsetAsync(c->curv, 0, sizeof(float) * curv_stride(c), c->stream));
     for (int n = 0; n < 2; ++n) {
         const int64_t nf = (int64_t)(n ? d.I2 : d.I1) * row_stride(n ? d.J2 : d.J1, d.I3);
-        SNECT_CUDA(c, cudaMalloc((void **)&c->gacc[n], sizeof(float) * nf));
+        SNECT_CUDA(c, scratch_alloc(c, &c->gacc[n], sizeof(float) * nf));
         SNECT_CUDA(c, cudaMemsetAsync(c->gacc[n], 0, sizeof(float) * nf, c->stream));
     }
     SNECT_CUDA(c, SNECT_DISPATCH_RANKS(d.J1, d.J2, d.J3, init_sweep, c));
     if (c->sweep_kind < 0) SNECT_CUDA(c, SNECT_DISPATCH_TC(d.J1, d.J2, init_sweep_tc, c));
     if (c->sweep_kind == 2) {
-        SNECT_CUDA(c, cudaMalloc((void **)&c->U2h, sizeof(__nv_bfloat16) * (size_t)d.I2 * d.J2));
+        SNECT_CUDA(c, scratch_alloc(c, &c->U2h, sizeof(__nv_bfloat16) * (size_t)d.I2 * d.J2));
         SNECT_CUDA(c, refresh_bf16_rows(c));
     }
     SNECT_CUDA(c, cudaMemsetAsync(c->flag + 2, 0, 2 * sizeof(int32_t), c->stream));
@@ -2691,8 +2691,8 @@ int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA
 }
 
 void free_fast(Ctx *c) {
-    auto f = [](auto *&p) {
-        if (p) cudaFree(p);
+    auto f = [c](auto *&p) {
+        if (p) cudaFreeAsync(p, c->stream);
         p = nullptr;
     };
     f(c->tile_start);
