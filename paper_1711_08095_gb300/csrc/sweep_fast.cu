@@ -783,10 +783,11 @@ __device__ __forceinline__ float slot_sum(float x) {
     }
 }
 
-// CTAs per SM the lane-group kernel's registers are cut for (its first CTAs also run the
-// dense pre-work, whose 16 x 16 eigen-solves need more than 64 registers)
+// CTAs per SM the lane-group kernel's registers are cut for: 64 registers, with the dense
+// pre-work's 16 x 16 eigen-solves in the same kernel (measured: 4 CTAs per SM at 16 x 16
+// against 3 at 80 registers)
 template <int CJ1, int CJ2, int GB = 0>
-constexpr int lg_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
+constexpr int lg_min_blocks() { return 4; }
 
 // The lane-group sweep of one problem's wave by the CTA's warps: W warps share the wave,
 // this CTA's warps are w0, w0 + 1, ...  (sm: the CTA's dynamic shared memory)
