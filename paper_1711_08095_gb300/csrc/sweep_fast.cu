@@ -783,11 +783,15 @@ __device__ __forceinline__ float slot_sum(float x) {
     }
 }
 
-// CTAs per SM the lane-group kernel's registers are cut for: 64 registers, with the dense
-// pre-work's 16 x 16 eigen-solves in the same kernel (measured: 4 CTAs per SM at 16 x 16
-// against 3 at 80 registers)
+// CTAs per SM the lane-group kernels' registers are cut for.  The single-problem kernel fits
+// 64 registers at every compiled shape, the dense pre-work's 16 x 16 eigen-solves included
+// (measured at 16 x 16 x 5: 26.9 G entries/s at 4 CTAs per SM against 25.4 G at 3).  The batch
+// kernel keeps its problem's arguments in shared memory and spills at 64 registers for
+// 16 x 16, which halved its speed, so it is cut for 3 CTAs per SM there.
 template <int CJ1, int CJ2, int GB = 0>
 constexpr int lg_min_blocks() { return 4; }
+template <int CJ1, int CJ2, int GB = 0>
+constexpr int lg_batch_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
 
 // The lane-group sweep of one problem's wave by the CTA's warps: W warps share the wave,
 // this CTA's warps are w0, w0 + 1, ...  (sm: the CTA's dynamic shared memory)
@@ -1010,7 +1014,7 @@ __global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2, GB>()) k
 // problem's dense pre-work; every other CTA serves one problem (cta_prob), as CTA number
 // cta_rank of the prob_ctas[p] CTAs the batch's autotuned allotment gave that problem.
 template <int CJ1, int CJ2, int CJ3, int GB>
-__global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2, GB>())
+__global__ void __launch_bounds__(kFastThreads, lg_batch_min_blocks<CJ1, CJ2, GB>())
     k_batch_sweep_lg(const FastArgs *__restrict__ probs, const int32_t *__restrict__ cta_prob,
                      const int32_t *__restrict__ cta_rank, const int32_t *__restrict__ prob_ctas, int32_t P) {
     extern __shared__ __align__(16) float sm[];
