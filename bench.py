@@ -316,9 +316,9 @@ def serving(args, snect):
     pool_n = 256
     pool = [S.serving_query(m, q=q) for q in range(pool_n)]  # distinct queries, resubmitted in turn
     srv = ctx.serve(n_slots=16, mem_budget_bytes=512 << 20, max_cells=75_000)
-    # warm-up: every query of the pool once (every kernel and size path loaded and touched)
-    for jk, x, _ in pool:
-        srv.poll(srv.submit(jk, x, 10), 10)
+    # warm-up: every query of the pool once (every kernel and size path loaded and touched);
+    # the folded-in profiles go on to the subtype analysis
+    served_u = np.stack([srv.poll(srv.submit(jk, x, 10), 10)[0] for jk, x, _ in pool])
     lat, dt = serve_stream(srv, pool, S.poisson_arrivals(args.serve_queries, args.serve_rate))
     st = srv.stats()
     cells = np.array([len(pool[qi % pool_n][1]) for qi in range(len(lat))])
@@ -341,7 +341,7 @@ def serving(args, snect):
     out["max_concurrent_over_sweep"] = srv.stats()["max_concurrent"]
     srv.stop()
     ctx.close()
-    return out
+    return out, served_u
 
 
 def precision_form(p, snect, epochs=10):
@@ -504,9 +504,10 @@ def lockfree_ablation(snect):
 
 def analyses(snect, served_u):
     """Downstream analyses on the paper-scale planted serving model (core 16x16x5): the
-    personalised subtype matrix and its norms (Sec. 3.3) for a batch of served profiles in one
-    call, and k-means stratification of the 4,500 patient rows into 13 clusters (Sec. 3.1.1)
-    from 13 seeded random rows; wall time of each call through the C ABI."""
+    personalised subtype matrix and its norms (Sec. 3.3) for the served new patients' folded-in
+    profiles (else the 4,500 patient rows) in one call, and k-means stratification of the 4,500
+    patient rows into 13 clusters (Sec. 3.1.1) from 13 seeded random rows; wall time of each
+    call through the C ABI."""
     import snect_synth as S
 
     m = S.serving_model()
@@ -526,7 +527,8 @@ def analyses(snect, served_u):
     a, _, upd, inertia = c.kmeans(init, 100)
     tk = time.perf_counter() - t0
     c.close()
-    return {"subtype": {"profiles": int(u.shape[0]), "ms": ts * 1e3},
+    return {"subtype": {"profiles": int(u.shape[0]), "ms": ts * 1e3,
+                        "of": "served new patients' fold-in profiles" if served_u is not None else "patient rows"},
             "kmeans": {"rows": I[0], "k": 13, "centroid_updates": upd, "ms": tk * 1e3,
                        "cluster_sizes": np.bincount(a, minlength=13).tolist()}}
 
@@ -808,12 +810,13 @@ def main():
         line["parity_config"] = parity_config(snect)
     if rank == 0 and args.batched_scale > 0:
         line["batched_form"] = batched_form(args, snect)
+    served_u = None
     if rank == 0 and args.serve_queries > 0:
-        line["serving"] = serving(args, snect)
+        line["serving"], served_u = serving(args, snect)
     if rank == 0 and not args.no_ablation:
         line["lockfree_ablation"] = lockfree_ablation(snect)
     if rank == 0:
-        line["analyses"] = analyses(snect, None)
+        line["analyses"] = analyses(snect, served_u)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -15,10 +15,14 @@
 // (no fused multiply-add) -- and every centroid coordinate is a sum over the rows in ascending
 // order divided by the count.  The FP32 rows convert to FP64 exactly, so the distances, the
 // assignments and the centroids are the same numbers a sequential FP64 program with that order
-// computes.  Iterations are queued in chunks; a device flag set by the update step when a pass
+// computes.  After each pass a stable radix sort of (cluster, row) pairs lists every cluster's
+// rows in ascending order, so each (cluster, coordinate) thread of the update adds only its own
+// rows, in that order.  Iterations are queued in chunks; a device flag set by the update step when a pass
 // changed nothing turns the remaining launches of the chunk into no-ops, and the host reads it
 // between chunks.
 #include <math.h>
+
+#include <cub/cub.cuh>
 
 #include "common.cuh"
 
@@ -107,11 +111,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// one thread per (centroid, coordinate): the mean of the centroid's rows, summed in row order
+// first position in the sorted cluster ids at which the id is >= c
+__device__ __forceinline__ int64_t km_lower(const int32_t *__restrict__ keys, int64_t n, int32_t c) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// one thread per (centroid, coordinate): the mean of the centroid's rows, summed in ascending
+// row order (keys: the cluster ids sorted stably, rows: the row of each sorted position)
 __global__ void __launch_bounds__(256)
     k_km_update(const float *__restrict__ X, int64_t n, int32_t d, int32_t k, double *__restrict__ cent,
-                const int32_t *__restrict__ assign, const int32_t *__restrict__ changed, int32_t *__restrict__ done,
-                int32_t *__restrict__ updates) {
+                const int32_t *__restrict__ keys, const int32_t *__restrict__ rows,
+                const int32_t *__restrict__ changed, int32_t *__restrict__ done, int32_t *__restrict__ updates) {
     if (*done) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (*changed == 0) {  // the pass changed nothing: converged, the centroids stay
@@ -121,14 +136,15 @@ __global__ void __launch_bounds__(256)
     if (t == 0) *updates += 1;
     if (t >= k * d) return;
     const int c = t / d, p = t % d;
+    const int64_t lo = km_lower(keys, n, c), hi = km_lower(keys, n, c + 1);
     double s = 0.0;
-    int64_t cnt = 0;
-    for (int64_t i = 0; i < n; ++i)
-        if (assign[i] == c) {
-            s = __dadd_rn(s, (double)X[i * d + p]);
-            ++cnt;
-        }
-    if (cnt > 0) cent[t] = __ddiv_rn(s, (double)cnt);
+    for (int64_t q = lo; q < hi; ++q) s = __dadd_rn(s, (double)X[(int64_t)rows[q] * d + p]);
+    if (hi > lo) cent[t] = __ddiv_rn(s, (double)(hi - lo));
+}
+
+__global__ void k_iota(int32_t *__restrict__ v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
 }
 
 __global__ void __launch_bounds__(256)
@@ -183,10 +199,27 @@ int run_kmeans(Ctx *c, int32_t k, const double *init, int32_t max_iter, int32_t 
     const int64_t n = d.I1;
     double *cent = nullptr, *dinert = nullptr;
     int32_t *dassign = nullptr, *words = nullptr;  // words: changed, done, updates
+    int32_t *keys = nullptr, *rows_in = nullptr, *rows = nullptr;  // the stable (cluster, row) sort
+    void *sort_tmp = nullptr;
+    size_t sort_bytes = 0;
+    int end_bit = 1;
+    while (end_bit < 31 && (k >> end_bit)) ++end_bit;
     cudaError_t e = scratch_alloc(c, &cent, sizeof(double) * k * d.J1);
     if (e == cudaSuccess) e = scratch_alloc(c, &dinert, sizeof(double));
     if (e == cudaSuccess) e = scratch_alloc(c, &dassign, sizeof(int32_t) * n);
     if (e == cudaSuccess) e = scratch_alloc(c, &words, sizeof(int32_t) * 3);
+    if (e == cudaSuccess) e = scratch_alloc(c, &keys, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = scratch_alloc(c, &rows_in, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = scratch_alloc(c, &rows, sizeof(int32_t) * n);
+    if (e == cudaSuccess)
+        e = cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, dassign, keys, rows_in, rows, n, 0, end_bit,
+                                            c->stream);
+    if (e == cudaSuccess) e = scratch_alloc(c, &sort_tmp, std::max<size_t>(sort_bytes, 16));
+    if (e == cudaSuccess) {
+        k_iota<<<ceil_div(n, 256), 256, 0, c->stream>>>(rows_in, n);
+        c->launches++;
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(cent, init, sizeof(double) * k * d.J1, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dassign, 0xff, sizeof(int32_t) * n, c->stream);  // -1: none yet
     if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, sizeof(int32_t) * 3, c->stream);
@@ -198,9 +231,14 @@ int run_kmeans(Ctx *c, int32_t k, const double *init, int32_t max_iter, int32_t 
             e = cudaMemsetAsync(words, 0, sizeof(int32_t), c->stream);
             if (e != cudaSuccess) break;
             k_km_assign<<<grid_rows, 256, 0, c->stream>>>(c->U[0], n, d.J1, k, cent, dassign, words, words + 1);
-            k_km_update<<<grid_upd, 256, 0, c->stream>>>(c->U[0], n, d.J1, k, cent, dassign, words, words + 1,
+            e = cudaGetLastError();
+            if (e == cudaSuccess)  // each cluster's rows, in ascending order (a stable sort)
+                e = cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, dassign, keys, rows_in, rows, n, 0,
+                                                    end_bit, c->stream);
+            if (e != cudaSuccess) break;
+            k_km_update<<<grid_upd, 256, 0, c->stream>>>(c->U[0], n, d.J1, k, cent, keys, rows, words, words + 1,
                                                          words + 2);
-            c->launches += 2;
+            c->launches += 3;
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&done, words + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -218,7 +256,8 @@ int run_kmeans(Ctx *c, int32_t k, const double *init, int32_t max_iter, int32_t 
         e = cudaMemcpyAsync(centroids, cent, sizeof(double) * k * d.J1, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&upd, words + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&in, dinert, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    for (void *p : {(void *)cent, (void *)dinert, (void *)dassign, (void *)words})
+    for (void *p : {(void *)cent, (void *)dinert, (void *)dassign, (void *)words, (void *)keys, (void *)rows_in,
+                    (void *)rows, sort_tmp})
         if (p) cudaFreeAsync(p, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, SNECT_ECUDA, std::string("kmeans: ") + cudaGetErrorString(e));
