@@ -1550,73 +1550,21 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
     float *rows = sm;                           // kRowsPerThreadCta x JE: updated rows times sqrt(weight)
     float *sCk = rows + kRowsPerThreadCta * JE; // I3 packed lower triangles (NLP floats each), if they fit
     const bool stage = I3 * NLP <= kCkStage;
-    constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int sCount[kRowsPerThreadCta / 32];
-    __shared__ int sList[kRowsPerThreadCta];
-    {  // every thread stages its own row for the moments (weight cnt / n folded in as its square
-       // root) and finds whether the row takes a step in this wave (it has entries in it)
-        const int64_t row = r0 + threadIdx.x;
-        const bool valid = row < I;
-        float u[J];
-        int nrow = 0;
-        float n = 0.f;
-        if (valid) {
-            nrow = cnt[row];
-            if (do_step) {  // the row's entries per platform: the set-up table, or the sweep's counts
-                const float *wn = wc ? wc + row * I3 : g + row * RS + JP;
+    const int64_t row = r0 + threadIdx.x;
+    const bool valid = row < I;
+    // the row's inputs, all loads in flight together
+    float u[J], b[J];
+    int nrow = 0;
+    float n = 0.f;  // the row's entries in this wave
+    float *acc = g + row * RS;
+    // the row's entries per platform in this wave: the set-up table, or the sweep's counts
+    const float *wn = wc ? wc + row * I3 : acc + JP;
+    if (valid) {
+        nrow = cnt[row];
+        if (do_step) {
 #pragma unroll 4
-                for (int k = 0; k < I3; ++k) n += wn[k];
-            }
-        if constexpr (J % 2 == 0) {  // the row starts on an 8-byte boundary
-#pragma unroll
-            for (int p = 0; p < J; p += 2) {
-                const float2 v = *reinterpret_cast<const float2 *>(U + row * J + p);
-                u[p] = v.x;
-                u[p + 1] = v.y;
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < J; ++p) u[p] = U[row * J + p];
+            for (int k = 0; k < I3; ++k) n += wn[k];
         }
-        } else {
-#pragma unroll
-            for (int p = 0; p < J; ++p) u[p] = 0.f;
-        }
-        const float sw = sqrtf((float)nrow * inv_n);
-#pragma unroll
-        for (int p = 0; p < JE; ++p) rows[threadIdx.x * JE + p] = p < J ? sw * u[p] : 0.f;
-        const bool act = valid && do_step && n > 0.f;
-        const unsigned bal = __ballot_sync(FULL, act);
-        if (lane == 0) sCount[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < wid; ++w) off += sCount[w];
-        if (act) sList[off + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
-    }
-    int n_act = 0;
-    for (int w = 0; w < kRowsPerThreadCta / 32; ++w) n_act += sCount[w];
-    if (stage && do_step)  // lower triangles, row p at p (p + 1) / 2
-        for (int e = threadIdx.x; e < I3 * NLP; e += blockDim.x) {
-            const int k = e / NLP, t = e % NLP;
-            int p = 0;
-            while ((p + 1) * (p + 2) / 2 <= t) ++p;
-            const int q = t - p * (p + 1) / 2;
-            sCk[e] = t < NL ? Ckg[(int64_t)k * J * J + p * J + q] : 0.f;
-        }
-    __syncthreads();
-    // the rows that take a step, packed onto the first threads: a warp's rows all solve, where
-    // rows without entries in the wave would otherwise leave lanes idle through the solve
-    if (threadIdx.x < n_act) {
-        const int lr = sList[threadIdx.x];
-        const int64_t row = r0 + lr;
-        float u[J], b[J];
-        const int nrow = cnt[row];
-        float *acc = g + row * RS;
-        const float *wn = wc ? wc + row * I3 : acc + JP;
-        float n = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < I3; ++k) n += wn[k];
         if constexpr (J % 2 == 0) {  // the row starts on an 8-byte boundary
 #pragma unroll
             for (int p = 0; p < J; p += 2) {
@@ -1636,7 +1584,21 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
             if (p + 2 < J) b[p + 2] = v.z;
             if (p + 3 < J) b[p + 3] = v.w;
         }
-        {
+    } else {
+#pragma unroll
+        for (int p = 0; p < J; ++p) u[p] = b[p] = 0.f;
+    }
+    if (stage && do_step)  // lower triangles, row p at p (p + 1) / 2
+        for (int e = threadIdx.x; e < I3 * NLP; e += blockDim.x) {
+            const int k = e / NLP, t = e % NLP;
+            int p = 0;
+            while ((p + 1) * (p + 2) / 2 <= t) ++p;
+            const int q = t - p * (p + 1) / 2;
+            sCk[e] = t < NL ? Ckg[(int64_t)k * J * J + p * J + q] : 0.f;
+        }
+    __syncthreads();
+    if (valid) {
+        if (do_step && n > 0.f) {
             float L[NL];
             const float nreg = n * lam / (float)max(nrow, 1);  // the wave's L2 weight
             const float diag = kBlocks * nreg + inv_lr;
@@ -1721,9 +1683,11 @@ __device__ void wave_rows_thread(int blk, int do_step, float *__restrict__ U, fl
                 }
             }
         }
+    }
+    {  // the row's share of the moments: weight cnt / n, folded into the row as its square root
         const float sw = sqrtf((float)nrow * inv_n);
 #pragma unroll
-        for (int p = 0; p < J; ++p) rows[lr * JE + p] = sw * u[p];
+        for (int p = 0; p < JE; ++p) rows[threadIdx.x * JE + p] = p < J ? sw * u[p] : 0.f;
     }
     __syncthreads();
     {  // every thread has read its accumulators: clear the CTA's rows of them, coalesced
