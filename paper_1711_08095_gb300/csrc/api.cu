@@ -36,6 +36,24 @@ void dfree(Ctx *c, T *&p) {
     p = nullptr;
 }
 
+// The address through which a kernel on the context's device reads p: device memory of that
+// device, managed memory, or page-locked host memory mapped into the device's address space
+// (read over the host link); NULL for pageable host memory, which is copied instead.
+template <typename T>
+const T *kernel_readable(const Ctx *c, const T *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const bool ok = (a.type == cudaMemoryTypeDevice && a.device == c->device) || a.type == cudaMemoryTypeManaged ||
+                    a.type == cudaMemoryTypeHost;
+    return ok ? static_cast<const T *>(a.devicePointer) : nullptr;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 // copies count elements from any memory into a fresh device buffer (stream-ordered)
 template <typename T>
 int stage(Ctx *c, T **dst, const T *src, int64_t count) {
@@ -324,17 +342,27 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
         (rc = dmalloc(c, &c->taken, d.I1)) || (rc = dmalloc(c, &c->top_i, 64)) ||
         (rc = dmalloc(c, &c->top_s, 64)))
         return bail(rc);
-    // inputs (any memory) -> device
+    // inputs (any memory) -> device.  The fast mode orders its entries by counting when its
+    // bucket table is small enough, in one pass that reads them where they are if a kernel can
+    // (device memory, or pinned host memory over the host link); otherwise they are copied
+    // to the device first.
+    const bool counting = cfg->batch == 0 && fast_counting_fits(c);
+    const int32_t *src_idx = counting ? kernel_readable(c, idx) : nullptr;
+    const float *src_val = counting ? kernel_readable(c, val) : nullptr;
     int32_t *d_idx = nullptr, *d_edges = nullptr;
     float *d_val = nullptr, *d_w = nullptr;
-    if ((rc = stage(c, &d_idx, idx, nnz * 3)) || (rc = stage(c, &d_val, val, nnz)) ||
+    if ((!src_idx && (rc = stage(c, &d_idx, idx, nnz * 3))) || (!src_val && (rc = stage(c, &d_val, val, nnz))) ||
         (rc = stage(c, &d_edges, edges, m * 2)) || (rc = stage(c, &d_w, w, m)))
         return bail(rc);
+    if (!src_idx) src_idx = d_idx;
+    if (!src_val) src_val = d_val;
     if (!rc) rc = copy_in(c, c->G, G0, c->PI);
     if (!rc) rc = copy_in(c, c->U[0], U1, (int64_t)d.I1 * d.J1);
     if (!rc) rc = copy_in(c, c->U[1], U2, (int64_t)d.I2 * d.J2);
     if (!rc) rc = copy_in(c, c->U[2], U3, (int64_t)d.I3 * d.J3);
-    if (!rc) rc = prep_problem(c, d_idx, d_val);
+    if (!rc)
+        rc = counting ? prep_fast_entries(c, src_idx, src_val, aligned16(src_idx) && aligned16(src_val))
+                      : prep_problem(c, src_idx, src_val);
     if (!rc) rc = prep_graph(c, d_edges, d_w);
     if (d_idx) cudaFreeAsync(d_idx, c->stream);
     if (d_val) cudaFreeAsync(d_val, c->stream);
@@ -357,7 +385,7 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
             return bail(SNECT_ECUDA);
         }
     } else {
-        if ((rc = prep_fast_tiles(c)) || (rc = init_fast(c))) return bail(rc);
+        if ((!counting && (rc = prep_fast_tiles(c))) || (rc = init_fast(c))) return bail(rc);
     }
     cudaError_t e = loss_init_attrs(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -184,6 +184,10 @@ int prep_problem(Ctx *c, const int32_t *d_idx, const float *d_val);
 int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w);
 int prep_det_groups(Ctx *c);
 int prep_fast_tiles(Ctx *c);       // prep.cu: groups each wave's entries by platform, tiles
+// fast mode: true when the set-up can order the entries by counting (sets the wave size);
+// prep_fast_entries then packs, validates, counts and orders them in one read of the inputs
+bool fast_counting_fits(Ctx *c);
+int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec);
 int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of the fast sweep
 int enqueue_fast_epoch(Ctx *c);
 cudaError_t refresh_bf16_rows(Ctx *c);  // U2 -> its BF16 copy, when the context keeps one

@@ -228,6 +228,168 @@ __global__ void k_wave_hist(const Rec *__restrict__ rec, int64_t n, int64_t wave
     }
 }
 
+// ---- fast mode: one pass over the inputs orders the entries by counting ----------------
+// Every entry falls in a bucket (wave, platform, patient), wave = position / W; buckets in
+// that order are the order the fast sweep wants.  The packing pass counts each bucket with an
+// atomic that also hands the entry its rank inside the bucket; an exclusive scan of the counts
+// gives each bucket's first position, and a scatter puts every entry at first + rank.  Inside
+// a bucket (one patient's entries of one platform in one wave) the order is that of the
+// atomics, which the sweep does not depend on: every gradient of a wave is taken at the
+// wave-start parameters.
+constexpr int kPackWarps = 32;   // warps per CTA of the packing pass
+constexpr int kPackChunk = 128;  // entries per warp step, four per lane
+
+struct PackFastArgs {
+    const int32_t *idx;  // nnz x 3, where a kernel can read it (device or pinned host memory)
+    const float *val;
+    int64_t n, W;
+    int32_t I1, I2, I3;
+    int32_t vec;         // idx and val 16-byte aligned: the warp reads its chunk with vector loads
+    Rec *out;            // entries in input order
+    int32_t *rank;       // rank of each entry inside its bucket
+    int32_t *bcnt;       // (wave, platform, patient) bucket counts, zeroed
+    float *wcnt;         // per-wave (row, platform) entry table or NULL; gene rows counted here
+    int32_t *c1, *c2, *c3, *flag;
+};
+
+// Packs, validates and counts the entries: rows of every mode (|Omega^{n,i}|, through shared
+// histograms when SMEM), buckets, and the wave table's gene rows.  A warp takes 128 entries
+// at a time; with aligned inputs its 1,536 index bytes arrive as three coalesced 512-byte
+// loads (the right shape for reads of host memory over the link) and are redistributed
+// through shared memory, four entries to a lane.
+template <bool SMEM>
+__global__ void __launch_bounds__(kPackWarps * 32) k_pack_fast(PackFastArgs A) {
+    extern __shared__ int32_t psm[];  // per warp 3 x 128 ints | histograms I1 | I2 | I3 (SMEM)
+    int32_t *tr = psm + (threadIdx.x >> 5) * 3 * kPackChunk;
+    int32_t *hs = psm + kPackWarps * 3 * kPackChunk;
+    const int32_t I1 = A.I1, I2 = A.I2, I3 = A.I3;
+    if (SMEM) {
+        for (int t = threadIdx.x; t < I1 + I2 + I3; t += blockDim.x) hs[t] = 0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t n_chunks = (A.n + kPackChunk - 1) / kPackChunk;
+    const int64_t n_warps = (int64_t)gridDim.x * kPackWarps;
+    for (int64_t ch = (int64_t)blockIdx.x * kPackWarps + (threadIdx.x >> 5); ch < n_chunks; ch += n_warps) {
+        const int64_t e0 = ch * kPackChunk + 4 * lane;  // this lane's first entry
+        int32_t ii[4], jj[4], kk[4];
+        float xx[4];
+        int m = 0;  // entries of this lane inside the input
+        if (A.vec && ch * kPackChunk + kPackChunk <= A.n) {  // uniform across the warp
+            const int4 *s4 = reinterpret_cast<const int4 *>(A.idx) + ch * (3 * kPackChunk / 4);
+            int4 *t4 = reinterpret_cast<int4 *>(tr);
+            t4[lane] = s4[lane];
+            t4[lane + 32] = s4[lane + 32];
+            t4[lane + 64] = s4[lane + 64];
+            const float4 v = reinterpret_cast<const float4 *>(A.val)[ch * (kPackChunk / 4) + lane];
+            __syncwarp();
+            // entries 4 lane .. 4 lane + 3 are ints 12 lane .. 12 lane + 11
+            const int4 a = t4[3 * lane], b = t4[3 * lane + 1], c = t4[3 * lane + 2];
+            __syncwarp();  // read before the next chunk overwrites them
+            ii[0] = a.x, jj[0] = a.y, kk[0] = a.z;
+            ii[1] = a.w, jj[1] = b.x, kk[1] = b.y;
+            ii[2] = b.z, jj[2] = b.w, kk[2] = c.x;
+            ii[3] = c.y, jj[3] = c.z, kk[3] = c.w;
+            xx[0] = v.x, xx[1] = v.y, xx[2] = v.z, xx[3] = v.w;
+            m = 4;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ii[q] = jj[q] = kk[q] = 0;
+                xx[q] = 0.f;
+                if (e0 + q < A.n) {
+                    ii[q] = A.idx[3 * (e0 + q)];
+                    jj[q] = A.idx[3 * (e0 + q) + 1];
+                    kk[q] = A.idx[3 * (e0 + q) + 2];
+                    xx[q] = A.val[e0 + q];
+                    m = q + 1;
+                }
+            }
+        }
+        int32_t rk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            rk[q] = 0;
+            if (q >= m) continue;
+            const int64_t e = e0 + q;
+            Rec r;
+            r.i = ii[q], r.j = jj[q], r.k = kk[q], r.x = xx[q];
+            if (r.i < 0 || r.i >= I1 || r.j < 0 || r.j >= I2 || r.k < 0 || r.k >= I3) {
+                atomicOr(A.flag, kBadIndex);
+                r.i = r.j = r.k = 0;  // keep later kernels in bounds; the call reports the error
+            }
+            if (!isfinite(r.x)) atomicOr(A.flag, kBadValue);
+            A.out[e] = r;
+            const int64_t w = e / A.W;
+            rk[q] = atomicAdd(A.bcnt + (w * I3 + r.k) * I1 + r.i, 1);
+            if (A.wcnt) atomicAdd(A.wcnt + (w * ((int64_t)I1 + I2) + I1 + r.j) * I3 + r.k, 1.f);
+            if (SMEM) {
+                atomicAdd(hs + r.i, 1);
+                atomicAdd(hs + I1 + r.j, 1);
+                atomicAdd(hs + I1 + I2 + r.k, 1);
+            } else {
+                atomicAdd(A.c1 + r.i, 1);
+                atomicAdd(A.c2 + r.j, 1);
+                atomicAdd(A.c3 + r.k, 1);
+            }
+        }
+        if (m == 4)  // e0 is a multiple of 4: one aligned 16-byte store
+            *reinterpret_cast<int4 *>(A.rank + e0) = make_int4(rk[0], rk[1], rk[2], rk[3]);
+        else
+            for (int q = 0; q < m; ++q) A.rank[e0 + q] = rk[q];
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < I1 + I2 + I3; t += blockDim.x) {
+            const int v = hs[t];
+            if (v == 0) continue;
+            if (t < I1) atomicAdd(A.c1 + t, v);
+            else if (t < I1 + I2) atomicAdd(A.c2 + (t - I1), v);
+            else atomicAdd(A.c3 + (t - I1 - I2), v);
+        }
+    }
+}
+
+// every entry to its bucket's first position + its rank
+__global__ void k_bucket_scatter(const Rec *__restrict__ src, const int32_t *__restrict__ rank,
+                                 const int32_t *__restrict__ first, int64_t n, int64_t W, int32_t I1, int32_t I3,
+                                 Rec *__restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const Rec r = src[e];
+    dst[first[(e / W * I3 + r.k) * I1 + r.i] + rank[e]] = r;
+}
+
+// the wave table's patient rows: bucket (w, k, i)'s count is row i's entries of platform k
+// in wave w
+__global__ void k_bucket_wave_rows(const int32_t *__restrict__ bcnt, int64_t nb, int32_t I1, int32_t I2,
+                                   int32_t I3, float *__restrict__ wcnt) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int64_t i = b % I1, wk = b / I1, k = wk % I3, w = wk / I3;
+    wcnt[(w * ((int64_t)I1 + I2) + i) * I3 + k] = (float)bcnt[b];
+}
+
+// tile t of the wave kernels: found by binary search over the segments' first tiles; seg
+// holds S segment starts, S counts and S + 1 first tiles (segment s = wave s / I3, platform
+// s % I3)
+__global__ void k_build_tiles(const int32_t *__restrict__ seg, int32_t S, int32_t I3, int64_t n_tiles,
+                              int32_t *__restrict__ ts, int32_t *__restrict__ tl, int32_t *__restrict__ tk) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const int32_t *pos = seg, *cnt = seg + S, *t0 = seg + 2 * S;
+    int lo = 0, hi = S;  // t0[lo] <= t < t0[hi]; the answer is the last segment with t0 <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (t0[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const int32_t lt = (int32_t)(t - t0[lo]);
+    ts[t] = pos[lo] + lt * kFastTile;
+    tl[t] = min(kFastTile, cnt[lo] - lt * kFastTile);
+    tk[t] = lo % I3;
+}
+
 std::string flag_message(int32_t f) {
     std::string s;
     if (f & kBadIndex) s += " index out of range;";
@@ -399,14 +561,17 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     return SNECT_OK;
 }
 
-// Fast mode: the visit order is cut into waves of c->wave entries; inside a wave the entries
-// are stably grouped by platform (so one tile of kFastTile entries holds one platform) and
-// each platform segment is cut into tiles.
-int prep_fast_tiles(Ctx *c) {
+namespace {
+
+// Fast mode: the visit order is cut into waves of c->wave entries, an even number of them
+// (>= 2, so the moment buffers alternate across epochs); inside a wave the entries are grouped
+// by platform (one tile of kFastTile entries holds one platform) and, inside a platform, by
+// patient (the sweep sums a patient's neighbouring entries before adding them to its row).
+// Gradients inside a wave all use the wave-start values, so the order inside a wave is free.
+void fast_waves(Ctx *c) {
     const int64_t n = c->nnz;
-    const int32_t I3 = c->d.I3;
     int64_t W = c->cfg.wave > 0 ? c->cfg.wave : std::min<int64_t>(kMaxWave, std::max<int64_t>(kMinWave, (n + 15) / 16));
-    if (n) {  // an even number of waves (>= 2), so the moment buffers alternate across epochs
+    if (n) {
         int64_t nw = (n + W - 1) / W;
         nw = std::max<int64_t>(2, (nw + 1) & ~(int64_t)1);
         W = (n + nw - 1) / nw;
@@ -417,6 +582,81 @@ int prep_fast_tiles(Ctx *c) {
     c->wave = W;
     c->wave_tile.assign(1, 0);
     c->wave_len.clear();
+}
+
+// the per-wave (row, platform) entry table is kept when it is no larger than the entries
+// themselves (else the sweep counts a wave's rows with atomics)
+int64_t wave_table_cells(const Ctx *c) {
+    const int64_t cells = c->n_waves * ((int64_t)c->d.I1 + c->d.I2) * c->d.I3;
+    return (size_t)cells * sizeof(float) <= std::max<size_t>((size_t)64 << 20, sizeof(Rec) * (size_t)c->nnz) ? cells
+                                                                                                               : 0;
+}
+
+int64_t fast_buckets(const Ctx *c) { return c->n_waves * (int64_t)c->d.I3 * c->d.I1; }
+
+// The tile lists of the wave kernels from the entries per (wave, platform), h[w I3 + k]: wave
+// w's platform-k segment starts where the previous one ends and is cut into tiles of
+// kFastTile entries.  The host walks the segments; one kernel writes the tiles.
+int build_fast_tiles(Ctx *c, const std::vector<int32_t> &h) {
+    const int64_t n = c->nnz, W = c->wave;
+    const int32_t I3 = c->d.I3;
+    const int64_t S = c->n_waves * I3;
+    std::vector<int32_t> seg((size_t)(3 * S + 1));  // starts | counts | first tiles (S + 1)
+    std::vector<float> nk((size_t)S);
+    int64_t tiles = 0;
+    for (int64_t w = 0; w < c->n_waves; ++w) {
+        int64_t pos = std::min<int64_t>(w * W, n);
+        c->wave_len.push_back(std::min<int64_t>(W, n - pos));
+        for (int32_t k = 0; k < I3; ++k) {
+            const int64_t s = w * I3 + k, cnt = h[(size_t)s];
+            seg[(size_t)s] = (int32_t)pos;
+            seg[(size_t)(S + s)] = (int32_t)cnt;
+            seg[(size_t)(2 * S + s)] = (int32_t)tiles;
+            nk[(size_t)s] = (float)cnt;
+            tiles += (cnt + kFastTile - 1) / kFastTile;
+            pos += cnt;
+        }
+        c->wave_tile.push_back(tiles);
+    }
+    seg[(size_t)(3 * S)] = (int32_t)tiles;
+    c->n_tiles = tiles;
+    int32_t *d_seg = nullptr;
+    const size_t tb = sizeof(int32_t) * (size_t)std::max<int64_t>(tiles, 1);
+    SNECT_CUDA(c, scratch_alloc(c, &c->tile_start, tb));
+    SNECT_CUDA(c, scratch_alloc(c, &c->tile_len, tb));
+    SNECT_CUDA(c, scratch_alloc(c, &c->tile_k, tb));
+    SNECT_CUDA(c, scratch_alloc(c, &c->wave_nk, sizeof(float) * nk.size()));
+    SNECT_CUDA(c, scratch_alloc(c, &d_seg, sizeof(int32_t) * seg.size()));
+    SNECT_CUDA(c, cudaMemcpyAsync(d_seg, seg.data(), sizeof(int32_t) * seg.size(), cudaMemcpyHostToDevice, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(c->wave_nk, nk.data(), sizeof(float) * nk.size(), cudaMemcpyHostToDevice, c->stream));
+    if (tiles) {
+        k_build_tiles<<<ceil_div(tiles, 256), 256, 0, c->stream>>>(d_seg, (int32_t)S, I3, tiles, c->tile_start,
+                                                                    c->tile_len, c->tile_k);
+        c->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(d_seg, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
+    if (e != cudaSuccess) return fail(c, SNECT_ECUDA, std::string("tile lists: ") + cudaGetErrorString(e));
+    return SNECT_OK;
+}
+
+}  // namespace
+
+bool fast_counting_fits(Ctx *c) {
+    fast_waves(c);
+    const int64_t nb = fast_buckets(c);
+    return c->nnz > 0 && nb <= INT32_MAX && nb <= std::max<int64_t>((int64_t)1 << 24, 2 * c->nnz);
+}
+
+// The radix-sort form of the fast mode's ordering, for problems whose bucket table would be
+// too large for the counting form: the entries (packed in input order by prep_problem) are
+// sorted stably by (wave, platform, patient), which keeps the visit order among one
+// patient's entries.
+int prep_fast_tiles(Ctx *c) {
+    fast_waves(c);
+    const int64_t n = c->nnz, W = c->wave;
+    const int32_t I3 = c->d.I3;
     if (n == 0) return SNECT_OK;
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int32_t *vals = nullptr, *vals2 = nullptr, *hist = nullptr;
@@ -427,10 +667,6 @@ int prep_fast_tiles(Ctx *c) {
     SNECT_CUDA(c, scratch_alloc(c, &vals2, sizeof(int32_t) * n));
     SNECT_CUDA(c, scratch_alloc(c, &tmp, sizeof(Rec) * n));
     SNECT_CUDA(c, scratch_alloc(c, &hist, sizeof(int32_t) * c->n_waves * I3));
-    // inside a wave and platform the entries are put in patient order (the sweep sums a
-    // patient's neighbouring entries before adding them to its row; gradients inside a wave
-    // all use the wave-start values, so the order inside a wave is free); the stable sort
-    // keeps the visit order among one patient's entries
     const int bw = bits_for((uint64_t)(c->n_waves - 1)), bk = bits_for((uint64_t)(I3 - 1));
     int bi = bits_for((uint64_t)(c->d.I1 - 1));
     if (bw + bk + bi > 64) bi = 0;
@@ -451,10 +687,7 @@ int prep_fast_tiles(Ctx *c) {
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * c->n_waves * I3, c->stream);
         k_wave_hist<<<ceil_div(n, 1024), 1024, 0, c->stream>>>(c->rec, n, W, I3, hist);
         c->launches += 2;
-        // the row steps' per-platform entry counts, fixed for every wave, when the table is no
-        // larger than the entries themselves (else the sweep counts them with atomics)
-        const int64_t cells = c->n_waves * ((int64_t)c->d.I1 + c->d.I2) * I3;
-        if ((size_t)cells * sizeof(float) <= std::max<size_t>((size_t)64 << 20, sizeof(Rec) * (size_t)n)) {
+        if (const int64_t cells = wave_table_cells(c)) {
             if (scratch_alloc(c, &c->wcnt, sizeof(float) * cells) == cudaSuccess) {
                 cudaMemsetAsync(c->wcnt, 0, sizeof(float) * cells, c->stream);
                 k_wave_row_counts<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->rec, n, W, c->d.I1, c->d.I2, I3,
@@ -480,40 +713,84 @@ int prep_fast_tiles(Ctx *c) {
     cudaFreeAsync(tmp, c->stream);
     cudaFreeAsync(hist, c->stream);
     if (rc) return rc;
-    std::vector<int32_t> ts, tl, tk;
-    const size_t tiles_max = (size_t)(n / kFastTile) + (size_t)c->n_waves * I3 + 1;
-    ts.reserve(tiles_max);
-    tl.reserve(tiles_max);
-    tk.reserve(tiles_max);
-    std::vector<float> nk((size_t)c->n_waves * I3);
-    for (int64_t w = 0; w < c->n_waves; ++w) {
-        int64_t pos = std::min<int64_t>(w * W, n);
-        const int64_t len = std::min<int64_t>(W, n - pos);
-        for (int32_t k = 0; k < I3; ++k) {
-            const int64_t cnt = h[(size_t)w * I3 + k];
-            nk[(size_t)w * I3 + k] = (float)cnt;
-            for (int64_t t = 0; t < cnt; t += kFastTile) {
-                ts.push_back((int32_t)(pos + t));
-                tl.push_back((int32_t)std::min<int64_t>(kFastTile, cnt - t));
-                tk.push_back(k);
-            }
-            pos += cnt;
+    return build_fast_tiles(c, h);
+}
+
+// The counting form (fast_counting_fits): packing, validation, the counts |Omega^{n,i}|, the
+// wave table and the ordering in one read of the inputs, which stay where the caller has
+// them when a kernel can read them there.
+int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec) {
+    fast_waves(c);
+    const int64_t n = c->nnz, W = c->wave, nb = fast_buckets(c), S = c->n_waves * c->d.I3;
+    const Dims &d = c->d;
+    for (int md = 0; md < 3; ++md)
+        SNECT_CUDA(c, cudaMemsetAsync(c->cnt[md], 0, sizeof(int32_t) * (md == 0 ? d.I1 : (md == 1 ? d.I2 : d.I3)),
+                                      c->stream));
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    if (n == 0) return SNECT_OK;
+    Rec *tmp = nullptr;
+    int32_t *rank = nullptr, *bcnt = nullptr, *first = nullptr;
+    SNECT_CUDA(c, scratch_alloc(c, &tmp, sizeof(Rec) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &rank, sizeof(int32_t) * n));
+    SNECT_CUDA(c, scratch_alloc(c, &bcnt, sizeof(int32_t) * nb));
+    SNECT_CUDA(c, scratch_alloc(c, &first, sizeof(int32_t) * nb));
+    SNECT_CUDA(c, cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * nb, c->stream));
+    if (const int64_t cells = wave_table_cells(c)) {
+        if (scratch_alloc(c, &c->wcnt, sizeof(float) * cells) == cudaSuccess) {
+            SNECT_CUDA(c, cudaMemsetAsync(c->wcnt, 0, sizeof(float) * cells, c->stream));
+        } else {
+            cudaGetLastError();
+            c->wcnt = nullptr;
         }
-        c->wave_tile.push_back((int64_t)ts.size());
-        c->wave_len.push_back(len);
     }
-    c->n_tiles = (int64_t)ts.size();
-    auto upload = [&](int32_t **dst, const std::vector<int32_t> &v) -> int {
-        SNECT_CUDA(c, scratch_alloc(c, dst, sizeof(int32_t) * v.size()));
-        SNECT_CUDA(c, cudaMemcpyAsync(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, c->stream));
-        return SNECT_OK;
-    };
-    if ((rc = upload(&c->tile_start, ts)) || (rc = upload(&c->tile_len, tl)) || (rc = upload(&c->tile_k, tk)))
-        return rc;
-    SNECT_CUDA(c, scratch_alloc(c, &c->wave_nk, sizeof(float) * nk.size()));
-    SNECT_CUDA(c, cudaMemcpyAsync(c->wave_nk, nk.data(), sizeof(float) * nk.size(), cudaMemcpyHostToDevice, c->stream));
-    SNECT_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
-    return SNECT_OK;
+    PackFastArgs A{idx, val, n, W, d.I1, d.I2, d.I3, vec ? 1 : 0, tmp, rank, bcnt, c->wcnt,
+                   c->cnt[0], c->cnt[1], c->cnt[2], c->flag};
+    const int64_t bins = (int64_t)d.I1 + d.I2 + d.I3;
+    const bool smem_hist = bins <= kCountBins;
+    const size_t smem = sizeof(int32_t) * (size_t)(kPackWarps * 3 * kPackChunk + (smem_hist ? bins : 0));
+    int sms = 0;
+    SNECT_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int64_t chunks = (n + kPackChunk - 1) / kPackChunk;
+    const int grid = (int)std::min<int64_t>(ceil_div(chunks, kPackWarps), (int64_t)sms * (smem_hist ? 1 : 2));
+    if (smem_hist) {
+        SNECT_CUDA(c, cudaFuncSetAttribute(k_pack_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_pack_fast<true><<<grid, kPackWarps * 32, smem, c->stream>>>(A);
+    } else {
+        SNECT_CUDA(c, cudaFuncSetAttribute(k_pack_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_pack_fast<false><<<grid, kPackWarps * 32, smem, c->stream>>>(A);
+    }
+    c->launches++;
+    SNECT_CUDA(c, cudaGetLastError());
+    size_t tmp_bytes = 0;
+    SNECT_CUDA(c, cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, bcnt, first, (int)nb, c->stream));
+    void *scan_tmp = nullptr;
+    SNECT_CUDA(c, scratch_alloc(c, &scan_tmp, tmp_bytes));
+    SNECT_CUDA(c, cub::DeviceScan::ExclusiveSum(scan_tmp, tmp_bytes, bcnt, first, (int)nb, c->stream));
+    c->launches++;
+    cudaFreeAsync(scan_tmp, c->stream);
+    // the validation flag, and each (wave, platform) segment's start: bucket (w, k, 0)'s
+    std::vector<int32_t> seg((size_t)S);
+    int32_t bad = 0;
+    SNECT_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaMemcpy2DAsync(seg.data(), sizeof(int32_t), first, sizeof(int32_t) * (size_t)d.I1,
+                                    sizeof(int32_t), (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+    k_bucket_scatter<<<ceil_div(n, 256), 256, 0, c->stream>>>(tmp, rank, first, n, W, d.I1, d.I3, c->rec);
+    c->launches++;
+    if (c->wcnt) {
+        k_bucket_wave_rows<<<ceil_div(nb, 256), 256, 0, c->stream>>>(bcnt, nb, d.I1, d.I2, d.I3, c->wcnt);
+        c->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(tmp, c->stream);
+    cudaFreeAsync(rank, c->stream);
+    cudaFreeAsync(bcnt, c->stream);
+    cudaFreeAsync(first, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SNECT_ECUDA, std::string("entry ordering: ") + cudaGetErrorString(e));
+    if (bad) return fail(c, SNECT_EINVAL, "entries:" + flag_message(bad));
+    std::vector<int32_t> h((size_t)S);
+    for (int64_t s = 0; s < S; ++s) h[(size_t)s] = (s + 1 < S ? seg[(size_t)s + 1] : (int32_t)n) - seg[(size_t)s];
+    return build_fast_tiles(c, h);
 }
 
 }  // namespace snect

@@ -52,10 +52,11 @@ def normwise(got, want):
     return float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30))
 
 
-def check_waves(p, tol, precision=0, wave=0, epochs_between=2):
+def check_waves(p, tol, precision=0, wave=0, epochs_between=2, entries=None):
     import paper_1711_08095_gb300 as snect
 
-    c = snect.Snect(p.I, p.J, p.idx, p.val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+    idx, val = entries if entries is not None else (p.idx, p.val)
+    c = snect.Snect(p.I, p.J, idx, val, p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
                     batch=0, wave=wave, precision=precision)
     report = []
     for stage in range(2):
@@ -136,3 +137,59 @@ def test_bf16_sweeps(form, gpu_lib):
 
     p = S.config2(n_patients=150, nnz=200_000, n_edges=10_000, J_fit=(16, 16, 5))
     check_waves(p, TOL_BF16, precision=snect.BF16 if form == "bf16_gather" else snect.BF16_TC)
+
+
+def _inputs(p, memory):
+    """The training entries in the given kind of memory; "+1" views start 4 bytes past a
+    16-byte boundary."""
+    import torch
+
+    if memory == "pageable":
+        return p.idx, p.val
+    off = 1 if memory.endswith("+1") else 0
+    kw = dict(device="cuda") if memory.startswith("device") else dict(pin_memory=True)
+    out = []
+    for a in (p.idx, p.val):
+        flat = torch.from_numpy(np.ascontiguousarray(a).reshape(-1))
+        buf = torch.empty(flat.numel() + off, dtype=flat.dtype, **kw)
+        buf[off:].copy_(flat)
+        out.append(buf[off:].view(a.shape))
+    return tuple(out)
+
+
+@pytest.mark.parametrize("memory", ["pageable", "pinned", "device", "pinned+1", "device+1"])
+def test_set_up_reads_the_entries_where_they_are(memory, gpu_lib):
+    """The counting form of the set-up packs, validates, counts and orders the entries in one
+    pass that reads them where the caller has them; aligned inputs arrive as 16-byte vector
+    loads, the "+1" views through the scalar loads.  200,003 entries: the last 128-entry chunk
+    is ragged, and the waves (1,999 entries) do not divide the chunks."""
+    p = S.config2(n_patients=150, nnz=222_226, n_edges=10_000)
+    assert p.nnz % 128 != 0
+    check_waves(p, TOL32, wave=1999, entries=_inputs(p, memory))
+
+
+def test_set_up_radix_form_for_large_bucket_tables(gpu_lib):
+    """20,000 patients x 5 platforms x 196 waves of 1,024 entries are 19.6M (wave, platform,
+    patient) buckets, above the counting form's limit: the set-up sorts the entries by radix
+    instead (and the wave table exceeds its budget, so the sweep counts with atomics)."""
+    p = S.config2(n_patients=20_000, n_genes=1_000, nnz=222_000, n_edges=3_000, J_true=(5, 5, 2),
+                  J_fit=(5, 5, 2))
+    check_waves(p, TOL32, wave=1024)
+
+
+@pytest.mark.parametrize("memory", ["pageable", "pinned", "device"])
+@pytest.mark.parametrize("case", ["index", "nan"])
+def test_set_up_rejects_invalid_entries(memory, case, gpu_lib):
+    import paper_1711_08095_gb300 as snect
+
+    p = S.config2(n_patients=60, n_genes=2000, nnz=40_000, n_edges=3_000)
+    idx, val = p.idx.copy(), p.val.copy()
+    if case == "index":
+        idx[12_345, 2] = p.I[2]
+    else:
+        val[33_333] = np.inf
+    q = S.Problem(**{**p.__dict__, "idx": idx, "val": val})
+    with pytest.raises(snect.SnectError) as ei:
+        snect.Snect(p.I, p.J, *_inputs(q, memory), p.edges, p.w, p.G0, p.U0, lam=p.lam, lam_g=p.lam_g, lr=p.lr,
+                    batch=0)
+    assert ei.value.code == -1
