@@ -52,6 +52,17 @@ const T *kernel_readable(const Ctx *c, const T *p) {
     return ok ? static_cast<const T *>(a.devicePointer) : nullptr;
 }
 
+// p is memory of the context's device (or managed memory): a kernel reads it in place
+bool on_device(const Ctx *c, const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == c->device) || a.type == cudaMemoryTypeManaged;
+}
+
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // copies count elements from any memory into a fresh device buffer (stream-ordered)
@@ -445,34 +456,49 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     if (!c || !out) return SNECT_EINVAL;
     if (n_test < 0) return fail(c, SNECT_EINVAL, "n_test must be >= 0");
     SNECT_CUDA(c, cudaMemsetAsync(c->lacc, 0, sizeof(double) * 8, c->stream));
-    SNECT_CUDA(c, launch_loss(c, c->rec, c->nnz, 0));
-    Rec *trec = nullptr;
+    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    float *W = nullptr;
+    SNECT_CUDA(c, loss_rows(c, &W));
+    {
+        cudaError_t e = launch_loss(c, c->rec, c->nnz, 0, W);
+        if (e != cudaSuccess) {
+            dfree(c, W);
+            return fail(c, SNECT_ECUDA, cudaGetErrorString(e));
+        }
+    }
     int32_t *d_idx = nullptr;
     float *d_val = nullptr;
     int rc = SNECT_OK;
     if (n_test > 0) {
-        if ((rc = stage(c, &d_idx, test_idx, n_test * 3)) || (rc = stage(c, &d_val, test_val, n_test)))
+        // test entries in device memory are read in place, others copied first; the loss
+        // kernel checks them as it reads them
+        const int32_t *ti = on_device(c, test_idx) ? test_idx : nullptr;
+        const float *tv = on_device(c, test_val) ? test_val : nullptr;
+        if ((!ti && (rc = stage(c, &d_idx, test_idx, n_test * 3))) || (!tv && (rc = stage(c, &d_val, test_val, n_test)))) {
+            dfree(c, d_idx);
+            dfree(c, d_val);
+            dfree(c, W);
             return rc;
-        SNECT_CUDA(c, scratch_alloc(c, (void **)&trec, sizeof(Rec) * n_test));
-        rc = pack_records(c, d_idx, d_val, n_test, trec, true, 3);
-        if (rc == SNECT_OK) {
-            cudaError_t e = launch_loss(c, trec, n_test, 1);
-            if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
         }
+        cudaError_t e = launch_loss_checked(c, ti ? ti : d_idx, tv ? tv : d_val, n_test, 1, c->flag, W);
+        if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
     }
     if (rc == SNECT_OK) {
         cudaError_t e = launch_loss_reg_graph(c);
         if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
     }
     double acc[8] = {0};
+    int32_t bad = 0;
     if (rc == SNECT_OK) {
         cudaError_t e = cudaMemcpyAsync(acc, c->lacc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));
     }
-    if (d_idx) cudaFreeAsync(d_idx, c->stream);
-    if (d_val) cudaFreeAsync(d_val, c->stream);
-    if (trec) cudaFreeAsync(trec, c->stream);
+    dfree(c, d_idx);
+    dfree(c, d_val);
+    dfree(c, W);
+    if (rc == SNECT_OK && bad) rc = fail(c, SNECT_EINVAL, "test " + entries_error(bad));
     if (rc) return rc;
     if (c->sweep_kind < 0) {  // a tensor-core wait that gave up
         int32_t tc_err = 0;

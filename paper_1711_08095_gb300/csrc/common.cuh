@@ -176,7 +176,17 @@ struct EdgeArgs {
 EdgeArgs make_edge_args(const Ctx *c);
 cudaError_t launch_batch_edge_pass(const EdgeArgs *d_args, int32_t P, int64_t max_cells, int64_t max_heavy,
                                    cudaStream_t st, int64_t *launches);
-cudaError_t launch_loss(Ctx *c, const Rec *recs, int64_t n, int which);
+// the loss kernels' per-(patient, platform) rows W[i][k] = (G x3 c_k)^T a_i, when there are
+// no more of them than training entries (*W from the pool, freed by the caller; NULL
+// otherwise, and the kernels form the products themselves)
+cudaError_t loss_rows(Ctx *c, float **W);
+cudaError_t launch_loss(Ctx *c, const Rec *recs, int64_t n, int which, const float *W);
+// the same over the caller's entries (idx n x 3, val n, device memory), checked on the way:
+// bit 1 of *flag for an index outside the tensor (the entry is left out), bit 2 for a
+// non-finite value
+cudaError_t launch_loss_checked(Ctx *c, const int32_t *idx, const float *val, int64_t n, int which,
+                                int32_t *flag, const float *W);
+std::string entries_error(int32_t flag);  // the message for such flag bits
 cudaError_t launch_loss_reg_graph(Ctx *c);
 
 // prep (prep.cu)

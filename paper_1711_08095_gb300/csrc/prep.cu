@@ -430,6 +430,8 @@ int bits_for(uint64_t v) {
 
 }  // namespace
 
+std::string entries_error(int32_t flag) { return "entries:" + flag_message(flag); }
+
 int pack_records(Ctx *c, const int32_t *d_idx, const float *d_val, int64_t n, Rec *out,
                  bool check_ranges, int32_t n_modes) {
     if (n == 0) return SNECT_OK;
