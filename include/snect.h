@@ -86,10 +86,15 @@ typedef struct {
  *   G0, U1, U2, U3  any, initial core and factors (layouts above)
  *   stream  a cudaStream_t, or NULL for the default stream
  * Validates ranges (indices, sizes, finite values, self loops); computes the counts
- * |Omega^{n,i}| and the per-batch row grouping on the GPU.  On failure *out is NULL.
- * Temporary set-up memory (staging, sort buffers) comes from a memory pool the library owns
- * on each device; memory freed back to that pool stays reserved (its high-water mark, about
- * 40 bytes per training entry) until the process exits, so later set-ups reuse it. */
+ * |Omega^{n,i}| and the per-batch row grouping on the GPU.  In fast mode one kernel packs,
+ * validates, counts and orders the entries into waves; it reads idx and val in place when
+ * they are device memory or pinned (page-locked) host memory, and pageable memory is copied
+ * first.  Inside a wave the entries are grouped by platform and patient; the order among one
+ * patient's entries of one platform is not fixed (every gradient of a wave is taken at the
+ * wave-start parameters).  On failure *out is NULL.
+ * Temporary set-up memory (staging, ordering buffers) comes from a memory pool the library
+ * owns on each device; memory freed back to that pool stays reserved (its high-water mark,
+ * about 40 bytes per training entry) until the process exits, so later set-ups reuse it. */
 int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, const float *val,
                int64_t nnz, const int32_t *edges, const float *w, int64_t m, const float *G0,
                const float *U1, const float *U2, const float *U3, void *stream);
@@ -109,7 +114,10 @@ int snect_batches(snect_ctx *ctx, int64_t first, int64_t count);
 int snect_edge_pass(snect_ctx *ctx);
 
 /* Objective terms and RMSE (Eq. 3, Sec. 2.3.2, graph regulariser; f_opt = f + lambda_g f_g).
- * test_idx/test_val: any, n_test held-out entries (may be 0).  Synchronises. */
+ * test_idx/test_val: any, n_test held-out entries (may be 0); read in place from device
+ * memory, copied otherwise.  Predictions are FP32, squared residuals summed in compensated
+ * FP32 per thread and in FP64 beyond.  Synchronises.  Errors: SNECT_EINVAL for a test entry
+ * with an index outside the tensor or a non-finite value (the context stays usable). */
 int snect_loss(snect_ctx *ctx, const int32_t *test_idx, const float *test_val, int64_t n_test,
                snect_loss_t *out);
 
