@@ -46,9 +46,9 @@ WORKLOAD = dict(
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per training entry of the FP32 sweep kernel (k_fast_sweep_lg, core
 # 10x10x5), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 12M-entry
-# case of the same structure (bench.py --small): 12.834 MB per 675,000-entry launch, scaled to a
+# case of the same structure (bench.py --small): 12.846 MB per 675,000-entry launch, scaled to a
 # launch by its entries.  To be re-measured, or set to None, whenever the sweep kernel changes.
-SWEEP_DRAM_BYTES_PER_ENTRY = 19.01
+SWEEP_DRAM_BYTES_PER_ENTRY = 19.03
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
@@ -783,7 +783,7 @@ def main():
                      "frac": (achieved / pk) if achieved else None,
                      "traffic": (SWEEP_DRAM_BYTES_PER_ENTRY * per_launch
                                  if (SWEEP_DRAM_BYTES_PER_ENTRY and not bf16 and tuple(p.J) == (10, 10, 5)) else None),
-                     "limiter": "ncu on the 12M-entry case: DRAM 5-6 % of peak, L2 23-29 %, L1 59 %, issue 61 %; "
+                     "limiter": "ncu on the 12M-entry case: DRAM 5-7 % of peak, L2 22-32 %, L1 69 %, issue 56 %; "
                                 "instruction issue and L1 bound the kernel, not HBM",
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 12M-entry case scaled by entries)",
                      "kernel": "%s (one launch per wave)" % {"fp32": "k_fast_sweep_lg", "bf16": "k_fast_sweep_lg (BF16 gathers)",
