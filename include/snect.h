@@ -219,8 +219,8 @@ void snect_batch_destroy(snect_batch *batch);
  * n <= 1,048,576 cells; larger queries return SNECT_EINVAL before any work is queued.  The
  * first call on each device does a one-time set-up with that device current (it looks up the
  * array's address and raises one kernel's shared-memory limit so that every core up to
- * J1*J2*J3 = 5,120 fits); make that first call before any stream capture begins.  Each call
- * ends by copying two status words to the host and synchronising the stream.  Calls share
+ * J1*J2*J3 = 5,120 fits).  Each call ends by copying two status words to the host and
+ * synchronising the stream, so no call can be captured into a CUDA graph.  Calls share
  * the array, so two calls whose work overlaps on the GPU (from different streams or threads)
  * race; serialise them.  Errors: SNECT_EINVAL for bad sizes, an out-of-range cell, a
  * non-finite value or a system that is not positive definite; on those two device-side

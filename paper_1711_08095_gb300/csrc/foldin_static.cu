@@ -12,8 +12,9 @@
 // host-side stand-in), so the first call on each device does a one-time set-up with that
 // device current: it looks the address up with cudaGetSymbolAddress and caches it, and it
 // raises the partial-sum kernel's dynamic shared-memory limit so that every core the entry
-// point accepts (J1*J2*J3 <= 5,120) fits beside the kernel's static tiles.  That first call
-// should come before any stream capture.  Every call shares the array and leaves its
+// point accepts (J1*J2*J3 <= 5,120) fits beside the kernel's static tiles.  Every call ends
+// by reading two status words back and synchronising, so none can be captured into a CUDA
+// graph.  Every call shares the array and leaves its
 // contents behind: the status words are cleared at the start of each call and every partial
 // is overwritten before it is read.  Two calls whose work overlaps on the GPU race on the
 // array.
