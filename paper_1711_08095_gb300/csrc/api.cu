@@ -65,14 +65,16 @@ bool on_device(const Ctx *c, const void *p) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// copies count elements from any memory into a fresh device buffer (stream-ordered)
+// copies count elements from any memory into a fresh device buffer, ordered on the context's
+// stream (or on its side stream)
 template <typename T>
-int stage(Ctx *c, T **dst, const T *src, int64_t count) {
+int stage(Ctx *c, T **dst, const T *src, int64_t count, bool side = false) {
     *dst = nullptr;
     if (count <= 0) return SNECT_OK;
     if (!src) return fail(c, SNECT_EINVAL, "null input pointer");
-    SNECT_CUDA(c, scratch_alloc(c, (void **)dst, sizeof(T) * (size_t)count));
-    SNECT_CUDA(c, cudaMemcpyAsync(*dst, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, c->stream));
+    cudaStream_t st = side ? c->side : c->stream;
+    SNECT_CUDA(c, cudaMallocFromPoolAsync((void **)dst, sizeof(T) * (size_t)count, scratch_pool(c->device), st));
+    SNECT_CUDA(c, cudaMemcpyAsync(*dst, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, st));
     return SNECT_OK;
 }
 
@@ -123,6 +125,12 @@ void free_all(Ctx *c) {
     dfree(c, c->top_s);
     dfree(c, c->lacc);
     dfree(c, c->flag);
+    if (c->side) cudaStreamDestroy(c->side);
+    c->side = nullptr;
+    for (auto &e : c->side_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
 }
 
 int check_config(const snect_config *cfg, std::string *why) {
@@ -339,6 +347,12 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
         return fail(nullptr, code, msg);
     };
     c->stream = (cudaStream_t)stream;  // NULL: the default stream
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->side_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        c->err = std::string("side stream: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(SNECT_ECUDA);
+    }
     const Dims &d = c->d;
     if ((rc = dmalloc(c, &c->rec, nnz)) || (rc = dmalloc(c, &c->cnt[0], d.I1)) ||
         (rc = dmalloc(c, &c->cnt[1], d.I2)) || (rc = dmalloc(c, &c->cnt[2], d.I3)) ||
@@ -348,7 +362,7 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
         (rc = dmalloc(c, &c->ew, m)) || (rc = dmalloc(c, &c->csr_ptr, (int64_t)d.I2 + 1)) ||
         (rc = dmalloc(c, &c->csr_col, 2 * m)) || (rc = dmalloc(c, &c->csr_w, 2 * m)) ||
         (rc = dmalloc(c, &c->snap, (int64_t)d.I2 * d.J2)) || (rc = dmalloc(c, &c->lacc, 8)) ||
-        (rc = dmalloc(c, &c->flag, 4)) || (rc = dmalloc(c, &c->q_u, kMaxRank)) ||
+        (rc = dmalloc(c, &c->flag, 8)) || (rc = dmalloc(c, &c->q_u, kMaxRank)) ||
         (rc = dmalloc(c, &c->q_status, 1)) || (rc = dmalloc(c, &c->score, d.I1)) ||
         (rc = dmalloc(c, &c->taken, d.I1)) || (rc = dmalloc(c, &c->top_i, 64)) ||
         (rc = dmalloc(c, &c->top_s, 64)))
@@ -367,14 +381,35 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
         return bail(rc);
     if (!src_idx) src_idx = d_idx;
     if (!src_val) src_val = d_val;
+    // the gene network's set-up runs on the side stream, beside the packing of the entries
+    // (which waits on the host link when they are in pinned host memory): it starts once the
+    // network's inputs are staged and the stream waits for it before anything that uses them
+    if (cudaEventRecord(c->side_ev[0], c->stream) != cudaSuccess) {
+        c->err = "event record";
+        return bail(SNECT_ECUDA);
+    }
+    auto graph_on_side = [&]() -> int {
+        SNECT_CUDA(c, cudaStreamWaitEvent(c->side, c->side_ev[0], 0));
+        cudaStream_t main_stream = c->stream;
+        c->stream = c->side;
+        const int r = prep_graph(c, d_edges, d_w);
+        c->stream = main_stream;
+        SNECT_CUDA(c, cudaEventRecord(c->side_ev[1], c->side));
+        SNECT_CUDA(c, cudaStreamWaitEvent(c->stream, c->side_ev[1], 0));
+        return r;
+    };
     if (!rc) rc = copy_in(c, c->G, G0, c->PI);
     if (!rc) rc = copy_in(c, c->U[0], U1, (int64_t)d.I1 * d.J1);
     if (!rc) rc = copy_in(c, c->U[1], U2, (int64_t)d.I2 * d.J2);
     if (!rc) rc = copy_in(c, c->U[2], U3, (int64_t)d.I3 * d.J3);
-    if (!rc)
-        rc = counting ? prep_fast_entries(c, src_idx, src_val, aligned16(src_idx) && aligned16(src_val))
-                      : prep_problem(c, src_idx, src_val);
-    if (!rc) rc = prep_graph(c, d_edges, d_w);
+    if (!rc) {
+        if (counting) {
+            rc = prep_fast_entries(c, src_idx, src_val, aligned16(src_idx) && aligned16(src_val), graph_on_side);
+        } else {
+            rc = prep_problem(c, src_idx, src_val);
+            if (!rc) rc = graph_on_side();
+        }
+    }
     if (d_idx) cudaFreeAsync(d_idx, c->stream);
     if (d_val) cudaFreeAsync(d_val, c->stream);
     if (d_edges) cudaFreeAsync(d_edges, c->stream);
@@ -470,15 +505,24 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     float *d_val = nullptr;
     int rc = SNECT_OK;
     if (n_test > 0) {
-        // test entries in device memory are read in place, others copied first; the loss
-        // kernel checks them as it reads them
+        // test entries in device memory are read in place; others are copied on the side
+        // stream while the training entries' pass runs; the loss kernel checks them as it
+        // reads them
         const int32_t *ti = on_device(c, test_idx) ? test_idx : nullptr;
         const float *tv = on_device(c, test_val) ? test_val : nullptr;
-        if ((!ti && (rc = stage(c, &d_idx, test_idx, n_test * 3))) || (!tv && (rc = stage(c, &d_val, test_val, n_test)))) {
-            dfree(c, d_idx);
-            dfree(c, d_val);
-            dfree(c, W);
-            return rc;
+        if (!ti || !tv) {
+            if ((!ti && (rc = stage(c, &d_idx, test_idx, n_test * 3, true))) ||
+                (!tv && (rc = stage(c, &d_val, test_val, n_test, true))) ||
+                (cudaEventRecord(c->side_ev[1], c->side) != cudaSuccess &&
+                 (rc = fail(c, SNECT_ECUDA, "event record"))) ||
+                (cudaStreamWaitEvent(c->stream, c->side_ev[1], 0) != cudaSuccess &&
+                 (rc = fail(c, SNECT_ECUDA, "stream wait")))) {
+                cudaStreamSynchronize(c->side);
+                dfree(c, d_idx);
+                dfree(c, d_val);
+                dfree(c, W);
+                return rc;
+            }
         }
         cudaError_t e = launch_loss_checked(c, ti ? ti : d_idx, tv ? tv : d_val, n_test, 1, c->flag, W);
         if (e != cudaSuccess) rc = fail(c, SNECT_ECUDA, cudaGetErrorString(e));

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -39,6 +40,10 @@ struct Ctx {
     int32_t PI = 0, SJ = 0;  // J1*J2*J3 and J1+J2+J3
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // a second stream for set-up and objective work that overlaps work on `stream`, and the
+    // events that order the two (created with the context)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int device = 0;
     std::atomic<int64_t> launches{0};
     std::string err;
@@ -197,7 +202,8 @@ int prep_fast_tiles(Ctx *c);       // prep.cu: groups each wave's entries by pla
 // fast mode: true when the set-up can order the entries by counting (sets the wave size);
 // prep_fast_entries then packs, validates, counts and orders them in one read of the inputs
 bool fast_counting_fits(Ctx *c);
-int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec);
+// (between: called once the packing pass is queued and before the host waits for it)
+int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec, const std::function<int()> &between);
 int init_fast(Ctx *c);             // sweep_fast.cu: buffers and launch shape of the fast sweep
 int enqueue_fast_epoch(Ctx *c);
 cudaError_t refresh_bf16_rows(Ctx *c);  // U2 -> its BF16 copy, when the context keeps one

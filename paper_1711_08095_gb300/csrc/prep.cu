@@ -506,7 +506,10 @@ int prep_det_groups(Ctx *c) {
 int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     int64_t m = c->m;
     int32_t I2 = c->d.I2;
-    SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    // the network's own status words (validation, maximum degree), so that it can run beside
+    // the packing of the entries, which uses the first
+    int32_t *gflag = c->flag + 4;
+    SNECT_CUDA(c, cudaMemsetAsync(gflag, 0, sizeof(int32_t), c->stream));
     if (m == 0) {
         SNECT_CUDA(c, cudaMemsetAsync(c->csr_ptr, 0, sizeof(int32_t) * (I2 + 1), c->stream));
         c->max_degree = 0;
@@ -519,19 +522,19 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     SNECT_CUDA(c, scratch_alloc(c, &vals, sizeof(int32_t) * 2 * m));
     SNECT_CUDA(c, scratch_alloc(c, &vals2, sizeof(int32_t) * 2 * m));
     k_half_edges<<<ceil_div(m, 256), 256, 0, c->stream>>>(d_edges, d_w, m, I2, keys, vals, c->edges,
-                                                          c->ew, c->flag);
+                                                          c->ew, gflag);
     c->launches++;
     int rc = sort_pairs(c, keys, vals, keys2, vals2, 2 * m, 32 + bits_for((uint64_t)I2));
     if (rc == SNECT_OK) {
         k_csr<<<ceil_div(2 * m + 1, 256), 256, 0, c->stream>>>(keys2, vals2, 2 * m, I2, c->ew,
                                                                c->csr_ptr, c->csr_col, c->csr_w,
-                                                               c->flag);
+                                                               gflag);
         c->launches++;
     }
     int32_t *d_maxdeg = nullptr;
     if (rc == SNECT_OK) {
         // the flag word's neighbour holds the maximum degree
-        d_maxdeg = c->flag + 1;
+        d_maxdeg = gflag + 1;
         cudaMemsetAsync(d_maxdeg, 0, sizeof(int32_t), c->stream);
         k_max_degree<<<ceil_div(I2, 256), 256, 0, c->stream>>>(c->csr_ptr, I2, d_maxdeg);
         c->launches++;
@@ -543,7 +546,7 @@ int prep_graph(Ctx *c, const int32_t *d_edges, const float *d_w) {
     if (rc) return rc;
     SNECT_CUDA(c, cudaGetLastError());
     int32_t hf[2] = {0, 0};
-    SNECT_CUDA(c, cudaMemcpyAsync(hf, c->flag, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
+    SNECT_CUDA(c, cudaMemcpyAsync(hf, gflag, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
     SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
     if (hf[0]) return fail(c, SNECT_EINVAL, "gene network:" + flag_message(hf[0]));
     c->max_degree = hf[1];
@@ -721,7 +724,7 @@ int prep_fast_tiles(Ctx *c) {
 // The counting form (fast_counting_fits): packing, validation, the counts |Omega^{n,i}|, the
 // wave table and the ordering in one read of the inputs, which stay where the caller has
 // them when a kernel can read them there.
-int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec) {
+int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec, const std::function<int()> &between) {
     fast_waves(c);
     const int64_t n = c->nnz, W = c->wave, nb = fast_buckets(c), S = c->n_waves * c->d.I3;
     const Dims &d = c->d;
@@ -770,6 +773,17 @@ int prep_fast_entries(Ctx *c, const int32_t *idx, const float *val, bool vec) {
     SNECT_CUDA(c, cub::DeviceScan::ExclusiveSum(scan_tmp, tmp_bytes, bcnt, first, (int)nb, c->stream));
     c->launches++;
     cudaFreeAsync(scan_tmp, c->stream);
+    // the caller's work that can run while the packing pass does (the host waits below)
+    if (between) {
+        const int r = between();
+        if (r) {
+            cudaFreeAsync(tmp, c->stream);
+            cudaFreeAsync(rank, c->stream);
+            cudaFreeAsync(bcnt, c->stream);
+            cudaFreeAsync(first, c->stream);
+            return r;
+        }
+    }
     // the validation flag, and each (wave, platform) segment's start: bucket (w, k, 0)'s
     std::vector<int32_t> seg((size_t)S);
     int32_t bad = 0;
