@@ -648,11 +648,19 @@ def quality(loss, job_loss, job_epochs, epochs_run, small):
     return q
 
 
+def run_config(args, p, world):
+    """The workload's description, the same on both arms of the comparison."""
+    return dict(WORKLOAD, parallelism="replicas x%d" % world if world > 1 else "single GPU",
+                l2="inputs larger than L2: %d MB of entry records streamed per epoch" % (p.nnz * 16 // 10 ** 6),
+                small=bool(args.small), precision=args.precision, I=list(p.I), J=list(p.J),
+                nnz_train=int(p.nnz))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    p = make_problem(args.small)
+    p = make_problem(args.small, (16, 16, 5) if args.precision != "fp32" else (10, 10, 5))
     import oracle
 
     oracle.build()
@@ -668,7 +676,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(WORKLOAD, sample_entries_per_step=n),
+            "config": run_config(args, p, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "sequential FP64 oracle epoch over the first %d training entries per step" % n},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -766,10 +774,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism="replicas x%d" % world if world > 1 else "single GPU",
-                       l2="inputs larger than L2: %d MB of entry records streamed per epoch" % (p.nnz * 16 // 10 ** 6),
-                       small=bool(args.small), precision=args.precision, I=list(p.I), J=list(p.J),
-                       nnz_train=int(p.nnz)),
+        "config": run_config(args, p, world),
         "e2e": {"value": p.nnz * job_epochs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "step": "one training job: snect_init from pinned host buffers, %d epochs, objective and "

@@ -100,7 +100,9 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
                const float *U1, const float *U2, const float *U3, void *stream);
 
 /* Runs n_epochs epochs of Alg. 1 lines 2-14: the entry sweep (every batch in order, or the
- * fast sweep) followed by one network pass over the gene factor.  Asynchronous. */
+ * fast sweep) followed by one network pass over the gene factor, each epoch one launch of a
+ * CUDA graph that snect_init captured (captured again after a change of timing mode).
+ * Asynchronous. */
 int snect_epoch(snect_ctx *ctx, int32_t n_epochs);
 
 /* Deterministic mode only: runs mini-batches [first, first+count) of the visit order

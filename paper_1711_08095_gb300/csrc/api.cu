@@ -434,7 +434,17 @@ int snect_init(snect_ctx **out, const snect_config *cfg, const int32_t *idx, con
         if ((!counting && (rc = prep_fast_tiles(c))) || (rc = init_fast(c))) return bail(rc);
     }
     cudaError_t e = loss_init_attrs(c);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("set-up: ") + cudaGetErrorString(e);
+        return bail(SNECT_ECUDA);
+    }
+    // the epoch's CUDA graph is captured (on a stream of its own) while the set-up's last
+    // kernels run; if that fails, the first snect_epoch captures it again and reports why
+    if (build_epoch_graph(c) != SNECT_OK) {
+        c->epoch_exec = nullptr;
+        c->err.clear();
+    }
+    e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         c->err = std::string("set-up: ") + cudaGetErrorString(e);
         return bail(SNECT_ECUDA);

@@ -639,9 +639,10 @@ int build_fast_tiles(Ctx *c, const std::vector<int32_t> &h) {
                                                                     c->tile_len, c->tile_k);
         c->launches++;
     }
+    // (the host vectors may go out of scope: an asynchronous copy from pageable memory has
+    // staged the data before it returns)
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(d_seg, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
     if (e != cudaSuccess) return fail(c, SNECT_ECUDA, std::string("tile lists: ") + cudaGetErrorString(e));
     return SNECT_OK;
 }

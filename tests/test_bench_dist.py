@@ -69,6 +69,12 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the workload's description is the GPU arm's own (bench.run_config), key for key
+    cfg = d["config"]
+    assert cfg["I"] == [4500, 15000, 5] and cfg["J"] == [10, 10, 5] and cfg["nnz_train"] == 27_000_000
+    assert cfg["parallelism"] == "single GPU" and cfg["precision"] == "fp32" and cfg["small"] is False
+    assert set(cfg) == {"workload", "I", "J", "nnz_train", "edges", "lam", "lam_g", "lr", "parallelism", "l2",
+                        "small", "precision"}
 
 
 def test_reference_arm_other_ranks_exit_without_work():
