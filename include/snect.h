@@ -147,7 +147,7 @@ int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, floa
  * staging for max_cells cells, and small fixed device buffers: the fold-in row, I1 scores and
  * flags, the top-k).  A scheduler thread admits queued requests oldest first whenever a slot
  * is free and the request's device memory -- its cells and its Gram partials, 256-byte aligned:
- * about 12 n + 4 ceil(n / 4096) (J1^2 + J1) bytes for n cells -- can be carved out of the arena;
+ * about 12 n + 4 ceil(n / 256) (J1^2 + J1) bytes for n cells -- can be carved out of the arena;
  * so the requests in flight never hold more device memory than the budget.  Admitted requests
  * run concurrently on their slots' streams; a host callback on each slot's stream hands the
  * finished request back to the scheduler.  A request's result does not depend on what else is

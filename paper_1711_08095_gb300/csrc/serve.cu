@@ -73,19 +73,36 @@ __global__ void __launch_bounds__(kFoldThreads)
         }
         for (int t = threadIdx.x; t < len; t += blockDim.x) sx[t] = val[base + t];
         __syncthreads();
+        // four independent sums over the cells (e mod 4), added in a fixed order at the end
 #pragma unroll
         for (int t = 0; t < kFoldPerThread; ++t) {
             const int s = threadIdx.x + t * kFoldThreads;
             if (s < nG) {
                 const int p = s / J1, q = s % J1;
-                float a = acc[t];
-                for (int e = 0; e < len; ++e) a = fmaf(sw[e * J1 + p], sw[e * J1 + q], a);
-                acc[t] = a;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                int e = 0;
+                for (; e + 4 <= len; e += 4) {
+                    a0 = fmaf(sw[e * J1 + p], sw[e * J1 + q], a0);
+                    a1 = fmaf(sw[(e + 1) * J1 + p], sw[(e + 1) * J1 + q], a1);
+                    a2 = fmaf(sw[(e + 2) * J1 + p], sw[(e + 2) * J1 + q], a2);
+                    a3 = fmaf(sw[(e + 3) * J1 + p], sw[(e + 3) * J1 + q], a3);
+                }
+                for (; e < len; ++e) a0 = fmaf(sw[e * J1 + p], sw[e * J1 + q], a0);
+                acc[t] += (a0 + a1) + (a2 + a3);
             }
         }
         if (threadIdx.x < J1) {
             const int p = threadIdx.x;
-            for (int e = 0; e < len; ++e) accx = fmaf(sx[e], sw[e * J1 + p], accx);
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int e = 0;
+            for (; e + 4 <= len; e += 4) {
+                a0 = fmaf(sx[e], sw[e * J1 + p], a0);
+                a1 = fmaf(sx[e + 1], sw[(e + 1) * J1 + p], a1);
+                a2 = fmaf(sx[e + 2], sw[(e + 2) * J1 + p], a2);
+                a3 = fmaf(sx[e + 3], sw[(e + 3) * J1 + p], a3);
+            }
+            for (; e < len; ++e) a0 = fmaf(sx[e], sw[e * J1 + p], a0);
+            accx += (a0 + a1) + (a2 + a3);
         }
     }
     float *out = part + (int64_t)blockIdx.x * (nG + J1);
@@ -102,6 +119,7 @@ __global__ void __launch_bounds__(kFoldThreads)
                    float *__restrict__ u_out, int32_t *__restrict__ status) {
     __shared__ double M[kMaxRank * kMaxRank];
     __shared__ double rhs[kMaxRank];
+    __shared__ double dinv[kMaxRank];  // 1 / L[j][j]
     const int nG = J1 * J1;
     for (int s = threadIdx.x; s < nG + J1; s += blockDim.x) {
         float a = 0.f;
@@ -113,36 +131,48 @@ __global__ void __launch_bounds__(kFoldThreads)
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    // Cholesky M = L L^T (lower triangle, in place), then two triangular solves
+    if (threadIdx.x >= 32) return;
+    // Cholesky M = L L^T (right-looking, lower triangle in place) by one warp: lane i owns row
+    // i; then the two triangular solves, one column at a time
+    const int lane = threadIdx.x;
+    constexpr unsigned FULL = 0xffffffffu;
     for (int j = 0; j < J1; ++j) {
-        double d = M[j * J1 + j];
-        for (int k = 0; k < j; ++k) d -= M[j * J1 + k] * M[j * J1 + k];
-        if (!(d > 0.0)) {
-            *status = 1;
-            for (int p = 0; p < J1; ++p) u_out[p] = 0.f;
+        const double dj = M[j * J1 + j];
+        if (!(dj > 0.0)) {  // the same value in every lane
+            if (lane < J1) u_out[lane] = 0.f;
+            if (lane == 0) *status = 1;
             return;
         }
-        d = sqrt(d);
-        M[j * J1 + j] = d;
-        for (int i = j + 1; i < J1; ++i) {
-            double s = M[i * J1 + j];
-            for (int k = 0; k < j; ++k) s -= M[i * J1 + k] * M[j * J1 + k];
-            M[i * J1 + j] = s / d;
+        const double d = sqrt(dj), inv = 1.0 / d;
+        __syncwarp(FULL);
+        if (lane == j) {
+            M[j * J1 + j] = d;
+            dinv[j] = inv;
         }
+        if (lane > j && lane < J1) M[lane * J1 + j] *= inv;
+        __syncwarp(FULL);
+        if (lane > j && lane < J1) {
+            const double lij = M[lane * J1 + j];
+            for (int m = j + 1; m <= lane; ++m) M[lane * J1 + m] -= lij * M[m * J1 + j];
+        }
+        __syncwarp(FULL);
     }
-    for (int i = 0; i < J1; ++i) {
-        double s = rhs[i];
-        for (int k = 0; k < i; ++k) s -= M[i * J1 + k] * rhs[k];
-        rhs[i] = s / M[i * J1 + i];
+    for (int i = 0; i < J1; ++i) {  // L y = rhs
+        const double yi = rhs[i] * dinv[i];
+        __syncwarp(FULL);
+        if (lane == i) rhs[i] = yi;
+        if (lane > i && lane < J1) rhs[lane] -= M[lane * J1 + i] * yi;
+        __syncwarp(FULL);
     }
-    for (int i = J1 - 1; i >= 0; --i) {
-        double s = rhs[i];
-        for (int k = i + 1; k < J1; ++k) s -= M[k * J1 + i] * rhs[k];
-        rhs[i] = s / M[i * J1 + i];
+    for (int i = J1 - 1; i >= 0; --i) {  // L^T u = y
+        const double ui = rhs[i] * dinv[i];
+        __syncwarp(FULL);
+        if (lane == i) rhs[i] = ui;
+        if (lane < i) rhs[lane] -= M[i * J1 + lane] * ui;
+        __syncwarp(FULL);
     }
-    for (int p = 0; p < J1; ++p) u_out[p] = (float)rhs[p];
-    *status = 0;
+    if (lane < J1) u_out[lane] = (float)rhs[lane];
+    if (lane == 0) *status = 0;
 }
 
 __global__ void k_cosine(const float *__restrict__ U1, int32_t I1, int32_t J1,

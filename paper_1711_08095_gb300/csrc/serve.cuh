@@ -8,7 +8,7 @@ namespace snect {
 constexpr int kFoldThreads = 256;                                       // threads per CTA
 constexpr int kFoldTile = 256;                                          // cells staged at once
 constexpr int kFoldPerThread = (kMaxRank * kMaxRank + kFoldThreads - 1) / kFoldThreads;
-constexpr int64_t kFoldChunk = 4096;                                    // cells per CTA
+constexpr int64_t kFoldChunk = 256;                                     // cells per CTA (one tile)
 
 // number of per-CTA partials of a query with n cells
 int64_t foldin_parts(int64_t n);

@@ -54,14 +54,25 @@ struct Result {
     double queue_ms = 0.0;
 };
 
+// byte offsets of a request's results in a slot's result block
+constexpr int64_t kResU = 0;                            // J1 <= 32 floats
+constexpr int64_t kResIdx = kResU + 4 * kMaxRank;       // k <= 64 rows
+constexpr int64_t kResScore = kResIdx + 4 * 64;         // their scores
+constexpr int64_t kResFlag = kResScore + 4 * 64;        // cell flag, solve status
+constexpr int64_t kResBytes = kResFlag + 8;
+
 struct Slot {
     Server *srv = nullptr;
     int index = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    int32_t *h_jk = nullptr;  // pinned
-    float *h_val = nullptr;
-    float *h_u = nullptr;
+    // pinned staging of a request: its cells, then its values at the offset they take in the
+    // arena block, so that one copy moves both
+    char *h_in = nullptr;
+    // a request's results, one block on the device and its pinned copy (one copy back):
+    // the fold-in row, the top-k rows and scores, the cell flag and the solve status
+    char *h_res = nullptr, *d_res = nullptr;
+    float *h_u = nullptr;  // views of h_res
     int32_t *h_idx = nullptr;
     float *h_score = nullptr;
     int32_t *h_flag = nullptr;
@@ -142,18 +153,10 @@ void arena_free(Server *S, int64_t off, int64_t bytes) {
 
 void free_slot(Slot &s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    cudaFreeHost(s.h_jk);
-    cudaFreeHost(s.h_val);
-    cudaFreeHost(s.h_u);
-    cudaFreeHost(s.h_idx);
-    cudaFreeHost(s.h_score);
-    cudaFreeHost(s.h_flag);
-    cudaFree(s.d_u);
+    cudaFreeHost(s.h_in);
+    cudaFreeHost(s.h_res);
+    cudaFree(s.d_res);
     cudaFree(s.d_score);
-    cudaFree(s.d_top_s);
-    cudaFree(s.d_status);
-    cudaFree(s.d_top_i);
-    cudaFree(s.d_flag);
     cudaFree(s.d_taken);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
@@ -168,18 +171,19 @@ cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
     if ((e = (x)) != cudaSuccess) return e;
     TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
     TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-    TRY(cudaMallocHost((void **)&s.h_jk, sizeof(int32_t) * 2 * max_cells));
-    TRY(cudaMallocHost((void **)&s.h_val, sizeof(float) * max_cells));
-    TRY(cudaMallocHost((void **)&s.h_u, sizeof(float) * kMaxRank));
-    TRY(cudaMallocHost((void **)&s.h_idx, sizeof(int32_t) * 64));
-    TRY(cudaMallocHost((void **)&s.h_score, sizeof(float) * 64));
-    TRY(cudaMallocHost((void **)&s.h_flag, sizeof(int32_t) * 2));
-    TRY(cudaMalloc((void **)&s.d_u, sizeof(float) * kMaxRank));
+    TRY(cudaMallocHost((void **)&s.h_in, align_up((int64_t)max_cells * sizeof(int2)) + sizeof(float) * max_cells));
+    TRY(cudaMallocHost((void **)&s.h_res, kResBytes));
+    TRY(cudaMalloc((void **)&s.d_res, kResBytes));
+    s.h_u = reinterpret_cast<float *>(s.h_res + kResU);
+    s.h_idx = reinterpret_cast<int32_t *>(s.h_res + kResIdx);
+    s.h_score = reinterpret_cast<float *>(s.h_res + kResScore);
+    s.h_flag = reinterpret_cast<int32_t *>(s.h_res + kResFlag);
+    s.d_u = reinterpret_cast<float *>(s.d_res + kResU);
+    s.d_top_i = reinterpret_cast<int32_t *>(s.d_res + kResIdx);
+    s.d_top_s = reinterpret_cast<float *>(s.d_res + kResScore);
+    s.d_flag = reinterpret_cast<int32_t *>(s.d_res + kResFlag);
+    s.d_status = s.d_flag + 1;
     TRY(cudaMalloc((void **)&s.d_score, sizeof(float) * c->d.I1));
-    TRY(cudaMalloc((void **)&s.d_top_s, sizeof(float) * 64));
-    TRY(cudaMalloc((void **)&s.d_status, sizeof(int32_t)));
-    TRY(cudaMalloc((void **)&s.d_top_i, sizeof(int32_t) * 64));
-    TRY(cudaMalloc((void **)&s.d_flag, sizeof(int32_t)));
     TRY(cudaMalloc((void **)&s.d_taken, c->d.I1));
 #undef TRY
     return cudaSuccess;
@@ -206,22 +210,18 @@ cudaError_t launch_request(Ctx *c, Slot &s) {
     s.d_val = reinterpret_cast<float *>(base + align_up(n * (int64_t)sizeof(int2)));
     s.d_part = reinterpret_cast<float *>(base + align_up(n * (int64_t)sizeof(int2)) +
                                          align_up(n * (int64_t)sizeof(float)));
-    std::memcpy(s.h_jk, r.jk.data(), sizeof(int32_t) * 2 * n);
-    std::memcpy(s.h_val, r.val.data(), sizeof(float) * n);
+    // cells and values staged as they lie in the arena block: one copy in
+    const int64_t val_off = align_up(n * (int64_t)sizeof(int2));
+    std::memcpy(s.h_in, r.jk.data(), sizeof(int32_t) * 2 * n);
+    std::memcpy(s.h_in + val_off, r.val.data(), sizeof(float) * n);
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(s.d_jk, s.h_jk, sizeof(int2) * n, cudaMemcpyHostToDevice, s.stream))) return e;
-    if ((e = cudaMemcpyAsync(s.d_val, s.h_val, sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(base, s.h_in, val_off + sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
     if ((e = cudaMemsetAsync(s.d_flag, 0, sizeof(int32_t), s.stream))) return e;
     if ((e = launch_check_cells(c, s.stream, s.d_jk, s.d_val, n, s.d_flag))) return e;
     if ((e = launch_foldin(c, s.stream, s.d_jk, s.d_val, n, c->wtable, s.d_part, s.d_u, s.d_status))) return e;
     if ((e = launch_topk(c, s.stream, s.d_u, r.k, s.d_score, s.d_taken, s.d_top_i, s.d_top_s))) return e;
-    if ((e = cudaMemcpyAsync(s.h_u, s.d_u, sizeof(float) * c->d.J1, cudaMemcpyDeviceToHost, s.stream))) return e;
-    if ((e = cudaMemcpyAsync(s.h_idx, s.d_top_i, sizeof(int32_t) * r.k, cudaMemcpyDeviceToHost, s.stream))) return e;
-    if ((e = cudaMemcpyAsync(s.h_score, s.d_top_s, sizeof(float) * r.k, cudaMemcpyDeviceToHost, s.stream)))
-        return e;
-    if ((e = cudaMemcpyAsync(s.h_flag, s.d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream))) return e;
-    if ((e = cudaMemcpyAsync(s.h_flag + 1, s.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream)))
-        return e;
+    // every result in one copy back
+    if ((e = cudaMemcpyAsync(s.h_res, s.d_res, kResBytes, cudaMemcpyDeviceToHost, s.stream))) return e;
     if ((e = cudaEventRecord(s.done, s.stream))) return e;
     return cudaLaunchHostFunc(s.stream, on_slot_done, &s);
 }

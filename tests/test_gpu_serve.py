@@ -70,9 +70,7 @@ def test_foldin_is_the_same_alone_and_repeated(served):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("k", [1, 10, 64])
-def test_topk_matches_oracle(served, k):
-    m, c = served
+def check_topk(m, c, k):
     jk, x, _ = S.serving_query(m, q=100 + k, size=5000)
     u = c.foldin(jk, x)
     idx, sc = c.topk(u, k)
@@ -88,6 +86,11 @@ def test_topk_matches_oracle(served, k):
         sep = (t == 0 or osc[t - 1] - osc[t] > tol) and (t == k - 1 or osc[t] - osc[t + 1] > tol)
         if sep:
             assert idx[t] == oi[t]
+
+
+@pytest.mark.parametrize("k", [1, 10, 64])
+def test_topk_matches_oracle(served, k):
+    check_topk(*served, k)
 
 
 def test_bad_queries_are_rejected(served):

@@ -16,9 +16,9 @@ pytestmark = pytest.mark.gpu
 
 def request_bytes(n, J1):
     """Arena bytes of a request of n cells: cells (8 B), values (4 B) and the fold-in's
-    per-4,096-cell Gram partials, each rounded up to 256 bytes."""
+    per-256-cell Gram partials, each rounded up to 256 bytes."""
     up = lambda x: -(-x // 256) * 256
-    return up(8 * n) + up(4 * n) + up(4 * math.ceil(n / 4096) * (J1 * J1 + J1))
+    return up(8 * n) + up(4 * n) + up(4 * math.ceil(n / 256) * (J1 * J1 + J1))
 
 
 @pytest.fixture(scope="module")
