@@ -119,7 +119,8 @@ int snect_edge_pass(snect_ctx *ctx);
  * test_idx/test_val: any, n_test held-out entries (may be 0); read in place from device
  * memory, copied otherwise.  Predictions are FP32, squared residuals summed in compensated
  * FP32 per thread and in FP64 beyond.  Synchronises.  Errors: SNECT_EINVAL for a test entry
- * with an index outside the tensor or a non-finite value (the context stays usable). */
+ * with an index outside the tensor or a non-finite value (the context stays usable);
+ * SNECT_ETIMEDOUT when a completion wait of an earlier fast-mode sweep gave up. */
 int snect_loss(snect_ctx *ctx, const int32_t *test_idx, const float *test_val, int64_t n_test,
                snect_loss_t *out);
 
@@ -310,7 +311,7 @@ int snect_sweep_times(snect_ctx *ctx, double *ms_total, int64_t *n_launches, int
  * The factors and core are not changed, and the accumulators are cleared again afterwards;
  * the fast mode's curvature state (platform systems, eigenbases) is refreshed as the wave's
  * own sweep refreshes it.  Fast mode only.  Synchronises.  Errors: SNECT_EINVAL (mode, wave
- * index), SNECT_ETIMEDOUT (a tensor-core wait of the BF16 sweep gave up), SNECT_ECUDA. */
+ * index), SNECT_ETIMEDOUT (a completion wait of the sweep gave up), SNECT_ECUDA. */
 int snect_wave_grads(snect_ctx *ctx, int64_t w, float *gA, float *gB, float *M, float *nA, float *nB,
                      int64_t *first, int64_t *count);
 

@@ -554,10 +554,10 @@ int snect_loss(snect_ctx *h, const int32_t *test_idx, const float *test_val, int
     dfree(c, W);
     if (rc == SNECT_OK && bad) rc = fail(c, SNECT_EINVAL, "test " + entries_error(bad));
     if (rc) return rc;
-    if (c->sweep_kind < 0) {  // a tensor-core wait that gave up
-        int32_t tc_err = 0;
-        SNECT_CUDA(c, cudaMemcpy(&tc_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a tensor-core completion wait timed out in the sweep");
+    if (c->cfg.batch == 0) {  // a sweep wait that gave up (tensor-core completion, record copies)
+        int32_t sweep_err = 0;
+        SNECT_CUDA(c, cudaMemcpy(&sweep_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (sweep_err) return fail(c, SNECT_ETIMEDOUT, "a completion wait timed out in the sweep");
     }
     const double lam = c->cfg.lambda, lg = c->cfg.lambda_g;
     out->data = 0.5 * acc[0];

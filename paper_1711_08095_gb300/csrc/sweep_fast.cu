@@ -740,6 +740,22 @@ __global__ void __launch_bounds__(kFastThreads, sweep_min_blocks<CJ1, CJ2>()) k_
 // 4 components per lane where J2 allows (FP32: one 16-byte load; BF16: one 8-byte load),
 // else 2 or 1.  (8 BF16 components per lane, 2 lanes per entry at J2 = 16, was measured slower:
 // 16-entry steps cross patient runs twice as often and a run's close costs twice the shuffles.)
+// In the batched sweep, entry records reach a lane-group warp by bulk copies (the TMA
+// engine's cp.async.bulk) into shared memory, kRecSteps steps of records at a time, two
+// chunks per warp in flight.
+constexpr int kRecSteps = 16;
+
+// lane 0 of a warp: copies `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on the mbarrier, which expects the bytes
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
 template <int CJ2, int GB>
 struct LaneGroup {
     static constexpr int VEC = (GB || CJ2 % 4 == 0) ? 4 : (CJ2 % 2 == 0 ? 2 : 1);
@@ -797,7 +813,7 @@ constexpr int lg_batch_min_blocks() { return CJ1 * CJ2 <= 100 ? 4 : 3; }
 
 // The lane-group sweep of one problem's wave by the CTA's warps: W warps share the wave,
 // this CTA's warps are w0, w0 + 1, ...  (sm: the CTA's dynamic shared memory)
-template <int CJ1, int CJ2, int CJ3, int GB>
+template <int CJ1, int CJ2, int CJ3, int GB, bool TMA>
 __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int64_t W, int64_t w0) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int J1 = CJ1, J2 = CJ2, J3 = CJ3, Q = J1 * J2, PI = Q * J3;
@@ -885,12 +901,56 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
             w2v[v] = acc;
         }
     };
-    auto load_rec = [&](int e, bool ok) {
+    // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
+    const int lo32 = (int)lo, hi32 = (int)hi;
+    // TMA: the warp's records arrive in chunks of kRecSteps steps (CH records) by bulk copies
+    // into two shared buffers: chunk c goes to buffer c & 1 and completes its barrier's phase
+    // (c >> 1) & 1.  Entering chunk c the warp starts chunk c + 1's copy (into chunk c - 1's
+    // buffer, which every lane has read) and waits for chunk c.  A wait that gives up sets the
+    // error word and ends the warp's range before the records it never got.  Otherwise each
+    // lane loads its records from global memory, evict-first (they are streamed once per
+    // epoch).  Measured on the paper-scale problem, the copies made the single-problem sweep
+    // slower (45.98 -> 50.97 us per wave at 10 x 10 x 5, 1.040 -> 1.104 ms per epoch at
+    // 16 x 16 x 5) and the batched sweep faster (19.15 -> 18.41 ms per epoch of the 96
+    // decompositions), so only the batch kernel takes them.
+    constexpr int CH = kRecSteps * E;
+    Rec *rbuf = nullptr;
+    uint64_t *rbar = nullptr;
+    if constexpr (TMA) {
+        __shared__ __align__(128) Rec sRec[kFastThreads / 32][2][CH];
+        __shared__ __align__(8) uint64_t sRecBar[kFastThreads / 32][2];
+        rbuf = &sRec[warp][0][0];
+        rbar = sRecBar[warp];
+    }
+    int issued = -1, waited = -1;  // the same in every lane
+    int hi_eff = hi32;
+    auto issue = [&](int c) {
+        const int s0 = lo32 + c * CH;
+        if (s0 >= hi_eff) return;
+        issued = c;
+        if (lane == 0)
+            bulk_load(rbuf + (c & 1) * CH, A.rec + s0, (uint32_t)(min(CH, hi32 - s0) * (int)sizeof(Rec)),
+                      rbar + (c & 1));
+    };
+    auto await = [&](int c) {
+        const bool ok = __all_sync(FULL, tc::mbar_wait(rbar + (c & 1), (uint32_t)((c >> 1) & 1)));
+        waited = c;
+        if (!ok) {
+            if (lane == 0) atomicOr(A.err, 1);
+            hi_eff = min(hi_eff, lo32 + c * CH);
+        }
+    };
+    // the record of slot g at step t (entry e = lo + t E + g)
+    auto load_rec = [&](int t, int e, bool ok) {
         Rec r;
         r.i = r.j = r.k = -1;
         r.x = 0.f;
-        if (ok) {  // streamed once per epoch: evict-first
-            const int4 v = __ldcs(reinterpret_cast<const int4 *>(A.rec + e));
+        if (ok) {
+            int4 v;
+            if constexpr (TMA)
+                v = *reinterpret_cast<const int4 *>(rbuf + ((t / kRecSteps) & 1) * CH + (t % kRecSteps) * E + g);
+            else
+                v = __ldcs(reinterpret_cast<const int4 *>(A.rec + e));
             r.i = v.x;
             r.j = v.y;
             r.k = v.z;
@@ -898,8 +958,16 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
         }
         return r;
     };
-    // entry positions and row offsets fit in 32 bits here (the kernel is chosen only then)
-    const int lo32 = (int)lo, hi32 = (int)hi;
+    if constexpr (TMA) {
+        if (lane == 0) {
+            tc::mbar_init(rbar);
+            tc::mbar_init(rbar + 1);
+        }
+        __syncwarp();
+        issue(0);
+        issue(1);
+        if (issued >= 0) await(0);
+    }
     // this lane's VEC components of the gene row of record r (zeros when !ok), as loaded: VEC
     // floats, or for BF16 gathers 4 BF16 values in one 8-byte word (unpacked when used, so the
     // prefetched row takes 2 registers)
@@ -950,16 +1018,26 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     // without moves (measured at 10 x 10 x 5: 46.95 -> 45.22 us per paper-scale wave, with the
     // shuffle-tree group sum); at J2 = 16 the unrolled loop spilled, and it is left rolled.
     constexpr int UNROLL = (!GB && CJ2 % 4 != 0) ? 3 : 1;
-    Rec cur = load_rec(lo32 + g, act && lo32 + g < hi32);
-    Rec nxt = load_rec(lo32 + g + E, act && lo32 + g + E < hi32);
-    Raw bnext = load_row(cur, act && lo32 + g < hi32);
+    static_assert(kRecSteps >= 2, "the first two steps' records come from chunk 0");
+    Rec cur = load_rec(0, lo32 + g, act && lo32 + g < (TMA ? hi_eff : hi32));
+    Rec nxt = load_rec(1, lo32 + g + E, act && lo32 + g + E < (TMA ? hi_eff : hi32));
+    Raw bnext = load_row(cur, act && lo32 + g < (TMA ? hi_eff : hi32));
     auto step = [&](int base) {
         const int e = base + g;
-        const bool valid = act && e < hi32;
+        const bool valid = act && e < (TMA ? hi_eff : hi32);
         float b[VEC];
         unpack(bnext, b);
-        const Rec nn = load_rec(e + 2 * E, act && e + 2 * E < hi32);
-        bnext = load_row(nxt, act && e + E < hi32);
+        int tn = 0;  // the step whose records are fetched now
+        if constexpr (TMA) {
+            tn = (base - lo32) / E + 2;
+            if (tn % kRecSteps == 0 && lo32 + tn * E < (TMA ? hi_eff : hi32)) {  // entering a chunk (the same in every lane)
+                __syncwarp();  // every lane is done with the previous chunk's buffer
+                issue(tn / kRecSteps + 1);
+                await(tn / kRecSteps);
+            }
+        }
+        const Rec nn = load_rec(tn, e + 2 * E, act && e + 2 * E < (TMA ? hi_eff : hi32));
+        bnext = load_row(nxt, act && e + E < (TMA ? hi_eff : hi32));
         // an entry's residual, its gene-row gradient and its share of s (b = 0 off the wave)
         auto entry = [&](bool mine) {
             float part = 0.f;
@@ -1000,10 +1078,12 @@ __device__ __forceinline__ void lg_sweep_body(const FastArgs &A, float *sm, int6
     };
     if constexpr (UNROLL > 1) {
 #pragma unroll(UNROLL)
-        for (int base = lo32; base < hi32; base += E) step(base);
+        for (int base = lo32; base < (TMA ? hi_eff : hi32); base += E) step(base);
     } else {
-        for (int base = lo32; base < hi32; base += E) step(base);
+        for (int base = lo32; base < (TMA ? hi_eff : hi32); base += E) step(base);
     }
+    if constexpr (TMA)
+        for (int c = waited + 1; c <= issued; ++c) await(c);  // no copy left in flight at exit
     if (ci >= 0) close_run();
     flush_m();
     __syncthreads();
@@ -1018,7 +1098,7 @@ __global__ void __launch_bounds__(kFastThreads, lg_min_blocks<CJ1, CJ2, GB>()) k
         dense_pre<CJ1, CJ2, CJ3>(A.pre, sm, (int)blockIdx.x);
         return;
     }
-    lg_sweep_body<CJ1, CJ2, CJ3, GB>(A, sm, (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32),
+    lg_sweep_body<CJ1, CJ2, CJ3, GB, false>(A, sm, (int64_t)(gridDim.x - kPreCtas) * (kFastThreads / 32),
                                      (int64_t)(blockIdx.x - kPreCtas) * (kFastThreads / 32));
 }
 
@@ -1039,7 +1119,7 @@ __global__ void __launch_bounds__(kFastThreads, lg_batch_min_blocks<CJ1, CJ2, GB
     const int pid = cta_prob[b];
     if (threadIdx.x == 0) sArgs = probs[pid];
     __syncthreads();
-    lg_sweep_body<CJ1, CJ2, CJ3, GB>(sArgs, sm, (int64_t)prob_ctas[pid] * (kFastThreads / 32),
+    lg_sweep_body<CJ1, CJ2, CJ3, GB, true>(sArgs, sm, (int64_t)prob_ctas[pid] * (kFastThreads / 32),
                                      (int64_t)cta_rank[b] * (kFastThreads / 32));
 }
 
@@ -2703,7 +2783,7 @@ int fast_wave_grads(Ctx *c, int64_t w, float *gA, float *gB, float *M, float *nA
     SNECT_CUDA(c, cudaMemcpyAsync(&tc_err, c->flag + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     SNECT_CUDA(c, clear());
     SNECT_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a tensor-core completion wait timed out in the sweep");
+    if (tc_err) return fail(c, SNECT_ETIMEDOUT, "a completion wait timed out in the sweep");
     return SNECT_OK;
 }
 
