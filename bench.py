@@ -70,7 +70,7 @@ def parse():
                          "instead (for profiling)")
     ap.add_argument("--serve-queries", type=int, default=20000, help="fold-in + top-k queries (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, queries/s")
-    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[5000.0, 10000.0, 20000.0, 40000.0],
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[5000.0, 10000.0, 20000.0, 40000.0, 80000.0],
                     help="higher offered rates (queries/s) for the capacity sweep")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 vs BF16 refit at 16x16x5")
     ap.add_argument("--batched-scale", type=float, default=1.0,
@@ -271,30 +271,33 @@ def kernel_breakdown(ctx, nnz, epochs):
     return out
 
 
-def serve_stream(srv, pool, arrivals, k=10):
-    """Submits pool[q % len(pool)] at each arrival time (seconds from now) from a producer
-    thread and collects every result; returns (latencies ms, seconds from the first arrival
-    to the last result)."""
+def serve_stream(srv, pool, arrivals, k=10, producers=4):
+    """Submits pool[q % len(pool)] at each arrival time (seconds from now) and collects every
+    result; returns (latencies ms, seconds from the first arrival to the last result).  The
+    arrivals are dealt round-robin to several producer threads (the library call releases
+    the interpreter lock), so that the submitting side keeps up with high offered rates."""
     tickets = [None] * len(arrivals)
     t0 = time.perf_counter()
 
-    def producer():
-        for qi, ta in enumerate(arrivals):
-            d = t0 + ta - time.perf_counter()
+    def producer(first):
+        for qi in range(first, len(arrivals), producers):
+            d = t0 + arrivals[qi] - time.perf_counter()
             if d > 0:
                 time.sleep(d)
             jk, x, _ = pool[qi % len(pool)]
             tickets[qi] = srv.submit(jk, x, k)
 
-    th = threading.Thread(target=producer)
-    th.start()
+    ths = [threading.Thread(target=producer, args=(f,)) for f in range(producers)]
+    for th in ths:
+        th.start()
     lat = []
     for qi in range(len(arrivals)):
         while tickets[qi] is None:
             time.sleep(0.0002)
         lat.append(srv.poll(tickets[qi], k)[3])
     t_end = time.perf_counter()
-    th.join()
+    for th in ths:
+        th.join()
     return np.array(lat), t_end - t0
 
 
