@@ -157,7 +157,8 @@ int snect_topk(snect_ctx *ctx, const float *u, int32_t k, int32_t *idx_out, floa
 typedef struct snect_server snect_server;
 int snect_serve_start(snect_ctx *ctx, int32_t n_slots, int64_t mem_budget_bytes, int32_t max_cells,
                       snect_server **out);
-/* Queues one query: jk (host, n*2 int32 (gene, platform)), val (host, n floats) are copied;
+/* Queues one query: jk (host, n*2 int32 (gene, platform)), val (host, n floats) are copied
+ * (into a pinned buffer from the server's pool, four per slot, when one is free);
  * 1 <= n <= max_cells, 1 <= k <= min(I1, 64).  Thread-safe.  *ticket identifies the result. */
 int snect_serve_submit(snect_server *srv, const int32_t *jk, const float *val, int64_t n, int32_t k,
                        int64_t *ticket);

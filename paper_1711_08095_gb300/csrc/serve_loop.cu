@@ -39,7 +39,10 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
     int64_t ticket;
-    std::vector<int32_t> jk;
+    int64_t n = 0;            // cells
+    char *pin = nullptr;      // pinned staging from the server's pool, laid out like the arena
+                              // block (cells, then values at their aligned offset), or null:
+    std::vector<int32_t> jk;  // then the cells and values are held here
     std::vector<float> val;
     int32_t k;
     Clock::time_point t_submit;
@@ -103,6 +106,10 @@ struct Server {
     std::condition_variable cv_submit, cv_done;
     std::deque<Request> queue;
     std::unordered_map<int64_t, Result> done;
+    // pinned staging for submitted requests (4 per slot): submit copies a request's cells and
+    // values into one on the submitting thread, so the scheduler only issues the copy to the
+    // device; a request that finds none free keeps its own copy, staged at admission
+    std::vector<char *> pin_free, pin_all;
     std::atomic<bool> stop{false};
     std::thread worker;
     int64_t next_ticket = 1;
@@ -204,7 +211,7 @@ void CUDART_CB on_slot_done(void *p) {
 // launches one request on its slot (scheduler thread); its device buffers start at arena_off
 cudaError_t launch_request(Ctx *c, Slot &s) {
     const Request &r = s.req;
-    const int64_t n = (int64_t)r.val.size();
+    const int64_t n = r.n;
     char *base = s.srv->arena + s.arena_off;
     s.d_jk = reinterpret_cast<int2 *>(base);
     s.d_val = reinterpret_cast<float *>(base + align_up(n * (int64_t)sizeof(int2)));
@@ -212,10 +219,14 @@ cudaError_t launch_request(Ctx *c, Slot &s) {
                                          align_up(n * (int64_t)sizeof(float)));
     // cells and values staged as they lie in the arena block: one copy in
     const int64_t val_off = align_up(n * (int64_t)sizeof(int2));
-    std::memcpy(s.h_in, r.jk.data(), sizeof(int32_t) * 2 * n);
-    std::memcpy(s.h_in + val_off, r.val.data(), sizeof(float) * n);
+    const char *staged = r.pin;
+    if (!staged) {
+        std::memcpy(s.h_in, r.jk.data(), sizeof(int32_t) * 2 * n);
+        std::memcpy(s.h_in + val_off, r.val.data(), sizeof(float) * n);
+        staged = s.h_in;
+    }
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(base, s.h_in, val_off + sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
+    if ((e = cudaMemcpyAsync(base, staged, val_off + sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
     if ((e = cudaMemsetAsync(s.d_flag, 0, sizeof(int32_t), s.stream))) return e;
     if ((e = launch_check_cells(c, s.stream, s.d_jk, s.d_val, n, s.d_flag))) return e;
     if ((e = launch_foldin(c, s.stream, s.d_jk, s.d_val, n, c->wtable, s.d_part, s.d_u, s.d_status))) return e;
@@ -252,6 +263,8 @@ void scheduler(Server *S) {
                 res.score.assign(s.h_score, s.h_score + s.req.k);
             }
             S->done[s.req.ticket] = std::move(res);
+            if (s.req.pin) S->pin_free.push_back(s.req.pin);
+            s.req.pin = nullptr;
             s.busy = false;
             arena_free(S, s.arena_off, s.bytes);
             s.arena_off = -1;
@@ -268,7 +281,7 @@ void scheduler(Server *S) {
                     break;
                 }
             if (free_slot_i < 0) break;
-            const int64_t need = request_bytes(c, (int64_t)S->queue.front().val.size());
+            const int64_t need = request_bytes(c, S->queue.front().n);
             const int64_t off = arena_alloc(S, need);
             if (off < 0) break;  // wait for requests in flight to return their memory
             Slot &s = S->slots[free_slot_i];
@@ -292,6 +305,8 @@ void scheduler(Server *S) {
                 S->done[s.req.ticket] = std::move(res);
                 S->err = std::string("serving launch: ") + cudaGetErrorString(e);
                 cudaStreamSynchronize(s.stream);
+                if (s.req.pin) S->pin_free.push_back(s.req.pin);
+                s.req.pin = nullptr;
                 s.busy = false;
                 arena_free(S, s.arena_off, s.bytes);
                 s.arena_off = -1;
@@ -353,6 +368,17 @@ int snect_serve_start(snect_ctx *h, int32_t n_slots, int64_t mem_budget_bytes, i
             return fail(c, SNECT_ENOMEM, std::string("serving slot: ") + cudaGetErrorString(e));
         }
     }
+    // pinned request staging: up to 4 per slot (fewer if pinned memory runs short)
+    const size_t pin_bytes = (size_t)(align_up((int64_t)max_cells * sizeof(int2)) + (int64_t)sizeof(float) * max_cells);
+    for (int i = 0; i < 4 * n_slots; ++i) {
+        char *b = nullptr;
+        if (cudaMallocHost((void **)&b, pin_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        S->pin_all.push_back(b);
+        S->pin_free.push_back(b);
+    }
     S->worker = std::thread(scheduler, S);
     *out = reinterpret_cast<snect_server *>(S);
     return SNECT_OK;
@@ -365,13 +391,29 @@ int snect_serve_submit(snect_server *h, const int32_t *jk, const float *val, int
     if (n < 1 || n > S->max_cells) return SNECT_EINVAL;
     if (k < 1 || k > 64 || k > S->c->d.I1) return SNECT_EINVAL;
     Request r;
-    r.jk.assign(jk, jk + 2 * n);
-    r.val.assign(val, val + n);
-    r.k = k;
     r.t_submit = Clock::now();
+    r.n = n;
+    r.k = k;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->stop.load()) return SNECT_EBUSY;
+        if (!S->pin_free.empty()) {
+            r.pin = S->pin_free.back();
+            S->pin_free.pop_back();
+        }
+    }
+    if (r.pin) {  // staged as it will lie in the arena block, outside the lock
+        std::memcpy(r.pin, jk, sizeof(int32_t) * 2 * n);
+        std::memcpy(r.pin + align_up(n * (int64_t)sizeof(int2)), val, sizeof(float) * n);
+    } else {
+        r.jk.assign(jk, jk + 2 * n);
+        r.val.assign(val, val + n);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop.load()) {
+            if (r.pin) S->pin_free.push_back(r.pin);
+            return SNECT_EBUSY;
+        }
         r.ticket = S->next_ticket++;
         *ticket = r.ticket;
         S->queue.push_back(std::move(r));
@@ -423,6 +465,7 @@ int snect_serve_stop(snect_server *h) {
     S->cv_submit.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto &s : S->slots) free_slot(s);
+    for (char *b : S->pin_all) cudaFreeHost(b);
     cudaFree(S->arena);
     delete S;
     return SNECT_OK;
