@@ -2,7 +2,8 @@
 
 Each query's result must be the same alone (snect_foldin + snect_topk on the context) and in
 a mix of concurrent queries: the kernels and their CTA partition depend only on the query, so
-the tolerance is exact equality.  Admission follows the device-memory budget.
+the tolerance is exact equality.  Admission follows the device-memory budget, and requests
+staged in the server's pinned pool or from their own copy give the same results.
 """
 import math
 
@@ -51,6 +52,21 @@ def test_results_are_the_same_alone_and_in_the_mix(served):
     srv.stop()
     assert st["admitted"] == st["completed"] == len(queries)
     assert st["max_concurrent"] > 1  # requests overlapped on the device
+
+
+def test_requests_beyond_the_pinned_pool(served):
+    """A server keeps four pinned request buffers per slot; with one slot and 40 requests
+    submitted at once, most requests find the pool empty and are staged at admission from
+    their own copy instead.  Every result is still that of the request alone."""
+    m, c, queries, alone = served
+    srv = c.serve(n_slots=1, mem_budget_bytes=64 << 20, max_cells=15000)
+    tickets = [srv.submit(jk, x, 10) for jk, x, _ in queries]
+    for t, (u0, i0, s0) in zip(tickets, alone):
+        u, i, sc, _ = srv.poll(t, 10)
+        assert np.array_equal(u, u0) and np.array_equal(i, i0) and np.array_equal(sc, s0)
+    st = srv.stats()
+    srv.stop()
+    assert st["admitted"] == st["completed"] == len(queries) and st["max_concurrent"] == 1
 
 
 @pytest.mark.parametrize("fit", [1, 2])
