@@ -158,8 +158,10 @@ typedef struct snect_server snect_server;
 int snect_serve_start(snect_ctx *ctx, int32_t n_slots, int64_t mem_budget_bytes, int32_t max_cells,
                       snect_server **out);
 /* Queues one query: jk (host, n*2 int32 (gene, platform)), val (host, n floats) are copied
- * (into a pinned buffer from the server's pool, four per slot, when one is free);
- * 1 <= n <= max_cells, 1 <= k <= min(I1, 64).  Thread-safe.  *ticket identifies the result. */
+ * into a pinned buffer from the server's pool (four per slot); when all are in use the call
+ * waits for one to come back, up to 100 ms (SNECT_SERVE_PIN_WAIT_MS in the environment at
+ * snect_serve_start), then keeps its own copy.  1 <= n <= max_cells, 1 <= k <= min(I1, 64).
+ * Thread-safe.  *ticket identifies the result. */
 int snect_serve_submit(snect_server *srv, const int32_t *jk, const float *val, int64_t n, int32_t k,
                        int64_t *ticket);
 /* Result of a ticket: u_out (J1 floats), idx_out / score_out (k each), latency_ms (submit to

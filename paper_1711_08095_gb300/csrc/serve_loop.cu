@@ -17,6 +17,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -110,6 +111,8 @@ struct Server {
     // values into one on the submitting thread, so the scheduler only issues the copy to the
     // device; a request that finds none free keeps its own copy, staged at admission
     std::vector<char *> pin_free, pin_all;
+    std::condition_variable cv_pin;  // a pinned buffer was returned (or the server stops)
+    std::chrono::milliseconds pin_wait{100};
     std::atomic<bool> stop{false};
     std::thread worker;
     int64_t next_ticket = 1;
@@ -120,6 +123,11 @@ struct Server {
 namespace {
 
 constexpr int64_t kArenaAlign = 256;
+// How long snect_serve_submit waits for a pinned staging buffer when all are in use (100 ms,
+// or SNECT_SERVE_PIN_WAIT_MS in the environment at snect_serve_start): buffers come back as
+// requests complete, so under load the wait is short and keeps every request on the pinned
+// path; only a server that stops completing requests sends them to the fallback.
+constexpr int kPinWaitMs = 100;
 
 int64_t align_up(int64_t x) { return (x + kArenaAlign - 1) / kArenaAlign * kArenaAlign; }
 
@@ -263,7 +271,10 @@ void scheduler(Server *S) {
                 res.score.assign(s.h_score, s.h_score + s.req.k);
             }
             S->done[s.req.ticket] = std::move(res);
-            if (s.req.pin) S->pin_free.push_back(s.req.pin);
+            if (s.req.pin) {
+                S->pin_free.push_back(s.req.pin);
+                S->cv_pin.notify_one();
+            }
             s.req.pin = nullptr;
             s.busy = false;
             arena_free(S, s.arena_off, s.bytes);
@@ -305,7 +316,10 @@ void scheduler(Server *S) {
                 S->done[s.req.ticket] = std::move(res);
                 S->err = std::string("serving launch: ") + cudaGetErrorString(e);
                 cudaStreamSynchronize(s.stream);
-                if (s.req.pin) S->pin_free.push_back(s.req.pin);
+                if (s.req.pin) {
+                    S->pin_free.push_back(s.req.pin);
+                    S->cv_pin.notify_one();
+                }
                 s.req.pin = nullptr;
                 s.busy = false;
                 arena_free(S, s.arena_off, s.bytes);
@@ -368,6 +382,10 @@ int snect_serve_start(snect_ctx *h, int32_t n_slots, int64_t mem_budget_bytes, i
             return fail(c, SNECT_ENOMEM, std::string("serving slot: ") + cudaGetErrorString(e));
         }
     }
+    {
+        const char *env = getenv("SNECT_SERVE_PIN_WAIT_MS");
+        S->pin_wait = std::chrono::milliseconds(env ? std::max(0, atoi(env)) : kPinWaitMs);
+    }
     // pinned request staging: up to 4 per slot (fewer if pinned memory runs short)
     const size_t pin_bytes = (size_t)(align_up((int64_t)max_cells * sizeof(int2)) + (int64_t)sizeof(float) * max_cells);
     for (int i = 0; i < 4 * n_slots; ++i) {
@@ -394,8 +412,10 @@ int snect_serve_submit(snect_server *h, const int32_t *jk, const float *val, int
     r.t_submit = Clock::now();
     r.n = n;
     r.k = k;
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
+    {  // a pooled buffer, waiting up to kPinWait for one to come back when all are taken
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (!S->pin_all.empty())
+            S->cv_pin.wait_for(lk, S->pin_wait, [S] { return !S->pin_free.empty() || S->stop.load(); });
         if (!S->pin_free.empty()) {
             r.pin = S->pin_free.back();
             S->pin_free.pop_back();
@@ -463,6 +483,7 @@ int snect_serve_stop(snect_server *h) {
         S->stop.store(true);
     }
     S->cv_submit.notify_all();
+    S->cv_pin.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto &s : S->slots) free_slot(s);
     for (char *b : S->pin_all) cudaFreeHost(b);

@@ -54,11 +54,18 @@ def test_results_are_the_same_alone_and_in_the_mix(served):
     assert st["max_concurrent"] > 1  # requests overlapped on the device
 
 
-def test_requests_beyond_the_pinned_pool(served):
-    """A server keeps four pinned request buffers per slot; with one slot and 40 requests
-    submitted at once, most requests find the pool empty and are staged at admission from
-    their own copy instead.  Every result is still that of the request alone."""
+@pytest.mark.parametrize("wait_ms", [None, "0"])
+def test_requests_beyond_the_pinned_pool(served, wait_ms, monkeypatch):
+    """A server keeps four pinned request buffers per slot.  With one slot and 40 requests
+    submitted at once, submit waits for buffers to come back as requests complete (the
+    default); with SNECT_SERVE_PIN_WAIT_MS=0 most requests find the pool empty and are staged
+    at admission from their own copy instead.  Every result is still that of the request
+    alone."""
     m, c, queries, alone = served
+    if wait_ms is None:
+        monkeypatch.delenv("SNECT_SERVE_PIN_WAIT_MS", raising=False)
+    else:
+        monkeypatch.setenv("SNECT_SERVE_PIN_WAIT_MS", wait_ms)
     srv = c.serve(n_slots=1, mem_budget_bytes=64 << 20, max_cells=15000)
     tickets = [srv.submit(jk, x, 10) for jk, x, _ in queries]
     for t, (u0, i0, s0) in zip(tickets, alone):
