@@ -508,9 +508,10 @@ def lockfree_ablation(snect):
 def analyses(snect, served_u):
     """Downstream analyses on the paper-scale planted serving model (core 16x16x5): the
     personalised subtype matrix and its norms (Sec. 3.3) for the served new patients' folded-in
-    profiles (else the 4,500 patient rows) in one call, and k-means stratification of the 4,500
-    patient rows into 13 clusters (Sec. 3.1.1) from 13 seeded random rows; wall time of each
-    call through the C ABI."""
+    profiles (else the 4,500 patient rows) in one call, k-means stratification of the 4,500
+    patient rows into 13 clusters (Sec. 3.1.1) from 13 seeded random rows, and the QR
+    orthogonalisation post-pass of the three factors into the core; wall time of each call
+    through the C ABI (the first QR call, cold)."""
     import snect_synth as S
 
     m = S.serving_model()
@@ -529,11 +530,15 @@ def analyses(snect, served_u):
     t0 = time.perf_counter()
     a, _, upd, inertia = c.kmeans(init, 100)
     tk = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    kept = c.qr_post()
+    tq = time.perf_counter() - t0
     c.close()
     return {"subtype": {"profiles": int(u.shape[0]), "ms": ts * 1e3,
                         "of": "served new patients' fold-in profiles" if served_u is not None else "patient rows"},
             "kmeans": {"rows": I[0], "k": 13, "centroid_updates": upd, "ms": tk * 1e3,
-                       "cluster_sizes": np.bincount(a, minlength=13).tolist()}}
+                       "cluster_sizes": np.bincount(a, minlength=13).tolist()},
+            "qr_post": {"factors": [list(x.shape) for x in m.U], "modes_kept_as_were": kept, "ms": tq * 1e3}}
 
 
 def parity_config(snect):
