@@ -133,8 +133,9 @@ int snect_set_factors(snect_ctx *ctx, const float *G, const float *U1, const flo
  * u = (sum w w^T + lambda I)^{-1} sum x w over the query's n observed (gene, platform) cells.
  * The J1 x J1 Gram and right-hand side are summed in FP32 on the GPU in a fixed order and
  * solved by an FP64 Cholesky factorisation.  jk: any, n*2 int32; val: any, n float;
- * u_out: any, J1 floats.  Returns SNECT_EINVAL if n < 1 or the system is not positive
- * definite.  Synchronises. */
+ * u_out: any, J1 floats.  Returns SNECT_EINVAL if n < 1, a cell lies outside the I2 x I3
+ * table or a value is not finite (checked as the Gram kernel stages the cells), or the system
+ * is not positive definite.  Synchronises. */
 int snect_foldin(snect_ctx *ctx, const int32_t *jk, const float *val, int64_t n, float *u_out);
 
 /* Top-k search (Sec. 3.2.1): the k rows of U1 with the largest cosine similarity to u

@@ -624,9 +624,8 @@ int snect_foldin(snect_ctx *h, const int32_t *jk, const float *val, int64_t n, f
     SNECT_CUDA(c, cudaMemcpyAsync(c->q_val, val, sizeof(float) * n, cudaMemcpyDefault, c->stream));
     SNECT_CUDA(c, cudaMemcpyAsync(c->q_jk, jk, sizeof(int2) * n, cudaMemcpyDefault, c->stream));
     SNECT_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
-    SNECT_CUDA(c, launch_check_cells(c, c->stream, c->q_jk, c->q_val, n, c->flag));
     SNECT_CUDA(c, launch_foldin(c, c->stream, c->q_jk, c->q_val, n, c->wtable, c->fold_part, c->q_u,
-                                c->q_status));
+                                c->q_status, c->flag, nullptr));
     int32_t status = 0, bad = 0;
     SNECT_CUDA(c, cudaMemcpyAsync(&status, c->q_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     SNECT_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));

@@ -7,8 +7,8 @@
 // L2 terms of Sec. 2.3.2 add up to for one row.
 //   k_wtable         w_jk for every (gene, platform) pair once the factors are fixed
 //                    (I2*I3 rows of J1 floats; L2-resident at the paper's sizes);
-//   k_foldin_partial each CTA sums w w^T and x w over a fixed run of the query's cells, in
-//                    cell order (one thread per Gram element), into its own partial;
+//   k_foldin_partial each CTA checks a fixed run of the query's cells and sums w w^T and x w
+//                    over it, in cell order (one thread per Gram element), into its own partial;
 //   k_foldin_solve   one CTA adds the partials in CTA order, adds lambda I, and solves by an
 //                    FP64 Cholesky factorisation.
 // The partition into CTAs depends only on the query's size, so the result of a query is the
@@ -49,11 +49,13 @@ __global__ void k_wtable(const float *__restrict__ G, const float *__restrict__ 
     }
 }
 
-// cells [blockIdx.x * chunk, ...) of one query; part: (J1*J1 + J1) floats per CTA
+// cells [blockIdx.x * chunk, ...) of one query; part: (J1*J1 + J1) floats per CTA.  Each
+// cell is checked as it is staged: one outside the I2 x I3 table is read as (0, 0) and ORs 1
+// into *flag, a value that is not finite ORs 2 (the query is then rejected)
 __global__ void __launch_bounds__(kFoldThreads)
     k_foldin_partial(const int2 *__restrict__ jk, const float *__restrict__ val, int64_t n,
-                     int64_t chunk, const float *__restrict__ table, int32_t I3, int32_t J1,
-                     float *__restrict__ part) {
+                     int64_t chunk, const float *__restrict__ table, int32_t I2, int32_t I3, int32_t J1,
+                     float *__restrict__ part, int32_t *__restrict__ flag) {
     __shared__ float sw[kFoldTile * kMaxRank];
     __shared__ float sx[kFoldTile];
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
@@ -68,10 +70,18 @@ __global__ void __launch_bounds__(kFoldThreads)
         __syncthreads();
         for (int t = threadIdx.x; t < len * J1; t += blockDim.x) {
             const int e = t / J1, p = t % J1;
-            const int2 cell = jk[base + e];
+            int2 cell = jk[base + e];
+            if (cell.x < 0 || cell.x >= I2 || cell.y < 0 || cell.y >= I3) {
+                cell = make_int2(0, 0);
+                if (p == 0) atomicOr(flag, 1);
+            }
             sw[e * J1 + p] = table[((int64_t)cell.x * I3 + cell.y) * J1 + p];
         }
-        for (int t = threadIdx.x; t < len; t += blockDim.x) sx[t] = val[base + t];
+        for (int t = threadIdx.x; t < len; t += blockDim.x) {
+            const float x = val[base + t];
+            if (!isfinite(x)) atomicOr(flag, 2);
+            sx[t] = x;
+        }
         __syncthreads();
         // four independent sums over the cells (e mod 4), added in a fixed order at the end
 #pragma unroll
@@ -114,12 +124,19 @@ __global__ void __launch_bounds__(kFoldThreads)
     if (threadIdx.x < J1) out[nG + threadIdx.x] = accx;
 }
 
+// flag_out, if given, receives the partials' cell flag, which is zeroed for the next query
+// of the stream (every partial CTA has finished when this kernel starts)
 __global__ void __launch_bounds__(kFoldThreads)
     k_foldin_solve(const float *__restrict__ part, int32_t n_part, int32_t J1, float ridge,
-                   float *__restrict__ u_out, int32_t *__restrict__ status) {
+                   float *__restrict__ u_out, int32_t *__restrict__ status, int32_t *__restrict__ flag,
+                   int32_t *__restrict__ flag_out) {
     __shared__ double M[kMaxRank * kMaxRank];
     __shared__ double rhs[kMaxRank];
     __shared__ double dinv[kMaxRank];  // 1 / L[j][j]
+    if (flag_out && threadIdx.x == 0) {
+        *flag_out = *flag;
+        *flag = 0;
+    }
     const int nG = J1 * J1;
     for (int s = threadIdx.x; s < nG + J1; s += blockDim.x) {
         float a = 0.f;
@@ -238,27 +255,7 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// validates a query's cells in place: out-of-range cells become (0, 0) and set the flag
-__global__ void k_check_cells(int2 *__restrict__ jk, const float *__restrict__ val, int64_t n,
-                              int32_t I2, int32_t I3, int32_t *flag) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int2 c = jk[e];
-    if (c.x < 0 || c.x >= I2 || c.y < 0 || c.y >= I3) {
-        jk[e] = make_int2(0, 0);
-        atomicOr(flag, 1);
-    }
-    if (!isfinite(val[e])) atomicOr(flag, 2);
-}
-
 }  // namespace
-
-cudaError_t launch_check_cells(Ctx *c, cudaStream_t st, int2 *jk, const float *val, int64_t n,
-                               int32_t *flag) {
-    k_check_cells<<<ceil_div(n, 256), 256, 0, st>>>(jk, val, n, c->d.I2, c->d.I3, flag);
-    c->launches++;
-    return cudaGetLastError();
-}
 
 int64_t foldin_parts(int64_t n) { return std::max<int64_t>(1, ceil_div(n, kFoldChunk)); }
 
@@ -271,11 +268,13 @@ cudaError_t launch_wtable(Ctx *c, float *table) {
 }
 
 cudaError_t launch_foldin(Ctx *c, cudaStream_t st, const int2 *jk, const float *val, int64_t n,
-                          const float *table, float *part, float *u_out, int32_t *status) {
+                          const float *table, float *part, float *u_out, int32_t *status, int32_t *flag,
+                          int32_t *flag_out) {
     const int64_t np = foldin_parts(n);
-    k_foldin_partial<<<(unsigned)np, kFoldThreads, 0, st>>>(jk, val, n, kFoldChunk, table, c->d.I3,
-                                                            c->d.J1, part);
-    k_foldin_solve<<<1, kFoldThreads, 0, st>>>(part, (int32_t)np, c->d.J1, c->cfg.lambda, u_out, status);
+    k_foldin_partial<<<(unsigned)np, kFoldThreads, 0, st>>>(jk, val, n, kFoldChunk, table, c->d.I2, c->d.I3,
+                                                            c->d.J1, part, flag);
+    k_foldin_solve<<<1, kFoldThreads, 0, st>>>(part, (int32_t)np, c->d.J1, c->cfg.lambda, u_out, status, flag,
+                                               flag_out);
     c->launches += 2;
     return cudaGetLastError();
 }

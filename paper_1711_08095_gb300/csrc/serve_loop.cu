@@ -69,7 +69,6 @@ struct Slot {
     Server *srv = nullptr;
     int index = 0;
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
     // pinned staging of a request: its cells, then its values at the offset they take in the
     // arena block, so that one copy moves both
     char *h_in = nullptr;
@@ -84,6 +83,8 @@ struct Slot {
     float *d_val = nullptr, *d_part = nullptr;
     float *d_u = nullptr, *d_score = nullptr, *d_top_s = nullptr;
     int32_t *d_status = nullptr, *d_top_i = nullptr, *d_flag = nullptr;
+    // the fold-in's cell flag: its solve moves it to d_flag and zeroes it for the next request
+    int32_t *d_cell_flag = nullptr;
     uint8_t *d_taken = nullptr;
     bool busy = false;
     Request req;
@@ -173,19 +174,18 @@ void free_slot(Slot &s) {
     cudaFree(s.d_res);
     cudaFree(s.d_score);
     cudaFree(s.d_taken);
-    if (s.done) cudaEventDestroy(s.done);
+    cudaFree(s.d_cell_flag);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
 }
 
-// the slot's stream, events, pinned staging for max_cells cells and its small fixed device
+// the slot's stream, pinned staging for max_cells cells and its small fixed device
 // buffers; the request's cells and partials come from the arena at admission
 cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
     cudaError_t e;
 #define TRY(x)                         \
     if ((e = (x)) != cudaSuccess) return e;
     TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
-    TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
     TRY(cudaMallocHost((void **)&s.h_in, align_up((int64_t)max_cells * sizeof(int2)) + sizeof(float) * max_cells));
     TRY(cudaMallocHost((void **)&s.h_res, kResBytes));
     TRY(cudaMalloc((void **)&s.d_res, kResBytes));
@@ -200,6 +200,8 @@ cudaError_t alloc_slot(Ctx *c, Slot &s, int32_t max_cells) {
     s.d_status = s.d_flag + 1;
     TRY(cudaMalloc((void **)&s.d_score, sizeof(float) * c->d.I1));
     TRY(cudaMalloc((void **)&s.d_taken, c->d.I1));
+    TRY(cudaMalloc((void **)&s.d_cell_flag, sizeof(int32_t)));
+    TRY(cudaMemset(s.d_cell_flag, 0, sizeof(int32_t)));
 #undef TRY
     return cudaSuccess;
 }
@@ -234,14 +236,14 @@ cudaError_t launch_request(Ctx *c, Slot &s) {
         staged = s.h_in;
     }
     cudaError_t e;
+    // six calls: the copy in, four kernels (the cells are checked inside the fold-in's
+    // partials), the copy back of every result; then the hand-over to the scheduler
     if ((e = cudaMemcpyAsync(base, staged, val_off + sizeof(float) * n, cudaMemcpyHostToDevice, s.stream))) return e;
-    if ((e = cudaMemsetAsync(s.d_flag, 0, sizeof(int32_t), s.stream))) return e;
-    if ((e = launch_check_cells(c, s.stream, s.d_jk, s.d_val, n, s.d_flag))) return e;
-    if ((e = launch_foldin(c, s.stream, s.d_jk, s.d_val, n, c->wtable, s.d_part, s.d_u, s.d_status))) return e;
+    if ((e = launch_foldin(c, s.stream, s.d_jk, s.d_val, n, c->wtable, s.d_part, s.d_u, s.d_status, s.d_cell_flag,
+                           s.d_flag)))
+        return e;
     if ((e = launch_topk(c, s.stream, s.d_u, r.k, s.d_score, s.d_taken, s.d_top_i, s.d_top_s))) return e;
-    // every result in one copy back
     if ((e = cudaMemcpyAsync(s.h_res, s.d_res, kResBytes, cudaMemcpyDeviceToHost, s.stream))) return e;
-    if ((e = cudaEventRecord(s.done, s.stream))) return e;
     return cudaLaunchHostFunc(s.stream, on_slot_done, &s);
 }
 
@@ -259,7 +261,13 @@ void scheduler(Server *S) {
             const auto now = Clock::now();
             res.latency_ms = std::chrono::duration<double, std::milli>(now - s.req.t_submit).count();
             res.queue_ms = std::chrono::duration<double, std::milli>(s.t_admit - s.req.t_submit).count();
-            const cudaError_t q = cudaEventQuery(s.done);
+            // the stream holds only this request's work, all done but for the hand-over call,
+            // which may still be returning (not ready); any other answer is a device error
+            cudaError_t q = cudaStreamQuery(s.stream);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();
+                q = cudaSuccess;
+            }
             if (q != cudaSuccess) {
                 res.status = SNECT_ECUDA;
                 S->err = std::string("serving: ") + cudaGetErrorString(q);
@@ -316,6 +324,8 @@ void scheduler(Server *S) {
                 S->done[s.req.ticket] = std::move(res);
                 S->err = std::string("serving launch: ") + cudaGetErrorString(e);
                 cudaStreamSynchronize(s.stream);
+                // a partial launch may have left cell flags for the next request on this slot
+                cudaMemset(s.d_cell_flag, 0, sizeof(int32_t));
                 if (s.req.pin) {
                     S->pin_free.push_back(s.req.pin);
                     S->cv_pin.notify_one();

@@ -102,6 +102,11 @@ def test_bad_queries_are_rejected(served):
     bad[5, 0] = m.U[1].shape[0]
     with pytest.raises(snect.SnectError):
         c.foldin(bad, x)
+    for col, v in ((0, -1), (1, -1), (1, m.U[2].shape[0])):  # gene below, platform either side
+        bad = jk.copy()
+        bad[99, col] = v  # the last cell of the last CTA
+        with pytest.raises(snect.SnectError):
+            c.foldin(bad, x)
     xn = x.copy()
     xn[3] = np.inf
     with pytest.raises(snect.SnectError):

@@ -96,21 +96,27 @@ def test_admission_follows_the_memory_budget(served, fit):
 
 
 def test_bad_requests(served):
+    """Out-of-range cells and non-finite values fail their own request only.  With one slot,
+    the request after a bad one runs on the same stream and must not see its flag."""
     import paper_1711_08095_gb300 as snect
 
     m, c, queries, _ = served
     with pytest.raises(snect.SnectError):
         c.serve(n_slots=2, mem_budget_bytes=1000, max_cells=15000)  # below one largest request
-    srv = c.serve(n_slots=2, mem_budget_bytes=64 << 20, max_cells=1000)
+    srv = c.serve(n_slots=1, mem_budget_bytes=64 << 20, max_cells=1000)
     jk, x, _ = queries[0]
     with pytest.raises(snect.SnectError):
         srv.submit(jk, x, 10)  # more cells than max_cells
-    bad = jk[:50].copy()
-    bad[3, 0] = 10 ** 6
-    t = srv.submit(bad, x[:50], 10)
-    with pytest.raises(snect.SnectError):
-        srv.poll(t, 10)
-    t = srv.submit(jk[:50], x[:50], 10)  # the server keeps serving
-    u, _, _, _ = srv.poll(t, 10)
-    assert np.isfinite(u).all()
+    u0 = c.foldin(jk[:50], x[:50])
+    bad_cell = jk[:50].copy()
+    bad_cell[3, 0] = 10 ** 6
+    bad_val = x[:50].copy()
+    bad_val[7] = np.nan
+    for bj, bx in ((bad_cell, x[:50]), (jk[:50], bad_val)):
+        t = srv.submit(bj, bx, 10)
+        with pytest.raises(snect.SnectError):
+            srv.poll(t, 10)
+        t = srv.submit(jk[:50], x[:50], 10)  # the server keeps serving
+        u, _, _, _ = srv.poll(t, 10)
+        assert np.array_equal(u, u0)
     srv.stop()
