@@ -44,7 +44,7 @@ def test_foldin_matches_oracle(served, n):
 
 def test_foldin_matches_oracle_at_the_largest_query(gpu_lib):
     """The serving workload's largest query: 75,000 cells (every (gene, platform) pair of a
-    15,000 x 5 model), 19 partial-sum CTAs."""
+    15,000 x 5 model), 293 partial-sum CTAs of 256 cells."""
     import paper_1711_08095_gb300 as snect
 
     m = S.serving_model(I=(600, 15000, 5), J=(16, 16, 5))
