@@ -160,7 +160,21 @@ __global__ void __launch_bounds__(kFoldThreads)
             if (lane == 0) *status = 1;
             return;
         }
-        const double d = sqrt(dj), inv = 1.0 / d;
+        // 1/sqrt(dj) from the FP32 estimate and two Newton-Raphson steps r <- r (3 - dj r^2) / 2
+        // (each squares the relative error: 2^-22 -> 2^-43 -> below FP64 rounding), then
+        // sqrt(dj) = dj r; pivots outside the FP32 normal range take the FP64 square root
+        double inv, d;
+        const float jf = (float)dj;
+        if (jf >= 1.1754944e-38f && jf <= 3.4e38f) {
+            double r = (double)rsqrtf(jf);
+            r = r * (1.5 - 0.5 * dj * r * r);
+            r = r * (1.5 - 0.5 * dj * r * r);
+            inv = r;
+            d = dj * r;
+        } else {
+            d = sqrt(dj);
+            inv = 1.0 / d;
+        }
         __syncwarp(FULL);
         if (lane == j) {
             M[j * J1 + j] = d;
