@@ -41,7 +41,8 @@ def _digest(files, flags) -> str:
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compiles every csrc/*.cu and links libsnect.so; returns the library path."""
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+                     glob.glob(os.path.join(ROOT, "include", "*.h")))
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
     digest = _digest(sources + headers, CFLAGS)

@@ -26,6 +26,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "common.cuh"
 #include "serve.cuh"
 
@@ -100,7 +101,7 @@ struct Server {
     int64_t budget = 0;
     int64_t in_flight_bytes = 0;
     char *arena = nullptr;                 // the budget: one device allocation
-    std::map<int64_t, int64_t> free_blocks;  // arena offset -> bytes, coalesced
+    ArenaBlocks blocks;                    // the arena's free blocks (first fit, merged)
     std::vector<int> finished;             // slots whose stream work has completed
     bool kick = false;                     // a request was submitted since the scheduler last looked
     std::vector<Slot> slots;
@@ -137,34 +138,6 @@ int64_t align_up(int64_t x) { return (x + kArenaAlign - 1) / kArenaAlign * kAren
 int64_t request_bytes(const Ctx *c, int64_t n) {
     return align_up(n * (int64_t)sizeof(int2)) + align_up(n * (int64_t)sizeof(float)) +
            align_up(foldin_parts(n) * ((int64_t)c->d.J1 * c->d.J1 + c->d.J1) * (int64_t)sizeof(float));
-}
-
-// first fit in the arena (scheduler thread, under the server lock); -1 if no block is large enough
-int64_t arena_alloc(Server *S, int64_t bytes) {
-    for (auto it = S->free_blocks.begin(); it != S->free_blocks.end(); ++it) {
-        if (it->second < bytes) continue;
-        const int64_t off = it->first, rest = it->second - bytes;
-        S->free_blocks.erase(it);
-        if (rest > 0) S->free_blocks[off + bytes] = rest;
-        return off;
-    }
-    return -1;
-}
-
-void arena_free(Server *S, int64_t off, int64_t bytes) {
-    auto it = S->free_blocks.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != S->free_blocks.end() && it->first + it->second == nx->first) {  // merge with the next
-        it->second += nx->second;
-        S->free_blocks.erase(nx);
-    }
-    if (it != S->free_blocks.begin()) {  // and with the previous
-        auto pv = std::prev(it);
-        if (pv->first + pv->second == it->first) {
-            pv->second += it->second;
-            S->free_blocks.erase(it);
-        }
-    }
 }
 
 void free_slot(Slot &s) {
@@ -285,7 +258,7 @@ void scheduler(Server *S) {
             }
             s.req.pin = nullptr;
             s.busy = false;
-            arena_free(S, s.arena_off, s.bytes);
+            S->blocks.release(s.arena_off, s.bytes);
             s.arena_off = -1;
             S->in_flight_bytes -= s.bytes;
             S->completed++;
@@ -301,7 +274,7 @@ void scheduler(Server *S) {
                 }
             if (free_slot_i < 0) break;
             const int64_t need = request_bytes(c, S->queue.front().n);
-            const int64_t off = arena_alloc(S, need);
+            const int64_t off = S->blocks.alloc(need);  // first fit
             if (off < 0) break;  // wait for requests in flight to return their memory
             Slot &s = S->slots[free_slot_i];
             s.req = std::move(S->queue.front());
@@ -332,7 +305,7 @@ void scheduler(Server *S) {
                 }
                 s.req.pin = nullptr;
                 s.busy = false;
-                arena_free(S, s.arena_off, s.bytes);
+                S->blocks.release(s.arena_off, s.bytes);
                 s.arena_off = -1;
                 S->in_flight_bytes -= s.bytes;
                 S->cv_done.notify_all();
@@ -377,7 +350,7 @@ int snect_serve_start(snect_ctx *h, int32_t n_slots, int64_t mem_budget_bytes, i
         cudaGetLastError();
         return fail(c, SNECT_ENOMEM, std::string("serving arena: ") + cudaGetErrorString(ea));
     }
-    S->free_blocks[0] = mem_budget_bytes;
+    S->blocks.reset(mem_budget_bytes);
     S->slots.resize(n_slots);
     for (int i = 0; i < n_slots; ++i) {
         Slot &s = S->slots[i];
